@@ -1,0 +1,304 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics (CPU only).
+
+Each test names the property it pins and the definition it follows.  None of them re-types the
+oracle's own formula: they use brute-force sums over closed triangles (C), closed forms for
+plane waves, Parseval's identity, expectations of seeded Gaussian fields with a known spectrum,
+and published known-answer vectors.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import binning, brute, ideal, philox, unwindowed
+from paper_2404_07249_gb300 import synth
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --------------------------------------------------------------------------------------- generator
+
+def test_philox_known_answers():
+    """Philox4x32-10 reproduces the published Random123 known-answer vectors (Salmon et al., SC'11)."""
+    rows = [l.split() for l in open(os.path.join(GOLD, "philox4x32_10_kat.txt")) if l.strip() and l[0] != "#"]
+    assert rows
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        out = philox.philox4x32_10(*v[:6])
+        assert [int(o) for o in out] == v[6:10]
+
+
+def test_gaussian_draws_moments():
+    """Box-Muller on Philox: unit-variance, zero-mean, uncorrelated cells, fourth moment 3 (Gaussian)."""
+    z = philox.gaussian_draw(400_000, seed=12345, draw=3, stream=1)
+    assert abs(z.mean()) < 5.0 / math.sqrt(z.size)
+    assert abs(z.var() - 1.0) < 6.0 * math.sqrt(2.0 / z.size)
+    assert abs(np.mean(z[1:] * z[:-1])) < 5.0 / math.sqrt(z.size)
+    assert abs(np.mean(z ** 4) - 3.0) < 0.05
+    z2 = philox.gaussian_draw(1000, seed=12345, draw=4, stream=1)
+    assert not np.allclose(z[:1000], z2)
+
+
+# --------------------------------------------------------------------------------------- N_abc and S_abc
+
+def _cubic(n, box, edges_kf):
+    kf = binning.kf_of(box)
+    return (n, n, n), kf, kf * np.asarray(edges_kf, dtype=float)
+
+
+@pytest.mark.parametrize("n,edges_kf", [(16, [1, 2.5, 4, 5.5, 7.0]), (32, [1, 3, 5, 7, 9, 11, 13])])
+def test_nabc_equals_brute_force_count(n, edges_kf):
+    """N_abc = N^2 T_abc equals the number of closed ordered triangles counted one by one
+    (Sec. 4.1, eq. N-ell-def with P_fid = 1; the FFT form of Sec. 4.3.1)."""
+    grid, kf, edges = _cubic(n, 1000.0, edges_kf)
+    nb = len(edges) - 1
+    N = n ** 3
+    bins = binning.bin_grid(grid, 1000.0, edges)
+    T = ideal.triple_sums(ideal.unit_maps(bins, nb))
+    cnt, _ = brute.brute_bk(None, grid, kf, edges)
+    assert np.array_equal(np.rint(N * N * T), cnt)
+    assert np.max(np.abs(N * N * T - cnt)) < 1e-6 * max(1.0, cnt.max())
+    closed = ideal.closed_triplets(T, N)
+    assert closed == [t for t in binning.triplets(nb) if cnt[t] > 0]
+
+
+@pytest.mark.parametrize("kind", ["grf", "lognormal"])
+def test_sabc_equals_brute_force_triangle_sum(kind):
+    """S_abc = sum_x g_a g_b g_c equals (1/N^2) sum over closed triangles of D(k1) D(k2) D(k3)
+    (separable form eq. beta-def vs the k-space definition eq. beta-def1)."""
+    grid, kf, edges = _cubic(16, 1000.0, [1, 2.5, 4, 5.5, 7.0])
+    f = synth.gaussian_field(grid, (1000.0,) * 3, 5) if kind == "grf" else \
+        synth.lognormal_field(grid, (1000.0,) * 3, 5)
+    f = f.astype(np.float32)
+    N = f.size
+    D = ideal.forward(f)
+    bins = binning.bin_grid(grid, 1000.0, edges)
+    S = ideal.triple_sums(ideal.shell_maps(D, bins, len(edges) - 1))
+    _, sdd = brute.brute_bk(D, grid, kf, edges)
+    assert np.max(np.abs(S - sdd / N ** 2)) <= 1e-11 * np.max(np.abs(S))
+
+
+def test_mixed_sums_equal_brute_force():
+    """The mixed sums of the linear term, sum_x gu_a gv_b gv_c, equal the closed-triangle sum of
+    U(k1) V(k2) V(k3) (Sec. 4.3.2, eq. b-numerator-practical)."""
+    grid, kf, edges = _cubic(16, 1000.0, [1, 2.5, 4, 5.5, 7.0])
+    u = synth.gaussian_field(grid, (1000.0,) * 3, 1)
+    v = synth.lognormal_field(grid, (1000.0,) * 3, 2)
+    nb = len(edges) - 1
+    bins = binning.bin_grid(grid, 1000.0, edges)
+    U, V = ideal.forward(u), ideal.forward(v)
+    M = ideal.mixed_triple_sums(ideal.shell_maps(U, bins, nb), ideal.shell_maps(V, bins, nb))
+    _, sdd = brute.brute_bk(U, grid, kf, edges, D2=V, D3=V)
+    assert np.max(np.abs(M - sdd / u.size ** 2)) <= 1e-11 * np.max(np.abs(M))
+
+
+def test_plane_wave_bispectrum_closed_form():
+    """Three cosines with k1 + k2 + k3 = 0 (and no other vanishing combination): the only closed
+    triangles are (k1,k2,k3) and its negative, so S_abc = (N/4) cos(phi1 + phi2 + phi3) for their bins
+    and 0 for every other triplet; N_abc is unchanged by the field."""
+    n = 32
+    grid = (n, n, n)
+    box = 1000.0
+    kf = binning.kf_of(box)
+    k1, k2 = np.array([3, 0, 0]), np.array([0, 5, 1])
+    k3 = -(k1 + k2)
+    ph = [0.3, -1.1, 0.7]
+    f = synth.plane_wave_field(grid, [(1.0, tuple(k1), ph[0]), (1.0, tuple(k2), ph[1]), (1.0, tuple(k3), ph[2])])
+    edges = kf * np.array([2.5, 3.5, 5.5, 6.5])   # bins: |n|=3 ; |n|^2 in (12.25,30.25) ; |n|=6ish
+    nb = 3
+    bins = binning.bin_grid(grid, box, edges)
+    D = ideal.forward(f)
+    S = ideal.triple_sums(ideal.shell_maps(D, bins, nb))
+    ba = int(binning.bin_of_s(np.array([k1 @ k1]), kf, edges)[0])
+    bb = int(binning.bin_of_s(np.array([k2 @ k2]), kf, edges)[0])
+    bc = int(binning.bin_of_s(np.array([k3 @ k3]), kf, edges)[0])
+    assert len({ba, bb, bc}) == 3
+    expect = np.zeros((nb, nb, nb))
+    val = (f.size / 4.0) * math.cos(sum(ph))
+    for p in [(ba, bb, bc), (ba, bc, bb), (bb, ba, bc), (bb, bc, ba), (bc, ba, bb), (bc, bb, ba)]:
+        expect[p] = val
+    assert np.max(np.abs(S - expect)) < 1e-9 * f.size
+
+
+def test_sum_rule_over_third_bin():
+    """Linearity: sum over all c of S_abc = sum_x g_a g_b delta_R with delta_R = IFT[D on binned modes]."""
+    grid, kf, edges = _cubic(24, 1000.0, [1, 3, 5, 7, 9, 11])
+    f = synth.lognormal_field(grid, (1000.0,) * 3, 3)
+    nb = len(edges) - 1
+    bins = binning.bin_grid(grid, 1000.0, edges)
+    D = ideal.forward(f)
+    g = ideal.shell_maps(D, bins, nb)
+    S = ideal.triple_sums(g)
+    dR = np.fft.ifftn(np.where(bins >= 0, D, 0.0)).real
+    for a in range(nb):
+        for b in range(nb):
+            ref = np.sum(g[a] * g[b] * dR)
+            assert abs(S[a, b].sum() - ref) <= 1e-10 * np.sum(np.abs(g[a] * g[b] * dR))
+
+
+# --------------------------------------------------------------------------------------- P_ell
+
+def test_parseval_and_full_coverage():
+    """Parseval: sum_x delta^2 = (1/N) sum_k |D|^2.  With bins covering every k != 0 mode, the binned
+    monopole numerators add up to sum_k |D|^2 - |D(0)|^2 (no mode dropped or double counted)."""
+    grid = (32, 32, 32)
+    box = 700.0
+    kf = binning.kf_of(box)
+    f = synth.lognormal_field(grid, (box,) * 3, 9).astype(np.float32).astype(np.float64)
+    f += 0.25  # nonzero mean: D(0) must be excluded from every bin
+    D = ideal.forward(f)
+    N = f.size
+    assert abs(np.sum(f * f) - np.sum(np.abs(D) ** 2) / N) < 1e-12 * np.sum(f * f)
+    edges = kf * np.array([0.0, 3.0, 7.5, 12.0, 20.0, 28.0])   # top above sqrt(3)*16
+    r = ideal.pk_ideal(f, box, edges, 0)
+    tot = np.sum(r["P"][0] * r["counts"]) * N * N / box ** 3
+    assert abs(tot - (np.sum(np.abs(D) ** 2) - abs(D[0, 0, 0]) ** 2)) < 1e-10 * tot
+    assert r["counts"].sum() == N - 1
+
+
+def test_pk_recovers_known_spectrum_with_kaiser():
+    """Mean of P_ell over seeded GRFs with D = W sqrt(P N / V) (1 + beta mu^2) matches the exact
+    expectation (2 ell + 1) (1/N_b) sum_{k in b} L_ell(mu) (1 + beta mu^2)^2 P(|k|)
+    (Sec. 3.4.1, eqs. pk-limit and fish-ideal-continuous; ell = 0, 2, 4)."""
+    w = synth.WORKLOADS[1]
+    grid, box = w.grid, w.box
+    edges = w.pk_edges
+    beta = 0.5
+    R = 24
+    acc = 0.0
+    for i in range(R):
+        f = synth.gaussian_field(grid, (box,) * 3, 50 + i, kaiser_beta=beta).astype(np.float32)
+        acc = acc + ideal.pk_ideal(f, box, edges, 4)["P"]
+    mean = acc / R
+    nb = len(edges) - 1
+    bins = binning.bin_grid(grid, box, edges)
+    mu2 = binning.mu2_grid(grid)
+    kmag = binning.kf_of(box) * np.sqrt(binning.n2_grid(grid).astype(float))
+    ptrue = synth.power_law(kmag) * (1.0 + beta * mu2) ** 2
+    counts = binning.mode_counts(bins, nb)
+    sel = bins >= 0
+    for il, ell in enumerate([0, 2, 4]):
+        L = binning.legendre(ell, mu2)
+        expect = (2 * ell + 1) * np.bincount(bins[sel], weights=(L * ptrue)[sel], minlength=nb) / counts
+        # variance of the per-realisation estimate: sum over independent +-k pairs of (2l+1)^2 L^2 P^2 / N_b^2
+        var = (2 * ell + 1) ** 2 * 2.0 * np.bincount(bins[sel], weights=(L * L * ptrue * ptrue)[sel],
+                                                    minlength=nb) / counts ** 2
+        z = (mean[il] - expect) / np.sqrt(var / R)
+        assert np.max(np.abs(z[1:])) < 4.5, (ell, z)
+
+
+def test_discrete_fisher_reduces_to_continuous_for_isotropic_sum():
+    """The discrete ideal Fisher (eq. pk-limit) is (1/2) sum_{k in b} L L'; for ell = ell' = 0 it is
+    N_b / 2 exactly, i.e. the continuous diagonal (eq. fish-ideal-continuous) at ell = 0."""
+    w = synth.WORKLOADS[1]
+    f = synth.gaussian_field(w.grid, (w.box,) * 3, 3).astype(np.float32)
+    r = ideal.pk_ideal(f, w.box, w.pk_edges, 4)
+    assert np.allclose(r["fisher"][:, 0, 0], 0.5 * r["counts"])
+    # monopole-only bins with ell-coupling: discrete and continuous P_0 agree to O(discreteness)
+    rel = np.abs(r["P_discrete"][0, 2:] - r["P"][0, 2:]) / np.abs(r["P"][0, 2:])
+    assert np.median(rel) < 0.1
+
+
+# --------------------------------------------------------------------------------------- B statistics
+
+def test_gaussian_bispectrum_mean_is_zero():
+    """For Gaussian fields <delta delta delta> = 0: the ideal B estimates over seeded realisations have
+    zero mean (per-triplet t statistics; at most a few beyond 3 sigma, none beyond 5)."""
+    grid = (32, 32, 32)
+    box = 1000.0
+    edges = binning.kf_of(box) * np.array([1, 3, 5, 7, 9, 11.0])
+    R = 40
+    vals = []
+    for i in range(R):
+        f = synth.gaussian_field(grid, (box,) * 3, 300 + i).astype(np.float32)
+        vals.append(ideal.bk_ideal(f, box, edges)["B"])
+    vals = np.array(vals)
+    t = vals.mean(0) / (vals.std(0, ddof=1) / math.sqrt(R))
+    assert np.max(np.abs(t)) < 5.0
+    assert np.mean(np.abs(t) > 3.0) < 0.05
+
+
+def test_lognormal_bispectrum_is_positive():
+    """A lognormal field has a positive bispectrum on all configurations (skewed one-point law);
+    the ideal estimator must see it (guards against sign errors in the triple product)."""
+    grid = (32, 32, 32)
+    box = 1000.0
+    edges = binning.kf_of(box) * np.array([1, 3, 5, 7, 9.0])
+    acc = 0.0
+    for i in range(6):
+        acc = acc + ideal.bk_ideal(synth.lognormal_field(grid, (box,) * 3, 70 + i).astype(np.float32), box,
+                                   edges)["B"]
+    assert np.all(acc > 0)
+
+
+# --------------------------------------------------------------------------------------- unwindowed
+
+def test_linear_term_vanishes_for_translation_averaged_mocks():
+    """Ideal limit (n = w = 1): the linear term averages <g_b[v] g_c[v]> over mocks; for a translation-
+    invariant average this is constant in x and multiplies sum_x g_a[u] = 0 (k = 0 is never binned),
+    so lin = 0 (Sec. 4.4.1: the linear term vanishes in the ideal limit).  The mocks are all cyclic
+    translates of one field, which makes the average exactly translation invariant."""
+    n = 8
+    grid = (n, n, n)
+    box = 400.0
+    edges = binning.kf_of(box) * np.array([0.5, 1.5, 2.5, 3.5])
+    bins = binning.bin_grid(grid, box, edges)
+    nb = 3
+    trip = binning.triplets(nb)
+    d = synth.lognormal_field(grid, (box,) * 3, 11)
+    v0 = synth.lognormal_field(grid, (box,) * 3, 12)
+    mocks = [np.roll(v0, (i, j, k), axis=(0, 1, 2)) for i in range(n) for j in range(n) for k in range(n)]
+    one = np.ones(grid)
+    r = unwindowed.bk_numerator(d, one, mocks, bins, nb, trip)
+    scale = np.max(np.abs(r["S"]))
+    assert np.max(np.abs(r["lin"])) < 1e-10 * scale
+    # and with a single mock it does not vanish (the test is not vacuous)
+    r1 = unwindowed.bk_numerator(d, one, mocks[:1], bins, nb, trip)
+    assert np.max(np.abs(r1["lin"])) > 1e-3 * scale
+
+
+def test_unwindowed_pk_unbiased_on_masked_mocks():
+    """Sec. 3.2 (eq. pk-estimator-def): with a bandpower-step spectrum P = sum_b p_b Theta_b (ell = 0),
+    no noise and any weighting, E[F^-1 p_num] = p.  Masked GRF mocks d = n delta with an FKP weight;
+    the Fisher matrix from Gaussian Monte Carlo draws (eq. fish-from-Q)."""
+    n = 24
+    grid = (n, n, n)
+    box = 600.0
+    kf = binning.kf_of(box)
+    edges = kf * np.array([0.0, 2.0, 4.0, 6.0, 8.0, 10.0])
+    nb = 5
+    ptrue = np.array([4.0e3, 3.0e3, 2.0e3, 1.5e3, 1.0e3])
+
+    def pk_step(k):
+        b = binning.bin_of_s(np.rint((k / kf) ** 2).astype(np.int64), kf, edges)
+        return np.where(b >= 0, ptrue[np.clip(b, 0, nb - 1)], 0.0)
+
+    geom = synth.SurveyGeometry(r_min=60.0, r_max=290.0, n_holes=4, hole_radius=30.0, n0=3.0e-4, r0=180.0,
+                                s2=2.0e4)
+    nmask = synth.survey_mask(grid, (box,) * 3, 5, geom)
+    w = unwindowed.fkp_weight(nmask, 1.0e4)
+    bins = binning.bin_grid(grid, box, edges)
+    mu2 = binning.mu2_grid(grid)
+    F = unwindowed.pk_fisher(nmask, w, bins, mu2, nb, [0], seed=77, n_mc=60)
+    est = []
+    for i in range(60):
+        dG = synth.gaussian_field(grid, (box,) * 3, 900 + i, pk=pk_step)
+        pn = unwindowed.pk_numerator(nmask * dG, w, bins, mu2, nb, [0])
+        est.append(unwindowed.solve(F, pn.ravel()) * box ** 3 / dG.size)
+    est = np.array(est)
+    z = (est.mean(0) - ptrue) / (est.std(0, ddof=1) / math.sqrt(len(est)))
+    assert np.max(np.abs(z)) < 4.0, z
+    # the windowed (ideal-on-masked) estimate is visibly biased: the test is not vacuous
+    ideal_on_masked = np.mean([ideal.pk_ideal(nmask * synth.gaussian_field(grid, (box,) * 3, 900 + i, pk=pk_step),
+                                              box, edges, 0)["P"][0] for i in range(10)], axis=0)
+    assert np.max(np.abs(ideal_on_masked / ptrue - 1.0)) > 0.5
+
+
+def test_fisher_solve_inverts():
+    """x = F^-1 b satisfies F x = b for a nonsymmetric Monte Carlo Fisher (eq. bk-estimator-def)."""
+    rng = np.random.Generator(np.random.PCG64(3))
+    F = np.eye(40) * 5 + rng.standard_normal((40, 40)) * 0.3
+    b = rng.standard_normal(40)
+    x = unwindowed.solve(F, b)
+    assert np.max(np.abs(F @ x - b)) < 1e-12
