@@ -1,0 +1,329 @@
+"""Throughput benchmark of the ideal bispectrum + P_ell hot path on one GB300 per rank.
+
+Default workload: 512^3 lognormal field with a Kaiser factor, box 2000 Mpc/h, 30 linear k-bins to 0.3 h/Mpc,
+bispectrum of every closed triplet plus P_ell (ell = 0, 2).  A step = one field through the whole ideal path
+(forward FFT, shell filter + inverse FFTs, triplet contraction, P_ell binning) via polybin_bk_pk_ideal.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--prec split|fp32|fp64] [--impl ours|reference]
+
+Under torchrun each rank runs its own realisation on its own GPU (weak scaling, no data-path collective);
+timing is bracketed by a barrier + synchronize and the maximum over ranks is reported.  Inputs (537 MB per
+field) are larger than L2, so no flush is needed between steps.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "512^3 bispectrum estimates/s, split-TC vs FP64 GPU path at 1e-6 rel. error"
+UNIT = "estimates/s"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+
+        def reader():
+            for line in self.proc.stdout:
+                self.rows.append([x.strip() for x in line.split(",")])
+
+        self.thread = threading.Thread(target=reader, daemon=True)
+        self.thread.start()
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            if len(r) < 9:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _workload(cfg: int):
+    from paper_2404_07249_gb300 import synth
+    w = synth.WORKLOADS[cfg]
+    edges = w.bk_edges
+    return w, edges
+
+
+def cpu_baseline(cfg: int, field: np.ndarray, edges, box: float, budget_s: float = 25.0) -> dict:
+    """The FP64 oracle as it stands, timed on the host cores on a bounded sample of the same workload:
+    one forward FFT of the field, one shell map (filter + inverse FFT) and the oracle's triple-sum routine on
+    all n_b shell maps restricted to a contiguous slab of cells; the per-estimate time is
+    t_forward + n_b t_shell + t_triple (N / N_slab) (every step of the oracle pipeline scales linearly in these)."""
+    from oracle import binning, ideal
+    nb = len(edges) - 1
+    N = field.size
+    t0 = time.perf_counter()
+    D = ideal.forward(field)
+    t_fwd = time.perf_counter() - t0
+    bins = binning.bin_grid(field.shape, box, edges)
+    t0 = time.perf_counter()
+    g0 = ideal.shell_maps(D, bins, nb, which=[nb // 2])
+    t_shell = time.perf_counter() - t0
+    del D
+    slab = max(1, min(field.shape[0], int(field.shape[0] * min(1.0, 2.0e6 / N * 8))))
+    rng = np.random.Generator(np.random.PCG64(1))
+    gs = rng.standard_normal((nb, slab) + field.shape[1:])
+    t0 = time.perf_counter()
+    ideal.triple_sums(gs)
+    t_tri = (time.perf_counter() - t0) * (field.shape[0] / slab)
+    del g0, gs
+    per = t_fwd + nb * t_shell + t_tri
+    return {"value": 1.0 / per, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"FP64 oracle, 1 forward FFT + 1 of {nb} shell maps + triple sums of {nb} maps over "
+                      f"{slab}/{field.shape[0]} slabs, scaled to one {field.shape[0]}^3 estimate "
+                      f"(t_fwd {t_fwd:.2f}s, t_shell {t_shell:.2f}s, t_triple {t_tri:.2f}s)"}
+
+
+def run_reference(args) -> None:
+    """--impl reference: the FP64 CPU oracle on the same workload, each step a bounded sample."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2404_07249_gb300 import synth
+    w, edges = _workload(args.config)
+    field = synth.workload_field(args.config, 0)
+    vals = []
+    last = None
+    for i in range(args.warmup + args.steps):
+        r = cpu_baseline(args.config, field, edges, w.box)
+        if i >= args.warmup:
+            vals.append(r["value"])
+        last = r
+    v = float(np.mean(vals))
+    cb = dict(last)
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "grid": list(w.grid), "box": w.box, "n_kbins": len(edges) - 1,
+                       "statistics": "B_abc(all closed) + P_ell(0,2)"},
+            "cpu_baseline": cb, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="fp32", choices=["split", "fp32", "fp64"])
+    ap.add_argument("--config", type=int, default=3)
+    ap.add_argument("--fp64-steps", type=int, default=1, help="steps of the FP64 GPU comparator (0 = skip)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_2404_07249_gb300 as pkg
+    from paper_2404_07249_gb300 import synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    w, edges = _workload(args.config)
+    grid, box = w.grid, w.box
+    field = synth.workload_field(args.config, rank)
+    d = torch.from_numpy(field).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    pb = pkg.PolyBin(grid, box, edges, lmax=max(w.lmax, 0), prec=args.prec, stream=stream.cuda_stream)
+    t0 = time.perf_counter()
+    ntrip = pb.num_triplets()            # N_abc (FP64, cached): timed separately
+    t_nabc = time.perf_counter() - t0
+    want_pk = w.pk_edges is not None
+
+    def step(x):
+        return pb.bk_pk(x, True, want_pk)
+
+    for _ in range(args.warmup):
+        step(d)
+    torch.cuda.synchronize(dev)
+
+    # ---- device-resident throughput
+    launches0 = pb.launch_count()
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(d)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    launches = pb.launch_count() - launches0
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * 1000.0 / ms
+
+    # ---- end to end through the C-ABI with host buffers (pinned), H2D copy inside the timed region
+    hfield = torch.from_numpy(field).pin_memory()
+    step(hfield)
+    barrier()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step(hfield)
+    torch.cuda.synchronize(dev)
+    barrier()
+    e2e_ms = (time.perf_counter() - t0) * 1000.0 / args.steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    h2d = field.nbytes
+    d2h = ntrip * 8 + (3 * (len(edges) - 1) * 8 if want_pk else 0)
+
+    # ---- per-stage device time (separate instrumented pass of the same steps)
+    pb.set_profiling(True)
+    pb.stage_times(reset=True)
+    for _ in range(args.steps):
+        step(d)
+    st = pb.stage_times(reset=True)
+    pb.set_profiling(False)
+    stage_ms = {k: v[0] / max(v[1], 1) for k, v in st.items()}
+
+    peaks, peak_src = _peaks()
+    N = float(np.prod(grid))
+    nb = len(edges) - 1
+    # dominant kernel: the triplet contraction.  Algorithmic work: 2 flops per closed triplet per cell.
+    algo_flops = 2.0 * ntrip * N
+    t_con = stage_ms["contract"] / 1000.0
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    if args.prec == "split":
+        peak_tf = float(peaks["bf16_tflops_sustained"]) / 2.0        # TF32 dense = bf16 / 2 (nominal ratio)
+        roof = {"bound": "tensor", "unit": "TFLOP/s", "peak": peak_tf,
+                "peak_source": f"{peak_src} bf16 sustained x 1/2 (TF32/bf16 nominal ratio)"}
+    else:
+        alu = 152 * 128 * 2 * sm_max * 1e6 / 1e12 if args.prec == "fp32" else 152 * 2 * 2 * sm_max * 1e6 / 1e12
+        roof = {"bound": "alu", "unit": "TFLOP/s", "peak": alu,
+                "peak_source": ("152 SMs x 128 FP32 lanes x 2 flop x max SM clock" if args.prec == "fp32"
+                                else "152 SMs x 2 FP64 FMA/clk x 2 flop x max SM clock")}
+    roof["achieved"] = algo_flops / t_con / 1e12 if t_con > 0 else None
+    roof["frac"] = roof["achieved"] / roof["peak"] if roof["achieved"] else None
+    roof["traffic"] = None
+    roof["kernel"] = "k_contract (triplet contraction, a3)"
+    roof["algorithmic"] = f"2 x {ntrip} closed triplets x {int(N)} cells = {algo_flops:.3e} flop per launch"
+    roof["stage_ms"] = stage_ms
+    hbm = float(peaks["hbm_gbs"])
+    roof["hbm_gbs_of_stages"] = {
+        "forward": (N * 4 + 0) / (stage_ms["forward"] / 1e3) / 1e9 if stage_ms["forward"] else None,
+        "shells_write_g": (nb * N * 4) / (stage_ms["shells"] / 1e3) / 1e9 if stage_ms["shells"] else None,
+        "contract_read_g": (nb * N * 4) / (t_con) / 1e9 if t_con else None,
+        "hbm_peak_gbs": hbm}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"split": "tf32x3", "fp32": "f32", "fp64": "f64"}[args.prec],
+            "data": "synthetic",
+            "config": {"workload": w.name, "grid": list(grid), "box": box, "n_kbins": nb, "n_triplets": ntrip,
+                       "statistics": "B_abc(all closed) + P_ell(0,2)", "precision_mode": args.prec,
+                       "l2": "inputs 537 MB > L2 (no flush needed)", "nabc_init_s": t_nabc},
+            "e2e": {"value": world * 1000.0 / e2e_ms, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches, "clocks": clocks, "roofline": roof}
+
+    # ---- FP64 GPU comparator (the plain double-precision path)
+    if args.fp64_steps > 0 and args.prec != "fp64":
+        pb64 = pkg.PolyBin(grid, box, edges, lmax=max(w.lmax, 0), prec="fp64", stream=stream.cuda_stream)
+        pb64.num_triplets()
+        pb64.bk_pk(d, True, want_pk)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(args.fp64_steps):
+            B64, _ = pb64.bk_pk(d, True, want_pk)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms64 = e0.elapsed_time(e1) / args.fp64_steps
+        B32, _ = step(d)
+        rel = np.abs(B32[0] - B64[0]) / np.abs(B64[0])
+        line["fp64_gpu_path"] = {"value": world * 1000.0 / ms64, "unit": UNIT, "ms_per_step": ms64,
+                                 "speedup_of_value": (world * 1000.0 / ms) / (world * 1000.0 / ms64),
+                                 "B_rel_err_vs_fp64_gpu": {"max": float(rel.max()), "median": float(np.median(rel)),
+                                                           "frac_le_1e-6": float(np.mean(rel <= 1e-6))}}
+        pb64.close()
+
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(args.config, field, edges, box)
+    pb.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,142 @@
+/* libpolybin -- binned power spectrum and bispectrum estimators on a periodic 3D grid, one GB300 (sm_103a).
+ *
+ * Method: PolyBin3D, O. H. E. Philcox & T. Floss, arXiv 2404.07249.  The library computes, with hand-written
+ * CUDA kernels:
+ *   - the shell-filtered maps g_b = IFT[Theta_b FT[delta]] (Sec. 4.3.1, eq. g-ell-def, global line of sight);
+ *   - the triplet sums S_abc = sum_x g_a g_b g_c and their normalisation N_abc from unit fields
+ *     (eqs. beta-def, N-ell-def) and the ideal bispectrum (Sec. 4.4.1, eqs. bk-num-ideal, bk-fish-ideal2);
+ *   - the Legendre-weighted power spectrum multipoles along the last grid axis (Sec. 3.4.1, eq. pk-limit,
+ *     eq. fish-ideal-continuous).
+ *
+ * Conventions shared by every entry point:
+ *   - Grids are C-order arrays [N0][N1][N2]; the line of sight is the last (fastest) axis.  Every N_i must be
+ *     even and have no prime factor other than 2, 3, 5, with N_i <= 1024.  The box is cubic (one side L for all
+ *     axes); boxsize[0..2] must be equal.
+ *   - k-bins are half-open [e_b, e_{b+1}) in |k| (h/Mpc), k = 0 never binned; 1 <= n_kbins <= 64, ascending edges.
+ *   - Inputs are float32 real fields.  A field pointer may be device memory (read in place) or host memory
+ *     (pinned or pageable; copied to the device inside the call).  Outputs are float64 on the host.
+ *   - The caller owns every input and output buffer; the context owns its device workspace, plans and caches.
+ *   - All work runs on the CUDA stream given to polybin_init (borrowed, not owned); each call synchronises that
+ *     stream before returning, so outputs are valid on return.  A context must not be used by two host threads
+ *     at once.
+ *   - Every int-returning function returns a polybin_status; on failure polybin_last_error() describes it.
+ *     Nothing throws across this interface.
+ */
+#ifndef POLYBIN_H
+#define POLYBIN_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct polybin_ctx polybin_ctx;
+
+typedef enum {
+    POLYBIN_OK = 0,
+    POLYBIN_EINVAL = -1,    /* bad argument: null pointer, unsupported grid, bad edges, ... */
+    POLYBIN_ENOMEM = -2,    /* device or host allocation failed */
+    POLYBIN_ECUDA = -3,     /* a CUDA call or kernel launch failed */
+    POLYBIN_ETIMEOUT = -4,  /* a bounded device-side wait gave up */
+    POLYBIN_ENOTREADY = -5, /* a prerequisite (e.g. a Fisher matrix) has not been computed */
+    POLYBIN_ETOL = -6       /* a self-check exceeded its tolerance */
+} polybin_status;
+
+typedef enum {
+    POLYBIN_FP64 = 0,         /* FP64 FFTs and FP64 contraction: the plain double-precision GPU path        */
+    POLYBIN_FP32 = 1,         /* FP32 FFTs, FP32 SIMT contraction with FP64 flushes and FP64 cross-CTA sums  */
+    POLYBIN_SPLIT_TF32X3 = 2  /* FP32 FFTs, tensor-core contraction with 3-term split TF32 products          */
+} polybin_prec;
+
+/* Create a context for one grid and one set of k-bins.
+ * grid[3]      : N0, N1, N2 (see conventions).
+ * boxsize[3]   : box side in Mpc/h (all three equal).
+ * k_edges      : n_kbins + 1 ascending edges in h/Mpc (host memory, copied).
+ * l_max        : largest even Legendre order of the power spectrum (0, 2 or 4).
+ * prec         : a polybin_prec value.
+ * cuda_stream  : cudaStream_t to run on (NULL = legacy default stream).
+ * On success *out receives the context (destroy with polybin_destroy); on failure *out is NULL and
+ * polybin_last_error(NULL) describes the error. */
+int polybin_init(polybin_ctx** out, const int grid[3], const double boxsize[3], const double* k_edges,
+                 int n_kbins, int l_max, int prec, void* cuda_stream);
+
+/* Release the context and all its device memory.  NULL is accepted. */
+void polybin_destroy(polybin_ctx* ctx);
+
+/* Message of the last failure on ctx (or of the last failed polybin_init on this thread when ctx is NULL).
+ * The string is owned by the library and valid until the next call on the same context. */
+const char* polybin_last_error(const polybin_ctx* ctx);
+
+/* ---- bispectrum (Sec. 4.4.1) ------------------------------------------------------------------------------ */
+
+/* Number of closed triplets a <= b <= c (N_abc > 0).  The first call computes N_abc on the GPU in FP64
+ * (eq. N-ell-def via unit-field shell maps) and caches it in the context. */
+int polybin_num_triplets(polybin_ctx* ctx, int* n);
+
+/* The closed triplets in lexicographic (a, b, c) order (abc: [n][3] ints, host) and, if n_abc is not NULL,
+ * their closed-triangle counts N_abc = N^2 T_abc (host, [n] doubles; exact integers). */
+int polybin_get_triplets(polybin_ctx* ctx, int* abc, double* n_abc);
+
+/* Ideal bispectrum monopole of `batch` fields delta ([batch][N0][N1][N2] float32, device or host):
+ * B_abc = (V^2 / N^3) S_abc / T_abc in (Mpc/h)^6 for every closed triplet (Sec. 4.4.1: b_num = S / Delta and
+ * F = N_abc / (N Delta) in pixel units, so Delta cancels).  bk_out: host [batch][n_triplets]. */
+int polybin_bk_ideal(polybin_ctx* ctx, const float* delta, int batch, double* bk_out);
+
+/* ---- power spectrum (Sec. 3.4.1) ------------------------------------------------------------------------- */
+
+/* Ideal P_ell (ell = 0, 2, .., l_max) with the continuous-limit Fisher normalisation (eq. fish-ideal-continuous):
+ * P_ell(b) = (2 ell + 1) (V / N^2) sum_{k in b} L_ell(mu) |D(k)|^2 / N_b, mu = k_z / |k|, D = DFT(delta).
+ * pk_out: host [batch][l_max/2 + 1][n_kbins] in (Mpc/h)^3. */
+int polybin_pk(polybin_ctx* ctx, const float* delta, int batch, double* pk_out);
+
+/* Same numerator with the discrete ideal Fisher of eq. pk-limit, F_{ell ell'}(b) = (1/2) sum_{k in b} L_ell L_ell',
+ * solved per bin (couples the multipoles through grid discreteness).  Same output layout as polybin_pk. */
+int polybin_pk_discrete(polybin_ctx* ctx, const float* delta, int batch, double* pk_out);
+
+/* Mode counts N_b of the full k-grid (host [n_kbins] doubles). */
+int polybin_mode_counts(const polybin_ctx* ctx, double* counts);
+
+/* Both statistics of the same fields from one forward transform: bk_out as polybin_bk_ideal, pk_out as
+ * polybin_pk (continuous normalisation).  Either output may be NULL to skip that statistic. */
+int polybin_bk_pk_ideal(polybin_ctx* ctx, const float* delta, int batch, double* bk_out, double* pk_out);
+
+/* ---- instrumentation -------------------------------------------------------------------------------------- */
+
+/* Enable (on != 0) or disable per-stage timing.  When enabled, each pipeline stage is bracketed by CUDA events on
+ * the context stream and the host waits for the closing event, so stages are timed exactly but back to back
+ * calls lose their overlap; leave it off for throughput measurements. */
+int polybin_set_profiling(polybin_ctx* ctx, int on);
+
+/* Accumulated device milliseconds and call counts of the stages since the last reset (reset != 0 clears them
+ * after reading).  Stage order: 0 forward transform (a1), 1 shell filter + inverse transforms (a2),
+ * 2 triplet contraction (a3), 3 P_ell binning (a4).  ms and calls: host arrays of 4 (calls may be NULL). */
+int polybin_get_stage_times(polybin_ctx* ctx, double* ms, long long* calls, int reset);
+
+/* Number of kernels this context has launched so far. */
+int polybin_launch_count(const polybin_ctx* ctx, long long* n);
+
+/* ---- individual steps, for testing and composition (device pointers only) --------------------------------- */
+
+/* Dimensions [Bx][By][Bz] of the pruned half-spectrum box: all wave numbers n with |n_x|, |n_y| <= m and
+ * 0 <= n_z <= m, where m is the largest |n_i| of any binned mode (full axis when 2m + 1 > N_i). */
+int polybin_spectrum_shape(const polybin_ctx* ctx, int dims[3], int lo[3]);
+
+/* Step a1: forward real-to-complex DFT of one field, pruned to the box.  delta: device float32 [N0][N1][N2];
+ * spec_out: device [Bx][By][Bz] complex (interleaved re, im) of float (FP32 modes) or double (FP64 mode);
+ * element (ix, iy, iz) holds D(n = (lo[0] + ix, lo[1] + iy, lo[2] + iz)) = sum_x e^{-i k.x} delta(x). */
+int polybin_forward(polybin_ctx* ctx, const float* delta, void* spec_out);
+
+/* Step a2: shell maps g_b(x) = IFT[Theta_b D](x) (with the 1/N of the inverse DFT) for every bin, from a box
+ * spectrum laid out as polybin_forward writes it.  g_out: device [n_kbins][N0][N1][N2] float (FP32 modes) or
+ * double (FP64 mode). */
+int polybin_shell_maps(polybin_ctx* ctx, const void* spec, void* g_out);
+
+/* Step a3: M[p][i] = sum_x g_{j_p}(x) g_{k_p}(x) h_i(x) for all pairs p = (j <= k) in lexicographic order and all
+ * i.  g: device [n_g][N] maps, h: device [n_h][N] maps or NULL (h = g, n_h = n_g); element type as for
+ * polybin_shell_maps.  m_out: host [n_g (n_g + 1) / 2][n_h] doubles.  n_g, n_h <= 64. */
+int polybin_contract(polybin_ctx* ctx, const void* g, int n_g, const void* h, int n_h, double* m_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* POLYBIN_H */

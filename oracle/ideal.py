@@ -15,13 +15,13 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import binning
+from . import _fft, binning
 
 
 def forward(delta: np.ndarray) -> np.ndarray:
     """D(k) = sum_x e^{-i k.x} delta(x): the discrete form of the paper's FT (Sec. 1, Fourier conventions).
     The input is promoted to float64 exactly."""
-    return np.fft.fftn(np.asarray(delta, dtype=np.float64))
+    return _fft.fftn(np.asarray(delta, dtype=np.float64))
 
 
 def shell_maps(D: np.ndarray, bins: np.ndarray, nb: int, which=None) -> np.ndarray:
@@ -31,7 +31,7 @@ def shell_maps(D: np.ndarray, bins: np.ndarray, nb: int, which=None) -> np.ndarr
     idx = list(range(nb)) if which is None else list(which)
     out = np.empty((len(idx),) + D.shape, dtype=np.float64)
     for j, b in enumerate(idx):
-        out[j] = np.fft.ifftn(np.where(bins == b, D, 0.0)).real
+        out[j] = _fft.ifftn(np.where(bins == b, D, 0.0)).real
     return out
 
 

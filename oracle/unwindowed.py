@@ -13,7 +13,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import binning
+from . import _fft, binning
 from .ideal import shell_maps
 from .philox import gaussian_draw
 
@@ -43,7 +43,7 @@ def pk_numerator(d, w, bins, mu2, nb, ells) -> np.ndarray:
     """p_num_alpha = (1/2) int_k Theta_b L_ell |FT[S^-1 d]|^2 (Sec. 3.3.1, global line of sight),
     pixel units: (1/2)(1/N) sum_{k in b} L_ell |fftn(w d)|^2.  Shape [len(ells), nb]."""
     N = d.size
-    U = np.fft.fftn(np.asarray(w, dtype=np.float64) * np.asarray(d, dtype=np.float64))
+    U = _fft.fftn(np.asarray(w, dtype=np.float64) * np.asarray(d, dtype=np.float64))
     pw = np.abs(U) ** 2
     sel = bins >= 0
     out = np.zeros((len(ells), nb))
@@ -63,15 +63,15 @@ def pk_fisher_draw(a, n, w, bins, mu2, nb, ells) -> np.ndarray:
     with s = w n and A = I."""
     N = a.size
     s = np.asarray(w, dtype=np.float64) * np.asarray(n, dtype=np.float64)
-    A = np.fft.fftn(a)
-    SA = np.fft.fftn(s * a)
+    A = _fft.fftn(a)
+    SA = _fft.fftn(s * a)
     alphas = alpha_list_p(nb, ells)
     Lw = {ell: binning.legendre(ell, mu2) for ell in ells}
     Y = np.stack([np.where(bins == b, Lw[ell] * A, 0.0).ravel() for ell, b in alphas])
     X = np.empty_like(Y)
     for i, (ell, b) in enumerate(alphas):
-        q = np.fft.ifftn(np.where(bins == b, Lw[ell] * SA, 0.0)).real
-        X[i] = np.fft.fftn(s * q).ravel()
+        q = _fft.ifftn(np.where(bins == b, Lw[ell] * SA, 0.0)).real
+        X[i] = _fft.fftn(s * q).ravel()
     return 0.5 * (np.conj(X) @ Y.T).real / N
 
 
@@ -96,13 +96,13 @@ def bk_numerator(d, w, mocks, bins, nb, trip) -> dict:
         lin_abc   = < sum_x g_a[u] g_b[v] g_c[v] + g_a[v] g_b[u] g_c[v] + g_a[v] g_b[v] g_c[u] >_Delta.
     """
     u = np.asarray(w, dtype=np.float64) * np.asarray(d, dtype=np.float64)
-    gu = shell_maps(np.fft.fftn(u), bins, nb)
+    gu = shell_maps(_fft.fftn(u), bins, nb)
     G = gu.reshape(nb, -1)
     S = np.array([np.dot(G[a] * G[b], G[c]) for a, b, c in trip])
     lin = np.zeros(len(trip))
     for mock in mocks:
         v = np.asarray(w, dtype=np.float64) * np.asarray(mock, dtype=np.float64)
-        H = shell_maps(np.fft.fftn(v), bins, nb).reshape(nb, -1)
+        H = shell_maps(_fft.fftn(v), bins, nb).reshape(nb, -1)
         lin += np.array([np.dot(G[a] * H[b], H[c]) + np.dot(H[a] * G[b], H[c]) + np.dot(H[a] * H[b], G[c])
                          for a, b, c in trip])
     if len(mocks):
@@ -118,20 +118,20 @@ def q_maps(u, bins, nb, trip) -> np.ndarray:
 
     with g = shell_maps(FT[u]); both complex conjugates of eq. Q-bis-global cancel for real u and are
     dropped.  Each pair product is transformed once.  Shape [len(trip), N]."""
-    g = shell_maps(np.fft.fftn(np.asarray(u, dtype=np.float64)), bins, nb)
+    g = shell_maps(_fft.fftn(np.asarray(u, dtype=np.float64)), bins, nb)
     pair_ft = {}
 
     def P(i, j):
         key = (min(i, j), max(i, j))
         if key not in pair_ft:
-            pair_ft[key] = np.fft.fftn(g[key[0]] * g[key[1]])
+            pair_ft[key] = _fft.fftn(g[key[0]] * g[key[1]])
         return pair_ft[key]
 
     out = np.empty((len(trip), u.size))
     for t, (a, b, c) in enumerate(trip):
         spec = np.where(bins == c, P(a, b), 0.0) + np.where(bins == a, P(b, c), 0.0) \
             + np.where(bins == b, P(a, c), 0.0)
-        out[t] = (2.0 / binning.degeneracy(a, b, c)) * np.fft.ifftn(spec).real.ravel()
+        out[t] = (2.0 / binning.degeneracy(a, b, c)) * _fft.ifftn(spec).real.ravel()
     return out
 
 

@@ -1,0 +1,229 @@
+"""Python binding of libpolybin (argument marshalling only; all compute runs in the CUDA library).
+
+The shared library is built in-tree by ``paper_2404_07249_gb300.build.build()`` (nvcc, sm_103a) into
+``paper_2404_07249_gb300/_build/libpolybin.so``.  There is no CPU fallback: if the library is missing,
+``load()`` raises.
+
+Device arrays are ``torch`` CUDA tensors (torch is used only for device memory and streams); host arrays are
+numpy.  Entry points mirror the C-ABI of ``include/polybin.h``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpolybin.so")
+
+FP64, FP32, SPLIT_TF32X3 = 0, 1, 2
+_PREC = {"fp64": FP64, "fp32": FP32, "split_tf32x3": SPLIT_TF32X3, "split": SPLIT_TF32X3}
+
+_lib = None
+
+_SIGS = {
+    "polybin_init": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                                    ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
+    "polybin_destroy": (None, [ctypes.c_void_p]),
+    "polybin_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "polybin_num_triplets": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
+    "polybin_get_triplets": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "polybin_bk_ideal": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "polybin_pk": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "polybin_pk_discrete": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "polybin_mode_counts": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "polybin_spectrum_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "polybin_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "polybin_shell_maps": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "polybin_contract": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                        ctypes.c_void_p]),
+    "polybin_bk_pk_ideal": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                           ctypes.c_void_p]),
+    "polybin_set_profiling": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "polybin_get_stage_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "polybin_launch_count": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong)]),
+}
+
+STAGES = ("forward", "shells", "contract", "pk_bin")
+
+
+class PolybinError(RuntimeError):
+    pass
+
+
+def load(path: str = LIB_PATH):
+    """Load libpolybin (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise PolybinError(f"libpolybin is not built ({path} missing); run paper_2404_07249_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(x):
+    """Raw address of a torch tensor (device or host) or numpy array."""
+    if hasattr(x, "data_ptr"):
+        return ctypes.c_void_p(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        return ctypes.c_void_p(x.ctypes.data)
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+def _f32(x):
+    """float32, C-contiguous view (torch tensor or numpy array)."""
+    if hasattr(x, "data_ptr"):
+        import torch
+        if x.dtype != torch.float32 or not x.is_contiguous():
+            x = x.to(torch.float32).contiguous()
+        return x
+    return np.ascontiguousarray(x, dtype=np.float32)
+
+
+class PolyBin:
+    """One grid + one set of k-bins on one GPU (wraps a polybin_ctx)."""
+
+    def __init__(self, grid, boxsize, k_edges, lmax: int = 0, prec="fp32", stream=None):
+        lib = load()
+        self.lib = lib
+        self.grid = tuple(int(g) for g in grid)
+        box = boxsize if np.ndim(boxsize) else (boxsize,) * 3
+        self.box = tuple(float(b) for b in box)
+        self.edges = np.ascontiguousarray(k_edges, dtype=np.float64)
+        self.nb = len(self.edges) - 1
+        self.lmax = int(lmax)
+        self.prec = _PREC[prec] if isinstance(prec, str) else int(prec)
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        self.stream = stream
+        ctx = ctypes.c_void_p()
+        g = (ctypes.c_int * 3)(*self.grid)
+        b = (ctypes.c_double * 3)(*self.box)
+        e = self.edges.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        rc = lib.polybin_init(ctypes.byref(ctx), g, b, e, self.nb, self.lmax, self.prec, ctypes.c_void_p(stream))
+        if rc != 0:
+            raise PolybinError(f"polybin_init: {rc}: {lib.polybin_last_error(None).decode()}")
+        self.ctx = ctx
+        self.ncell = int(np.prod(self.grid))
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.polybin_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, what):
+        if rc != 0:
+            raise PolybinError(f"{what}: {rc}: {self.lib.polybin_last_error(self.ctx).decode()}")
+
+    # ---- bispectrum
+    def num_triplets(self) -> int:
+        n = ctypes.c_int()
+        self._check(self.lib.polybin_num_triplets(self.ctx, ctypes.byref(n)), "polybin_num_triplets")
+        return n.value
+
+    def triplets(self):
+        n = self.num_triplets()
+        abc = np.zeros((n, 3), dtype=np.int32)
+        cnt = np.zeros(n, dtype=np.float64)
+        self._check(self.lib.polybin_get_triplets(self.ctx, _ptr(abc), _ptr(cnt)), "polybin_get_triplets")
+        return abc, cnt
+
+    def bk_ideal(self, delta) -> np.ndarray:
+        delta = _f32(delta)
+        batch = delta.shape[0] if delta.ndim == 4 else 1
+        out = np.zeros((batch, self.num_triplets()), dtype=np.float64)
+        self._check(self.lib.polybin_bk_ideal(self.ctx, _ptr(delta), batch, _ptr(out)), "polybin_bk_ideal")
+        return out
+
+    # ---- power spectrum
+    def pk(self, delta, discrete: bool = False) -> np.ndarray:
+        delta = _f32(delta)
+        batch = delta.shape[0] if delta.ndim == 4 else 1
+        out = np.zeros((batch, self.lmax // 2 + 1, self.nb), dtype=np.float64)
+        fn = self.lib.polybin_pk_discrete if discrete else self.lib.polybin_pk
+        self._check(fn(self.ctx, _ptr(delta), batch, _ptr(out)), "polybin_pk")
+        return out
+
+    def bk_pk(self, delta, want_bk: bool = True, want_pk: bool = True):
+        """(B [batch][n_triplets] or None, P [batch][n_ell][nb] or None) from one forward transform per field."""
+        delta = _f32(delta)
+        batch = delta.shape[0] if delta.ndim == 4 else 1
+        B = np.zeros((batch, self.num_triplets()), dtype=np.float64) if want_bk else None
+        P = np.zeros((batch, self.lmax // 2 + 1, self.nb), dtype=np.float64) if want_pk else None
+        self._check(self.lib.polybin_bk_pk_ideal(self.ctx, _ptr(delta), batch, None if B is None else _ptr(B),
+                                                 None if P is None else _ptr(P)), "polybin_bk_pk_ideal")
+        return B, P
+
+    def set_profiling(self, on: bool):
+        self._check(self.lib.polybin_set_profiling(self.ctx, int(bool(on))), "polybin_set_profiling")
+
+    def stage_times(self, reset: bool = True) -> dict:
+        ms = np.zeros(4, dtype=np.float64)
+        calls = np.zeros(4, dtype=np.int64)
+        self._check(self.lib.polybin_get_stage_times(self.ctx, _ptr(ms), _ptr(calls), int(reset)),
+                    "polybin_get_stage_times")
+        return {n: (float(ms[i]), int(calls[i])) for i, n in enumerate(STAGES)}
+
+    def launch_count(self) -> int:
+        n = ctypes.c_longlong()
+        self._check(self.lib.polybin_launch_count(self.ctx, ctypes.byref(n)), "polybin_launch_count")
+        return n.value
+
+    def mode_counts(self) -> np.ndarray:
+        out = np.zeros(self.nb, dtype=np.float64)
+        self._check(self.lib.polybin_mode_counts(self.ctx, _ptr(out)), "polybin_mode_counts")
+        return out
+
+    # ---- steps
+    def spectrum_shape(self):
+        dims = np.zeros(3, dtype=np.int32)
+        lo = np.zeros(3, dtype=np.int32)
+        self._check(self.lib.polybin_spectrum_shape(self.ctx, _ptr(dims), _ptr(lo)), "polybin_spectrum_shape")
+        return tuple(int(d) for d in dims), tuple(int(v) for v in lo)
+
+    def _real_dtype(self):
+        import torch
+        return torch.float64 if self.prec == FP64 else torch.float32
+
+    def forward(self, delta_dev):
+        import torch
+        dims, _ = self.spectrum_shape()
+        cdt = torch.complex128 if self.prec == FP64 else torch.complex64
+        out = torch.empty(dims, dtype=cdt, device=delta_dev.device)
+        d = _f32(delta_dev)
+        self._check(self.lib.polybin_forward(self.ctx, _ptr(d), _ptr(out)), "polybin_forward")
+        return out
+
+    def shell_maps(self, spec_dev):
+        import torch
+        out = torch.empty((self.nb,) + self.grid, dtype=self._real_dtype(), device=spec_dev.device)
+        self._check(self.lib.polybin_shell_maps(self.ctx, _ptr(spec_dev), _ptr(out)), "polybin_shell_maps")
+        return out
+
+    def contract(self, g_dev, h_dev=None) -> np.ndarray:
+        ng = g_dev.shape[0]
+        nh = ng if h_dev is None else h_dev.shape[0]
+        out = np.zeros((ng * (ng + 1) // 2, nh), dtype=np.float64)
+        self._check(self.lib.polybin_contract(self.ctx, _ptr(g_dev), ng, None if h_dev is None else _ptr(h_dev), nh,
+                                              _ptr(out)), "polybin_contract")
+        return out
+
+
+def pair_list(n: int):
+    """Pairs (j <= k) in the lexicographic order used by ``PolyBin.contract``."""
+    return [(j, k) for j in range(n) for k in range(j, n)]

@@ -1,0 +1,366 @@
+// Mixed-radix (2, 3, 4, 5, 8) Stockham FFT staged in shared memory, and the pass kernels of the
+// pruned 3D real transforms used by the estimators:
+//   forward  (R2C):  z-pass on pairs of real lines -> y-pass -> x-pass, keeping only the box of wave
+//                    numbers that any k-bin can reach (|n_i| <= m);
+//   inverse  (C2R):  x-pass that applies the shell filter Theta_b on load -> y-pass -> z-pass on pairs
+//                    of Hermitian half-lines, per bin b over that bin's own bounding box.
+// A line of length n lives in shared memory as element (l, e) at l + e * ES, so that consecutive
+// threads touch consecutive lines (conflict-free) in every radix pass.
+#pragma once
+#include "common.cuh"
+
+namespace pb {
+
+constexpr int kMaxPasses = 12;
+constexpr int kMaxItems = 64;
+
+struct FftPlan {
+    int n;
+    int nr;
+    int radix[kMaxPasses];
+};
+
+// Factor n into radices 8, 4, 2, 3, 5 (largest power-of-two radices first).  False if n has another
+// prime factor or is too long for shared-memory staging.
+inline bool make_plan(int n, FftPlan& p) {
+    p.n = n;
+    p.nr = 0;
+    if (n < 2 || n > 1024) return false;
+    int m = n;
+    while (m % 8 == 0) { p.radix[p.nr++] = 8; m /= 8; }
+    while (m % 4 == 0) { p.radix[p.nr++] = 4; m /= 4; }
+    while (m % 2 == 0) { p.radix[p.nr++] = 2; m /= 2; }
+    while (m % 3 == 0) { p.radix[p.nr++] = 3; m /= 3; }
+    while (m % 5 == 0) { p.radix[p.nr++] = 5; m /= 5; }
+    return m == 1 && p.nr <= kMaxPasses;
+}
+
+// In-register DFT of length R (R in {2,3,4,5,8}); DIR = -1 forward (e^{-2 pi i}), +1 inverse.
+template <typename T, int DIR>
+__device__ __forceinline__ void dft4(C<T>& a0, C<T>& a1, C<T>& a2, C<T>& a3) {
+    C<T> t0 = add<T>(a0, a2), t1 = sub<T>(a0, a2), t2 = add<T>(a1, a3), t3 = sub<T>(a1, a3);
+    // w = e^{DIR 2 pi i / 4} = DIR * i
+    C<T> wt3 = muli<T>(t3, DIR);
+    a0 = add<T>(t0, t2);
+    a2 = sub<T>(t0, t2);
+    a1 = add<T>(t1, wt3);
+    a3 = sub<T>(t1, wt3);
+}
+
+template <typename T, int DIR>
+__device__ __forceinline__ void dft(C<T>* v, int R) {
+    const T h = T(0.70710678118654752440);  // sqrt(1/2)
+    switch (R) {
+        case 2: {
+            C<T> a = v[0], b = v[1];
+            v[0] = add<T>(a, b);
+            v[1] = sub<T>(a, b);
+        } break;
+        case 4: dft4<T, DIR>(v[0], v[1], v[2], v[3]); break;
+        case 8: {
+            C<T> e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+            C<T> o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+            dft4<T, DIR>(e0, e1, e2, e3);
+            dft4<T, DIR>(o0, o1, o2, o3);
+            // o_q *= w8^q, w8 = e^{DIR 2 pi i / 8} = h (1 + DIR i)
+            o1 = mk<T>(h * (o1.x - DIR * o1.y), h * (o1.y + DIR * o1.x));
+            o2 = muli<T>(o2, DIR);
+            o3 = mk<T>(h * (-o3.x - DIR * o3.y), h * (-o3.y + DIR * o3.x));
+            v[0] = add<T>(e0, o0); v[4] = sub<T>(e0, o0);
+            v[1] = add<T>(e1, o1); v[5] = sub<T>(e1, o1);
+            v[2] = add<T>(e2, o2); v[6] = sub<T>(e2, o2);
+            v[3] = add<T>(e3, o3); v[7] = sub<T>(e3, o3);
+        } break;
+        case 3: {
+            const T s3 = T(0.86602540378443864676);  // sin(2 pi / 3)
+            C<T> s = add<T>(v[1], v[2]), d = sub<T>(v[1], v[2]);
+            C<T> t = mk<T>(v[0].x - T(0.5) * s.x, v[0].y - T(0.5) * s.y);
+            C<T> id = muli<T>(d, DIR);
+            v[0] = add<T>(v[0], s);
+            v[1] = mk<T>(t.x + s3 * id.x, t.y + s3 * id.y);
+            v[2] = mk<T>(t.x - s3 * id.x, t.y - s3 * id.y);
+        } break;
+        case 5: {
+            const T c1 = T(0.30901699437494742410), c2 = T(-0.80901699437494742410);   // cos(2pi/5), cos(4pi/5)
+            const T s1 = T(0.95105651629515357212), s2 = T(0.58778525229247312917);    // sin(2pi/5), sin(4pi/5)
+            C<T> a0 = v[0];
+            C<T> p1 = add<T>(v[1], v[4]), m1 = sub<T>(v[1], v[4]);
+            C<T> p2 = add<T>(v[2], v[3]), m2 = sub<T>(v[2], v[3]);
+            C<T> r1 = mk<T>(a0.x + c1 * p1.x + c2 * p2.x, a0.y + c1 * p1.y + c2 * p2.y);
+            C<T> r2 = mk<T>(a0.x + c2 * p1.x + c1 * p2.x, a0.y + c2 * p1.y + c1 * p2.y);
+            C<T> q1 = muli<T>(mk<T>(s1 * m1.x + s2 * m2.x, s1 * m1.y + s2 * m2.y), DIR);
+            C<T> q2 = muli<T>(mk<T>(s2 * m1.x - s1 * m2.x, s2 * m1.y - s1 * m2.y), DIR);
+            v[0] = add<T>(a0, add<T>(p1, p2));
+            v[1] = add<T>(r1, q1);
+            v[4] = sub<T>(r1, q1);
+            v[2] = add<T>(r2, q2);
+            v[3] = sub<T>(r2, q2);
+        } break;
+        default: break;
+    }
+}
+
+// Stockham autosort FFT of L lines (element (l, e) at l + e * ES) using a ping-pong buffer pair.
+// tw[m] = e^{-2 pi i m / n}.  Returns the buffer holding the result (natural order).
+// Pass with radix R after Ns = product of earlier radices: butterfly j (0 <= j < n/R), k = j mod Ns,
+// reads x[j + r n/R] (r < R), multiplies by w^{r k n/(Ns R)}, takes the R-point DFT and writes
+// output q to position (j - k) R + k + q Ns.
+template <typename T, int DIR>
+__device__ C<T>* fft_lines(C<T>* src, C<T>* dst, int L, int ES, const FftPlan& p, const C<T>* __restrict__ tw,
+                           int tid, int nthr) {
+    const int n = p.n;
+    int Ns = 1;
+    for (int pass = 0; pass < p.nr; ++pass) {
+        const int R = p.radix[pass];
+        const int nbf = n / R;
+        const int tstride = n / (Ns * R);
+        const int total = nbf * L;
+        for (int w = tid; w < total; w += nthr) {
+            const int l = w % L;
+            const int j = w / L;
+            const int k = j % Ns;
+            C<T> v[8];
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+                if (r < R) v[r] = src[l + (j + r * nbf) * ES];
+            if (Ns > 1) {
+#pragma unroll
+                for (int r = 1; r < 8; ++r)
+                    if (r < R) {
+                        C<T> t = tw[r * k * tstride];
+                        v[r] = DIR < 0 ? mul<T>(v[r], t) : mulc<T>(v[r], t);
+                    }
+            }
+            dft<T, DIR>(v, R);
+            const int base = (j - k) * R + k;
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (q < R) dst[l + (base + q * Ns) * ES] = v[q];
+        }
+        __syncthreads();
+        C<T>* t = src;
+        src = dst;
+        dst = t;
+        Ns *= R;
+    }
+    return src;
+}
+
+// ------------------------------------------------------------------------------------------------
+// z-pass, forward: pairs of real lines (lines 2p, 2p+1 of the flattened (x, y) index) packed as one
+// complex line, transformed, then split into the two Hermitian half-spectra; only kz < kout is stored.
+// Optional pointwise multipliers m1, m2 (same layout as the input) are applied on load.
+template <typename T, typename TIN>
+__global__ void __launch_bounds__(256) k_fwd_z(const TIN* __restrict__ in, const TIN* __restrict__ m1,
+                                               const TIN* __restrict__ m2, C<T>* __restrict__ out, long nlines,
+                                               int kout, FftPlan plan, const C<T>* __restrict__ tw, int LP) {
+    extern __shared__ unsigned char smem_raw[];
+    const int n = plan.n;
+    const int ES = LP + 1;
+    C<T>* b0 = reinterpret_cast<C<T>*>(smem_raw);
+    C<T>* b1 = b0 + (size_t)n * ES;
+    const long line0 = (long)blockIdx.x * 2 * LP;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    T* bs = reinterpret_cast<T*>(b0);
+    for (int idx = tid; idx < 2 * LP * n; idx += nthr) {
+        const int r = idx / n, e = idx - r * n;
+        const long gl = line0 + r;
+        T v = T(0);
+        if (gl < nlines) {
+            const long gi = gl * n + e;
+            v = T(in[gi]);
+            if (m1) v *= T(m1[gi]);
+            if (m2) v *= T(m2[gi]);
+        }
+        bs[2 * ((r >> 1) + e * ES) + (r & 1)] = v;
+    }
+    __syncthreads();
+    C<T>* z = fft_lines<T, -1>(b0, b1, LP, ES, plan, tw, tid, nthr);
+    for (int idx = tid; idx < LP * kout; idx += nthr) {
+        const int l = idx / kout, k = idx - l * kout;
+        const long gl = line0 + 2 * l;
+        if (gl >= nlines) continue;
+        const C<T> zk = z[l + k * ES];
+        const C<T> zm = z[l + ((n - k) % n) * ES];
+        // X1 = (Z[k] + conj Z[n-k]) / 2 ;  X2 = (Z[k] - conj Z[n-k]) / (2i)
+        const C<T> x1 = mk<T>(T(0.5) * (zk.x + zm.x), T(0.5) * (zk.y - zm.y));
+        const C<T> x2 = mk<T>(T(0.5) * (zk.y + zm.y), T(-0.5) * (zk.x - zm.x));
+        out[gl * kout + k] = x1;
+        if (gl + 1 < nlines) out[(gl + 1) * kout + k] = x2;
+    }
+}
+
+// z-pass, inverse (C2R): Hermitian half-lines X (kz < kin, zero above) of lines 2p, 2p+1 are packed as
+// Z = X1 + i X2 over the full axis, inverse-transformed, and the real / imaginary parts written as the two
+// real lines (times scale, times an optional pointwise multiplier).  As in a standard C2R the imaginary
+// parts of the kz = 0 and kz = n/2 coefficients are ignored.
+struct ZInvItem {
+    const void* in;   // C<T>* [nlines][kin]
+    void* out;        // T*    [nlines][n]
+    int kin;
+};
+struct ZInvBatch {
+    ZInvItem it[kMaxItems];
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_inv_z(ZInvBatch batch, long nlines, T scale, const T* __restrict__ mulout,
+                                               FftPlan plan, const C<T>* __restrict__ tw, int LP) {
+    extern __shared__ unsigned char smem_raw[];
+    const ZInvItem item = batch.it[blockIdx.y];
+    const C<T>* __restrict__ in = static_cast<const C<T>*>(item.in);
+    T* __restrict__ out = static_cast<T*>(item.out);
+    const int kin = item.kin;
+    const int n = plan.n;
+    const int ES = LP + 1;
+    C<T>* b0 = reinterpret_cast<C<T>*>(smem_raw);
+    C<T>* b1 = b0 + (size_t)n * ES;
+    const long line0 = (long)blockIdx.x * 2 * LP;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    for (int idx = tid; idx < LP * n; idx += nthr) b0[idx % LP + (idx / LP) * ES] = mk<T>(T(0), T(0));
+    __syncthreads();
+    for (int idx = tid; idx < LP * kin; idx += nthr) {
+        const int l = idx / kin, k = idx - l * kin;
+        if (k > n / 2) continue;
+        const long gl = line0 + 2 * l;
+        C<T> x1 = mk<T>(T(0), T(0)), x2 = mk<T>(T(0), T(0));
+        if (gl < nlines) x1 = in[gl * kin + k];
+        if (gl + 1 < nlines) x2 = in[(gl + 1) * kin + k];
+        if (k == 0 || 2 * k == n) {
+            b0[l + k * ES] = mk<T>(x1.x, x2.x);
+        } else {
+            b0[l + k * ES] = mk<T>(x1.x - x2.y, x1.y + x2.x);
+            b0[l + (n - k) * ES] = mk<T>(x1.x + x2.y, x2.x - x1.y);
+        }
+    }
+    __syncthreads();
+    C<T>* z = fft_lines<T, +1>(b0, b1, LP, ES, plan, tw, tid, nthr);
+    for (int idx = tid; idx < 2 * LP * n; idx += nthr) {
+        const int r = idx / n, e = idx - r * n;
+        const long gl = line0 + r;
+        if (gl >= nlines) continue;
+        const C<T> v = z[(r >> 1) + e * ES];
+        T o = ((r & 1) ? v.y : v.x) * scale;
+        if (mulout) o *= mulout[gl * n + e];
+        out[gl * n + e] = o;
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Strided column pass (y or x axis).  Each CTA transforms TK consecutive columns of one outer slab.
+//   forward (DIR = -1): input positions 0..n-1 at in[o*in_os + i*in_es + c]; keeps wave numbers
+//                       f in out_rng, stored at out[o*out_os + (f - lo)*out_es + c].
+//   inverse (DIR = +1): input holds wave numbers f = in_rng.lo + i (i < in_rng.cnt), zero elsewhere;
+//                       all n positions are stored.
+struct ColItem {
+    const void* in;
+    void* out;
+    long in_os, in_es, out_os, out_es;
+    int ncols, nouter;
+    AxisRange rng;
+};
+struct ColBatch {
+    ColItem it[kMaxItems];
+};
+
+template <typename T, int DIR>
+__global__ void __launch_bounds__(256) k_col(ColBatch batch, FftPlan plan, const C<T>* __restrict__ tw, int TK) {
+    extern __shared__ unsigned char smem_raw[];
+    const ColItem item = batch.it[blockIdx.z];
+    const int n = plan.n;
+    const int c0 = blockIdx.x * TK;
+    const int o = blockIdx.y;
+    if (c0 >= item.ncols || o >= item.nouter) return;
+    const int nc = min(TK, item.ncols - c0);
+    const C<T>* __restrict__ in = static_cast<const C<T>*>(item.in) + (long)o * item.in_os + c0;
+    C<T>* __restrict__ out = static_cast<C<T>*>(item.out) + (long)o * item.out_os + c0;
+    C<T>* b0 = reinterpret_cast<C<T>*>(smem_raw);
+    C<T>* b1 = b0 + (size_t)n * TK;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    if (DIR < 0) {
+        for (int idx = tid; idx < n * TK; idx += nthr) {
+            const int c = idx % TK, i = idx / TK;
+            b0[idx] = c < nc ? in[(long)i * item.in_es + c] : mk<T>(T(0), T(0));
+        }
+    } else {
+        for (int idx = tid; idx < n * TK; idx += nthr) b0[idx] = mk<T>(T(0), T(0));
+        __syncthreads();
+        for (int idx = tid; idx < item.rng.cnt * TK; idx += nthr) {
+            const int c = idx % TK, i = idx / TK;
+            if (c < nc) b0[c + pos_of(item.rng.lo + i, n) * TK] = in[(long)i * item.in_es + c];
+        }
+    }
+    __syncthreads();
+    C<T>* z = fft_lines<T, DIR>(b0, b1, TK, TK, plan, tw, tid, nthr);
+    if (DIR < 0) {
+        for (int idx = tid; idx < item.rng.cnt * TK; idx += nthr) {
+            const int c = idx % TK, i = idx / TK;
+            if (c < nc) out[(long)i * item.out_es + c] = z[c + pos_of(item.rng.lo + i, n) * TK];
+        }
+    } else {
+        for (int idx = tid; idx < n * TK; idx += nthr) {
+            const int c = idx % TK, i = idx / TK;
+            if (c < nc) out[(long)i * item.out_es + c] = z[idx];
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// First inverse pass with the shell filter: for bin b, columns are the (n_y, n_z) points of that bin's
+// bounding box (flattened, n_z fastest); along x only wave numbers in the bin's x-range are loaded,
+// each multiplied by Theta_b(|n|) (bin lookup on the integer |n|^2), an optional per-mode weight
+// (|n|^2-indexed table wtab, or the Legendre factor of the line of sight), and `scale`.
+// spec == nullptr means a unit spectrum (the t_b maps that normalise the bispectrum).
+struct XInvItem {
+    void* out;            // C<T>* [n0][ry.cnt * rz.cnt]
+    AxisRange rx, ry, rz; // bin bounding box
+    int bin;
+};
+struct XInvBatch {
+    XInvItem it[kMaxItems];
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_inv_x_filter(XInvBatch batch, const C<T>* __restrict__ spec,
+                                                      AxisRange gx, AxisRange gy, AxisRange gz,
+                                                      const int16_t* __restrict__ lut, int smax, T scale,
+                                                      FftPlan plan, const C<T>* __restrict__ tw, int TK) {
+    extern __shared__ unsigned char smem_raw[];
+    const XInvItem item = batch.it[blockIdx.y];
+    const int n = plan.n;
+    const int ncols = item.ry.cnt * item.rz.cnt;
+    const int c0 = blockIdx.x * TK;
+    if (c0 >= ncols) return;
+    const int nc = min(TK, ncols - c0);
+    C<T>* b0 = reinterpret_cast<C<T>*>(smem_raw);
+    C<T>* b1 = b0 + (size_t)n * TK;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    for (int idx = tid; idx < n * TK; idx += nthr) b0[idx] = mk<T>(T(0), T(0));
+    __syncthreads();
+    const long gyz = (long)gy.cnt * gz.cnt;
+    for (int idx = tid; idx < item.rx.cnt * TK; idx += nthr) {
+        const int c = idx % TK, i = idx / TK;
+        if (c >= nc) continue;
+        const int cc = c0 + c;
+        const int fy = item.ry.lo + cc / item.rz.cnt;
+        const int fz = item.rz.lo + cc % item.rz.cnt;
+        const int fx = item.rx.lo + i;
+        const int s = fx * fx + fy * fy + fz * fz;
+        if (s > smax || lut[s] != item.bin) continue;
+        C<T> v = mk<T>(scale, T(0));
+        if (spec) {
+            const C<T> d = spec[(long)(fx - gx.lo) * gyz + (long)(fy - gy.lo) * gz.cnt + (fz - gz.lo)];
+            v = mk<T>(d.x * scale, d.y * scale);
+        }
+        b0[c + pos_of(fx, n) * TK] = v;
+    }
+    __syncthreads();
+    C<T>* z = fft_lines<T, +1>(b0, b1, TK, TK, plan, tw, tid, nthr);
+    C<T>* __restrict__ out = static_cast<C<T>*>(item.out);
+    for (int idx = tid; idx < n * TK; idx += nthr) {
+        const int c = idx % TK, i = idx / TK;
+        if (c < nc) out[(long)i * ncols + c0 + c] = z[idx];
+    }
+}
+
+}  // namespace pb

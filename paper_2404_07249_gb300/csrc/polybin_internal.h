@@ -1,0 +1,156 @@
+// Internal declarations shared by the translation units of libpolybin (not part of the C-ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "contract.cuh"
+#include "fft.cuh"
+#include "polybin.h"
+
+#define PB_CUDA_OK_C(expr) PB_CUDA_OK(expr)
+
+namespace pb {
+
+// Per-bin bounding box of the inverse transforms and offsets of its intermediates.
+struct BinBox {
+    AxisRange rx, ry, rz;
+    long u1_off, u2_off;
+};
+
+// Device workspace of one compute precision.
+struct Work {
+    size_t elem = 0;
+    void* t1 = nullptr;      // forward z-pass output [N0*N1][Bz]
+    void* t2 = nullptr;      // forward y-pass output [N0][By][Bz]
+    void* box = nullptr;     // pruned spectrum [Bx][By][Bz]
+    void* u1 = nullptr;      // inverse x-pass outputs, all bins
+    void* u2 = nullptr;      // inverse y-pass outputs, all bins
+    void* g = nullptr;       // shell maps [nb][N]
+    double* partial = nullptr;
+    size_t partial_cap = 0;
+    double* mout = nullptr;  // contraction result [npairs][nh]
+};
+
+int fail(polybin_ctx* ctx, int status, const char* fmt, ...);
+int fail_cuda(polybin_ctx* ctx, cudaError_t e, const char* what, const char* file, int line);
+
+inline int pair_index(int nb, int a, int b) { return a * nb - a * (a - 1) / 2 + (b - a); }
+inline long pairs_offset(int n) { return (long)(n - 1) * n * (n + 1) / 6; }  // sum_{m<n} m(m+1)/2
+
+// Gaussian elimination with partial pivoting on an n x (n+1) augmented matrix (n <= 3).
+inline bool solve_small(double A[3][4], int n, double* x) {
+    for (int c = 0; c < n; ++c) {
+        int p = c;
+        for (int r = c + 1; r < n; ++r)
+            if ((A[r][c] < 0 ? -A[r][c] : A[r][c]) > (A[p][c] < 0 ? -A[p][c] : A[p][c])) p = r;
+        if (A[p][c] == 0.0) return false;
+        if (p != c)
+            for (int k = 0; k <= n; ++k) { double t = A[c][k]; A[c][k] = A[p][k]; A[p][k] = t; }
+        for (int r = c + 1; r < n; ++r) {
+            const double f = A[r][c] / A[c][c];
+            for (int k = c; k <= n; ++k) A[r][k] -= f * A[c][k];
+        }
+    }
+    for (int r = n - 1; r >= 0; --r) {
+        double s = A[r][n];
+        for (int k = r + 1; k < n; ++k) s -= A[r][k] * x[k];
+        x[r] = s / A[r][r];
+    }
+    return true;
+}
+
+ContractGeom contract_geom(int nb, int nh, long ncell);
+
+template <typename T> int run_forward(polybin_ctx*, const float*, const float*, const float*, C<T>*, C<T>*, C<T>*);
+template <typename T> int run_shells(polybin_ctx*, const C<T>*, C<T>*, C<T>*, T*);
+template <typename T> int run_contract(polybin_ctx*, const T*, int, const T*, int, double*, size_t, double*);
+// Contraction dispatch: the tensor-core kernel in POLYBIN_SPLIT_TF32X3 mode, the SIMT kernel otherwise.
+template <typename T> int run_contract_any(polybin_ctx*, const T*, int, const T*, int, double*, size_t, double*);
+template <typename T> int alloc_work(polybin_ctx*, Work&);
+int alloc_work_shells_double(polybin_ctx*, Work&);
+void free_work(Work&);
+int resolve_input(polybin_ctx*, const float*, size_t, const float**);
+int ensure_triplets(polybin_ctx*);
+bool split_tc_available();
+void destroy_extras(polybin_ctx*);
+
+}  // namespace pb
+
+struct polybin_ctx {
+    int N[3] = {0, 0, 0};
+    long ncell = 0;
+    double L = 0, vol = 0, kf = 0;
+    int nb = 0;
+    std::vector<double> edges;
+    int lmax = 0, nell = 1;
+    int prec = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+
+    // planner
+    pb::AxisRange gx{0, 0}, gy{0, 0}, gz{0, 0};
+    std::vector<pb::BinBox> bbox;
+    long u1_total = 0, u2_total = 0;
+    int smax = 0;
+    std::vector<int16_t> lut;
+    int16_t* d_lut = nullptr;
+    pb::FftPlan plan[3];
+    void* d_tw_f[3] = {nullptr, nullptr, nullptr};
+    void* d_tw_d[3] = {nullptr, nullptr, nullptr};
+    short2* d_pairs = nullptr;   // pair tables for every n <= 64, table n at pairs_offset(n)
+
+    // workspace
+    pb::Work w;
+    float* d_in = nullptr;
+    size_t in_cap = 0;
+
+    // P_ell binning
+    long nmodes = 0;
+    int* d_offs = nullptr;
+    double* d_coef = nullptr;
+    int* d_bin_start = nullptr;
+    double* d_pkpart = nullptr;
+    int pk_seg_len = 0, pk_nseg = 0;
+    std::vector<double> counts;
+    std::vector<double> fish_disc;   // [nb][nell][nell]
+
+    // closed triplets (lexicographic), T_abc and N_abc
+    bool trip_ready = false;
+    std::vector<int> trip;
+    std::vector<double> Tabc, Nabc;
+
+    // instrumentation: kernel launches issued, and (when enabled) per-stage device time from CUDA events
+    long launches = 0;
+    bool profiling = false;
+    double stage_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    long stage_calls[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+
+    // extension slots (tensor-core contraction state, unwindowed estimators)
+    void* ext = nullptr;
+};
+
+namespace pb {
+enum Stage { kStageForward = 0, kStageShells = 1, kStageContract = 2, kStagePk = 3, kNumStages = 4 };
+// Brackets a pipeline stage with CUDA events on the context stream when profiling is enabled.
+struct StageTimer {
+    polybin_ctx* ctx;
+    int stage;
+    StageTimer(polybin_ctx* c, int s) : ctx(c), stage(s) {
+        if (ctx->profiling) cudaEventRecord(ctx->ev[0], ctx->stream);
+    }
+    ~StageTimer() {
+        if (!ctx->profiling) return;
+        float ms = 0.f;
+        cudaEventRecord(ctx->ev[1], ctx->stream);
+        if (cudaEventSynchronize(ctx->ev[1]) == cudaSuccess && cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]) == cudaSuccess) {
+            ctx->stage_ms[stage] += ms;
+            ctx->stage_calls[stage] += 1;
+        }
+    }
+};
+}  // namespace pb
