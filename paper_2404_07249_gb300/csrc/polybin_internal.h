@@ -76,6 +76,8 @@ void free_work(Work&);
 int resolve_input(polybin_ctx*, const float*, size_t, const float**);
 int ensure_triplets(polybin_ctx*);
 bool split_tc_available();
+ContractGeom contract_geom_tc(int ng, int nh, long ncell);
+int run_contract_tc(polybin_ctx*, const float*, int, const float*, int, double*, size_t, double*);
 void destroy_extras(polybin_ctx*);
 
 }  // namespace pb
@@ -130,7 +132,10 @@ struct polybin_ctx {
     long stage_calls[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     cudaEvent_t ev[2] = {nullptr, nullptr};
 
-    // extension slots (tensor-core contraction state, unwindowed estimators)
+    // device error flag of the kernels with bounded waits
+    int* d_err = nullptr;
+
+    // extension slots (unwindowed estimators)
     void* ext = nullptr;
 };
 

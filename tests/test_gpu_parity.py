@@ -16,7 +16,11 @@ from paper_2404_07249_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp32": dict(l2=2e-6, norm=1e-6, rel=1e-6), "fp64": dict(l2=1e-12, norm=1e-12, rel=1e-11)}
+# kappa_max: e_rel is asserted for triplets with kappa * (FFT noise of the path) below the target, i.e. kappa <= 10
+# for the FP32 FFTs (relative noise ~1e-7) and kappa <= 1e3 for FP64; e_norm is asserted for every triplet.
+TOL = {"fp32": dict(l2=2e-6, norm=1e-6, rel=1e-6, kappa_max=10.0),
+       "split": dict(l2=2e-6, norm=1e-6, rel=1e-6, kappa_max=10.0),
+       "fp64": dict(l2=1e-12, norm=1e-12, rel=1e-11, kappa_max=1e3)}
 
 
 @pytest.fixture(scope="module")
@@ -83,15 +87,17 @@ def test_forward_and_shell_maps(pkg, case, prec):
     pb.close()
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("prec", ["fp32", "split", "fp64"])
 @pytest.mark.parametrize("nh_same", [True, False])
-def test_contraction(pkg, prec, nh_same):
-    grid, box = (40, 48, 32), 800.0
+@pytest.mark.parametrize("shape", [(9, 5, (40, 48, 32)), (30, 30, (24, 20, 18)), (31, 32, (16, 12, 10)),
+                                   (2, 1, (6, 4, 2))])
+def test_contraction(pkg, prec, nh_same, shape):
+    ng, nh, grid = shape
+    box = 800.0
     rng = np.random.Generator(np.random.PCG64(7))
-    ng, nh = 9, 5
-    dt = np.float32 if prec == "fp32" else np.float64
+    dt = np.float64 if prec == "fp64" else np.float32
     g = rng.standard_normal((ng,) + grid).astype(dt)
-    g[3] *= 1e3                     # dynamic range between maps
+    g[min(3, ng - 1)] *= 1e3        # dynamic range between maps
     h = rng.standard_normal((nh,) + grid).astype(dt)
     pb = pkg.PolyBin(grid, box, _kf(box) * np.array([1.0, 2.0]), prec=prec)
     tg = torch.from_numpy(g).cuda()
@@ -112,7 +118,7 @@ def test_contraction(pkg, prec, nh_same):
     pb.close()
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("prec", ["fp32", "split", "fp64"])
 @pytest.mark.parametrize("case", [0, 1, 3, 4])
 def test_bk_ideal_and_nabc(pkg, case, prec):
     grid, box, ek, kind = CASES[case]
@@ -133,9 +139,10 @@ def test_bk_ideal_and_nabc(pkg, case, prec):
     kappa = absS / np.abs(ref["S"])
     e_norm = np.abs(B - ref["B"]) / ((vol * vol / N ** 3) * absS / ref["T"])
     assert np.max(e_norm) < TOL[prec]["norm"], np.max(e_norm)
-    ok = kappa < 1e3
+    ok = kappa <= TOL[prec]["kappa_max"]
     e_rel = np.abs(B - ref["B"]) / np.abs(ref["B"])
-    assert np.max(e_rel[ok]) < TOL[prec]["rel"], (np.max(e_rel[ok]), np.argmax(e_rel))
+    if ok.any():
+        assert np.max(e_rel[ok]) < TOL[prec]["rel"], (np.max(e_rel[ok]), np.argmax(e_rel))
     # host input gives the same numbers as device input
     B2 = pb.bk_ideal(f)[0]
     assert np.array_equal(B, B2)
@@ -172,9 +179,16 @@ def test_batch_and_stream(pkg):
         pb = pkg.PolyBin(grid, box, edges, lmax=2, prec="fp32", stream=s.cuda_stream)
         B = pb.bk_ideal(torch.from_numpy(fs).cuda())
         P = pb.pk(torch.from_numpy(fs).cuda())
+    # a batch gives exactly the per-field results (same kernels, same order), and matches the oracle
     for i in range(3):
+        B1 = pb.bk_ideal(torch.from_numpy(fs[i]).cuda())[0]
+        assert np.array_equal(B[i], B1)
         ref = ideal.bk_ideal(fs[i], box, edges)
-        assert np.max(np.abs(B[i] - ref["B"]) / np.abs(ref["B"])) < 1e-5
+        e_norm_bound = 1e-6 * (box ** 6 / fs[i].size ** 3) / ref["T"]
+        bins = binning.bin_grid(grid, box, edges)
+        G = ideal.shell_maps(ideal.forward(fs[i]), bins, len(edges) - 1).reshape(len(edges) - 1, -1)
+        absS = np.array([np.sum(np.abs(G[a] * G[b] * G[c])) for a, b, c in ref["triplets"]])
+        assert np.all(np.abs(B[i] - ref["B"]) <= e_norm_bound * absS)
         pr = ideal.pk_ideal(fs[i], box, edges, 2)["P"]
         assert np.max(np.abs(P[i, 0] - pr[0]) / np.abs(pr[0])) < 1e-6
     pb.close()
