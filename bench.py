@@ -162,7 +162,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="fp32", choices=["split", "fp32", "fp64"])
+    ap.add_argument("--prec", default="split", choices=["split", "fp32", "fp64"])
     ap.add_argument("--config", type=int, default=3)
     ap.add_argument("--fp64-steps", type=int, default=1, help="steps of the FP64 GPU comparator (0 = skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
