@@ -115,7 +115,7 @@ def cpu_baseline(cfg: int, field: np.ndarray, edges, box: float, budget_s: float
     g0 = ideal.shell_maps(D, bins, nb, which=[nb // 2])
     t_shell = time.perf_counter() - t0
     del D
-    slab = max(1, min(field.shape[0], int(field.shape[0] * min(1.0, 2.0e6 / N * 8))))
+    slab = max(1, min(field.shape[0], int(field.shape[0] * min(1.0, 2.0e6 / N * 4))))
     rng = np.random.Generator(np.random.PCG64(1))
     gs = rng.standard_normal((nb, slab) + field.shape[1:])
     t0 = time.perf_counter()

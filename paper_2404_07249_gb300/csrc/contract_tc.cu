@@ -7,18 +7,22 @@
 // product is accumulated as hi_a hi_b + hi_a lo_b + lo_a hi_b (the lo_a lo_b term, ~2^-22 relative, is
 // dropped).
 //
-// Warp roles (288 threads, one CTA per SM):
-//   warps 0-3  producers: stream the map tiles into a shared-memory ring with cp.async, form the pair
-//              products (thread t owns TMEM lane t, i.e. row t of every pair tile), split them and write
-//              them into TMEM with tcgen05.st (the A operand never touches shared memory); convert the
-//              singles tile to hi/lo TF32 in the canonical no-swizzle K-major layout (the B operand).
-//   warp 4     allocates TMEM; lane 0 issues tcgen05.mma (A from TMEM, B from shared memory, D in TMEM)
-//              and tcgen05.commit to mbarriers.
-//   warps 5-8  epilogue: every kPeriod chunks read the FP32 accumulators with tcgen05.ld and add them
-//              into FP64 partial sums held in shared memory; finally write the CTA's FP64 partials.
-// TMEM (512 columns): D = 4 tiles x 32 columns at [0,128); A ring = 3 stages x (4 tiles x (16 hi + 16 lo))
-// at [128, 512).  Every mbarrier wait is bounded; on timeout the CTA raises an error flag and exits after
-// draining its own asynchronous work.
+// Warp roles (512 threads, one CTA per SM):
+//   warps 0-7   producers (two per scheduler): stream the map tiles into a shared-memory ring with cp.async,
+//               form the pair products (a thread owns one TMEM lane, i.e. one row of two of the pair tiles),
+//               split them and write them into TMEM with tcgen05.st (the A operand never touches shared
+//               memory); threads 0-127 also convert the singles tile to hi/lo TF32 in the canonical
+//               no-swizzle K-major layout (the B operand).
+//   warps 8-15  epilogue: every kPeriod chunks (64 cells) read the accumulators with tcgen05.ld into FP32
+//               register sums (round-to-nearest), every kSpill periods add those into FP64 partials in
+//               shared memory; finally write the CTA's FP64 partials.  Warp 8 also allocates TMEM and its
+//               lane 0 issues the tcgen05.mma (A from TMEM, B from shared memory, D in TMEM) and
+//               tcgen05.commit of period q before it drains period q-1 (D is double buffered).
+// Precision: the tensor core's internal accumulation is not round-to-nearest, so its error grows with the
+// number of MMAs accumulated into one D; the 64-cell periods keep that chain at 24 MMAs.
+// TMEM (512 columns): D double buffer 2 x (4 tiles x 32 columns) at [0, 256); A ring = 2 stages x
+// (4 tiles x (16 hi + 16 lo)) at [256, 512).  Every mbarrier wait is bounded; on timeout the CTA raises an
+// error flag and exits after draining its own asynchronous work.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -29,13 +33,18 @@ namespace pb {
 namespace tc {
 
 constexpr int kKC = 16;           // cells per chunk (two K=8 MMA steps)
-constexpr int kStages = 3;        // A/B pipeline depth
+constexpr int kStages = 2;        // A/B pipeline depth
 constexpr int kRing = 4;          // map-tile ring (prefetch distance 3)
-constexpr int kPeriod = 64;       // chunks per FP32 accumulation period (1024 cells)
+constexpr int kPeriod = 4;        // chunks per tensor-memory accumulation period (64 cells)
+constexpr int kSpill = 32;        // periods per FP32 register accumulation before the FP64 update (2048 cells)
 constexpr int kMaxTiles = 4;      // pair tiles of 128 rows (npairs <= 512)
 constexpr int kNCols = 32;        // singles per tile (nh <= 32)
 constexpr int kGS = 20;           // floats per map row in the ring (16 + 4 pad: conflict-free LDS.128)
-constexpr int kThreads = 288;
+constexpr int kProducerWarps = 8;
+constexpr int kProducers = 32 * kProducerWarps;
+constexpr int kMmaWarp = kProducerWarps;   // first epilogue warp; its lane 0 also issues the MMAs
+constexpr int kEpilogue = 256;             // 8 epilogue warps
+constexpr int kThreads = kProducers + kEpilogue;
 constexpr unsigned kSpinLimit = 1u << 22;
 
 struct Params {
@@ -73,10 +82,12 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
 
 // Bounded wait; returns false (and raises the abort flag) if the phase did not complete in time or another
 // role aborted.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err,
+                                          int backoff) {
     for (unsigned it = 0; it < kSpinLimit; ++it) {
         if (mbar_try(bar, parity)) return true;
         if (*abort_flag) return false;
+        if (backoff) __nanosleep(64);
     }
     *abort_flag = 1;
     atomicExch(err, 1);
@@ -92,9 +103,10 @@ __device__ __forceinline__ uint32_t to_tf32(float x) {
     return r;
 }
 
-__device__ __forceinline__ void split(float v, uint32_t& hi, uint32_t& lo) {
+// v = hi + lo with hi = rna_tf32(v) and lo = v - hi exact in FP32; the MMA reads lo's leading 11 bits.
+__device__ __forceinline__ void split2(float v, uint32_t& hi, uint32_t& lo) {
     hi = to_tf32(v);
-    lo = to_tf32(v - __uint_as_float(hi));
+    lo = __float_as_uint(v - __uint_as_float(hi));
 }
 
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* v) {
@@ -148,11 +160,11 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                  : "memory");
 }
 
-// Named-barrier AND-vote over the 128 producer threads (barrier 1): every producer gets the same answer.
+// Named-barrier AND-vote over the 256 producer threads (barrier 1): every producer gets the same answer.
 __device__ __forceinline__ bool producers_all(bool v) {
     uint32_t r;
     asm volatile(
-        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.and.pred q, 1, 128, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.and.pred q, 1, 256, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
         : "=r"(r)
         : "r"((uint32_t)v)
         : "memory");
@@ -166,18 +178,17 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_b
 
 __global__ void __launch_bounds__(kThreads, 1) k_contract_tc(Params P) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    // layout
     double* acc64 = reinterpret_cast<double*>(smem);                                   // [tiles][32][128]
     unsigned char* bbase = smem + (size_t)kMaxTiles * kNCols * 128 * sizeof(double);   // B stages
     const int BSTAGE = 2 * kNCols * kKC * 4;                                            // hi + lo, 4 KB
     float* ring = reinterpret_cast<float*>(bbase + kStages * BSTAGE);                   // [kRing][rows][kGS]
     const int rows = P.ng + (P.h != P.g ? P.nh : 0);
     uint64_t* bars = reinterpret_cast<uint64_t*>(ring + (size_t)kRing * rows * kGS);
-    uint64_t* full = bars;                  // [kStages]
-    uint64_t* empty = bars + kStages;       // [kStages]
-    uint64_t* dfull = bars + 2 * kStages;
-    uint64_t* dempty = dfull + 1;
-    uint64_t* fin = dempty + 1;
+    uint64_t* full = bars;                  // [kStages]   producers -> MMA
+    uint64_t* empty = bars + kStages;       // [kStages]   MMA commit -> producers
+    uint64_t* dfull = bars + 2 * kStages;   // [2]         MMA commit -> epilogue
+    uint64_t* dempty = dfull + 2;           // [2]         epilogue -> MMA
+    uint64_t* fin = dempty + 2;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
@@ -190,42 +201,43 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract_tc(Params P) {
 
     for (int i = tid; i < P.ntiles * kNCols * 128; i += blockDim.x) acc64[i] = 0.0;
     if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) { mbar_init(&full[s], 128); mbar_init(&empty[s], 1); }
-        mbar_init(dfull, 1);
-        mbar_init(dempty, 128);
+        for (int s = 0; s < kStages; ++s) { mbar_init(&full[s], kProducers); mbar_init(&empty[s], 1); }
+        for (int d = 0; d < 2; ++d) { mbar_init(&dfull[d], 1); mbar_init(&dempty[d], kEpilogue); }
         mbar_init(fin, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 4) {
+    if (warp == kMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = *tmem_slot;
-    const uint32_t D0 = tmem;                 // D tile t at column 32 t
-    const uint32_t A0 = tmem + 128;           // A stage s, tile t: hi at 128 s + 32 t, lo at +16
+    const uint32_t tmem = *tmem_slot;        // D buffer d, tile t at column 128 d + 32 t
+    const uint32_t A0 = tmem + 256;          // A stage s, tile t: hi at 256 + 128 s + 32 t, lo at +16
 
-    if (warp < 4) {
+    if (warp < kProducerWarps) {
         // ------------------------------------------------------------------ producers
-        const float* hsrc = P.h;
         const bool hsep = P.h != P.g;
-        int pj[kMaxTiles], pk[kMaxTiles];
+        const int quarter = warp & 3, half = warp >> 2;
+        const int row = 32 * quarter + lane;
+        const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
+        int pj[2], pk[2];
 #pragma unroll
-        for (int t = 0; t < kMaxTiles; ++t) {
-            const int p = 128 * t + tid;
-            if (t < P.ntiles && p < P.npairs) { short2 jk = P.pairs[p]; pj[t] = jk.x; pk[t] = jk.y; }
-            else { pj[t] = -1; pk[t] = -1; }
+        for (int u = 0; u < 2; ++u) {
+            const int t = 2 * half + u;
+            const int p = 128 * t + row;
+            if (t < P.ntiles && p < P.npairs) { short2 jk = P.pairs[p]; pj[u] = jk.x; pk[u] = jk.y; }
+            else { pj[u] = -1; pk[u] = -1; }
         }
         auto issue = [&](int c) {
             if (c < nchunks) {
                 float* slot = ring + (size_t)(c % kRing) * rows * kGS;
                 const long x0 = cbeg + (long)c * kKC;
-                for (int q = tid; q < rows * 4; q += 128) {
+                for (int q = tid; q < rows * 4; q += kProducers) {
                     const int r = q >> 2, quad = q & 3;
-                    const float* src = (r < P.ng) ? P.g + (long)r * P.ncell : hsrc + (long)(r - P.ng) * P.ncell;
+                    const float* src = (r < P.ng) ? P.g + (long)r * P.ncell : P.h + (long)(r - P.ng) * P.ncell;
                     const long cell = x0 + quad * 4;
                     const long valid = min(4L, max(0L, cend - cell));
                     cp_async16(slot + r * kGS + quad * 4, valid > 0 ? src + cell : src, (int)(valid * 4));
@@ -236,56 +248,56 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract_tc(Params P) {
         issue(0);
         issue(1);
         issue(2);
-        const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
         bool ok = true;
         for (int c = 0; c < nchunks; ++c) {
             const int s = c % kStages;
             asm volatile("cp.async.wait_group 2;" ::: "memory");
             bool mine = true;
-            if (c >= kStages) mine = mbar_wait(&empty[s], (uint32_t)((c / kStages - 1) & 1), abort_flag, P.err);
+            if (c >= kStages) mine = mbar_wait(&empty[s], (uint32_t)((c / kStages - 1) & 1), abort_flag, P.err, 0);
             // uniform decision + barrier: chunk c's tile is visible to all producers and chunk c-1 is finished
             ok = producers_all(mine);
             if (!ok) break;
             if (c >= kStages) tc_fence_after();
             issue(c + 3);
             const float* tile = ring + (size_t)(c % kRing) * rows * kGS;
-            // A operand: pair products, split, into TMEM
+            // A operand: pair products split into TF32 hi and FP32 remainder (read as TF32 by the MMA), into TMEM
 #pragma unroll
-            for (int t = 0; t < kMaxTiles; ++t) {
+            for (int u = 0; u < 2; ++u) {
+                const int t = 2 * half + u;
                 if (t >= P.ntiles) break;
                 uint32_t hi[kKC], lo[kKC];
-                if (pj[t] >= 0) {
-                    const float4* a = reinterpret_cast<const float4*>(tile + pj[t] * kGS);
-                    const float4* b = reinterpret_cast<const float4*>(tile + pk[t] * kGS);
+                if (pj[u] >= 0) {
+                    const float4* a = reinterpret_cast<const float4*>(tile + pj[u] * kGS);
+                    const float4* b = reinterpret_cast<const float4*>(tile + pk[u] * kGS);
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        const float4 u = a[q], v = b[q];
-                        split(u.x * v.x, hi[4 * q + 0], lo[4 * q + 0]);
-                        split(u.y * v.y, hi[4 * q + 1], lo[4 * q + 1]);
-                        split(u.z * v.z, hi[4 * q + 2], lo[4 * q + 2]);
-                        split(u.w * v.w, hi[4 * q + 3], lo[4 * q + 3]);
+                        const float4 x = a[q], y = b[q];
+                        split2(x.x * y.x, hi[4 * q + 0], lo[4 * q + 0]);
+                        split2(x.y * y.y, hi[4 * q + 1], lo[4 * q + 1]);
+                        split2(x.z * y.z, hi[4 * q + 2], lo[4 * q + 2]);
+                        split2(x.w * y.w, hi[4 * q + 3], lo[4 * q + 3]);
                     }
                 } else {
 #pragma unroll
                     for (int q = 0; q < kKC; ++q) { hi[q] = 0u; lo[q] = 0u; }
                 }
-                const uint32_t col = 128u + 128u * s + 32u * t;
+                const uint32_t col = 256u + 128u * s + 32u * t;
                 tmem_st16(tmem + lane_base + col, hi);
                 tmem_st16(tmem + lane_base + col + 16u, lo);
             }
-            // B operand: singles hi/lo in the no-swizzle K-major layout:
+            // B operand (threads 0..127): singles hi/lo in the no-swizzle K-major layout:
             // element (row r, cell k) at (r / 8) * 512 + (k / 4) * 128 + (r % 8) * 16 + (k % 4) * 4 bytes.
-            {
+            if (tid < 128) {
                 unsigned char* bs = bbase + s * BSTAGE;
                 const int r = tid >> 2, quad = tid & 3;
                 uint4 vh = make_uint4(0, 0, 0, 0), vl = make_uint4(0, 0, 0, 0);
                 if (r < P.nh) {
-                    const int row = hsep ? P.ng + r : r;
-                    const float4 v = *reinterpret_cast<const float4*>(tile + row * kGS + quad * 4);
-                    split(v.x, vh.x, vl.x);
-                    split(v.y, vh.y, vl.y);
-                    split(v.z, vh.z, vl.z);
-                    split(v.w, vh.w, vl.w);
+                    const int rr = hsep ? P.ng + r : r;
+                    const float4 v = *reinterpret_cast<const float4*>(tile + rr * kGS + quad * 4);
+                    split2(v.x, vh.x, vl.x);
+                    split2(v.y, vh.y, vl.y);
+                    split2(v.z, vh.z, vl.z);
+                    split2(v.w, vh.w, vl.w);
                 }
                 const int off = (r >> 3) * 512 + quad * 128 + (r & 7) * 16;
                 *reinterpret_cast<uint4*>(bs + off) = vh;
@@ -298,67 +310,104 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract_tc(Params P) {
         }
         asm volatile("cp.async.wait_all;" ::: "memory");
         if (!ok) *abort_flag = 1;
-    } else if (warp == 4) {
-        // ------------------------------------------------------------------ MMA issuer
-        if (lane == 0) {
+    } else {
+        // ------------------------------------------------------------------ epilogue (+ MMA issue in warp 8)
+        const int e = warp - kProducerWarps;       // 0..7
+        const int quarter = warp & 3;              // TMEM lane quarter this warp may access
+        const int half = e >> 2;                   // tiles 2 half, 2 half + 1
+        const int row = 32 * quarter + lane;
+        const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
+        const bool issuer = (warp == kMmaWarp);
+        float acc[2][kNCols];
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+            for (int i = 0; i < kNCols; ++i) acc[u][i] = 0.f;
+        auto spill = [&]() {
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int t = 2 * half + u;
+                if (t >= P.ntiles) break;
+#pragma unroll
+                for (int i = 0; i < kNCols; ++i) {
+                    acc64[(t * kNCols + i) * 128 + row] += (double)acc[u][i];
+                    acc[u][i] = 0.f;
+                }
+            }
+        };
+        // read the accumulators of period q, release the D buffer, add into the FP32 register sums
+        auto drain = [&](int q) -> bool {
+            const int d = q & 1;
+            if (!mbar_wait(&dfull[d], (uint32_t)((q >> 1) & 1), abort_flag, P.err, issuer ? 0 : 1)) return false;
+            tc_fence_after();
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int t = 2 * half + u;
+                if (t >= P.ntiles) break;
+                uint32_t v[kNCols];
+                tmem_ld32(tmem + lane_base + 128u * d + 32u * t, v);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int i = 0; i < kNCols; ++i) acc[u][i] += __uint_as_float(v[i]);
+            }
+            tc_fence_before();
+            mbar_arrive(&dempty[d]);
+            if ((q + 1) % kSpill == 0) spill();
+            return true;
+        };
+        // issue the MMAs of period q (lane 0 of the issuer warp)
+        bool mma_ok = true;
+        auto issue_period = [&](int q) {
             const uint32_t idesc = idesc_tf32(128, kNCols);
             const uint32_t bstage0 = smem_u32(bbase);
-            bool ok = true;
-            for (int c = 0; c < nchunks && ok; ++c) {
+            const int d = q & 1;
+            if (q >= 2 && !mbar_wait(&dempty[d], (uint32_t)((q / 2 - 1) & 1), abort_flag, P.err, 0)) { mma_ok = false; return; }
+            const int c1 = min(nchunks, (q + 1) * kPeriod);
+            for (int c = q * kPeriod; c < c1; ++c) {
                 const int s = c % kStages;
-                const int q = c / kPeriod;
-                const bool first = (c % kPeriod) == 0;
-                if (first && q > 0) {
-                    if (!mbar_wait(dempty, (uint32_t)((q - 1) & 1), abort_flag, P.err)) { ok = false; break; }
-                }
-                if (!mbar_wait(&full[s], (uint32_t)((c / kStages) & 1), abort_flag, P.err)) { ok = false; break; }
+                const bool first = c == q * kPeriod;
+                if (!mbar_wait(&full[s], (uint32_t)((c / kStages) & 1), abort_flag, P.err, 0)) { mma_ok = false; return; }
                 tc_fence_after();
                 const uint32_t bh = bstage0 + s * BSTAGE, bl = bh + 2048;
                 for (int t = 0; t < P.ntiles; ++t) {
-                    const uint32_t d = D0 + 32u * t;
+                    const uint32_t dcol = tmem + 128u * d + 32u * t;
                     const uint32_t ah = A0 + 128u * s + 32u * t, al = ah + 16u;
 #pragma unroll
                     for (int ks = 0; ks < kKC / 8; ++ks) {
                         const uint64_t dbh = sdesc(bh + ks * 256, 128, 512);
                         const uint64_t dbl = sdesc(bl + ks * 256, 128, 512);
-                        mma_tf32(d, ah + 8u * ks, dbh, idesc, (first && ks == 0) ? 0u : 1u);
-                        mma_tf32(d, ah + 8u * ks, dbl, idesc, 1u);
-                        mma_tf32(d, al + 8u * ks, dbh, idesc, 1u);
+                        mma_tf32(dcol, ah + 8u * ks, dbh, idesc, (first && ks == 0) ? 0u : 1u);
+                        mma_tf32(dcol, ah + 8u * ks, dbl, idesc, 1u);
+                        mma_tf32(dcol, al + 8u * ks, dbh, idesc, 1u);
                     }
                 }
                 mma_commit(&empty[s]);
-                if ((c % kPeriod) == kPeriod - 1 || c == nchunks - 1) mma_commit(dfull);
             }
-            // drain: every MMA issued by this thread has completed before TMEM is released
-            mma_commit(fin);
-            for (unsigned it = 0; it < kSpinLimit && !mbar_try(fin, 0); ++it) {
+            mma_commit(&dfull[d]);
+        };
+        bool ok = true;
+        if (issuer) {
+            for (int q = 0; q < nperiods; ++q) {
+                if (lane == 0 && mma_ok) issue_period(q);
+                __syncwarp();
+                if (q >= 1 && ok) ok = drain(q - 1);
             }
-            if (!ok) *abort_flag = 1;
+            if (nperiods >= 1 && ok) ok = drain(nperiods - 1);
+            if (lane == 0) {
+                // every MMA issued by this thread has completed before TMEM is released
+                mma_commit(fin);
+                for (unsigned it = 0; it < kSpinLimit && !mbar_try(fin, 0); ++it) {
+                }
+                if (!mma_ok) *abort_flag = 1;
+            }
+            __syncwarp();
+        } else {
+            for (int q = 0; q < nperiods && ok; ++q) ok = drain(q);
         }
-        __syncwarp();
-    } else {
-        // ------------------------------------------------------------------ epilogue
-        const int quarter = warp & 3;
-        const int row = 32 * quarter + lane;               // TMEM lane = row of every pair tile
-        const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
-        for (int q = 0; q < nperiods; ++q) {
-            if (!mbar_wait(dfull, (uint32_t)(q & 1), abort_flag, P.err)) break;
-            tc_fence_after();
-            uint32_t v[kMaxTiles][kNCols];
-#pragma unroll
-            for (int t = 0; t < kMaxTiles; ++t)
-                if (t < P.ntiles) tmem_ld32(tmem + lane_base + 32u * t, v[t]);
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            tc_fence_before();
-            mbar_arrive(dempty);
-#pragma unroll
-            for (int t = 0; t < kMaxTiles; ++t) {
-                if (t >= P.ntiles) break;
-#pragma unroll
-                for (int i = 0; i < kNCols; ++i) acc64[(t * kNCols + i) * 128 + row] += (double)__uint_as_float(v[t][i]);
-            }
-        }
-        for (int t = 0; t < P.ntiles; ++t) {
+        spill();
+        for (int u = 0; u < 2; ++u) {
+            const int t = 2 * half + u;
+            if (t >= P.ntiles) break;
             const int p = 128 * t + row;
             if (p >= P.npairs) continue;
             double* out = P.partial + ((size_t)blockIdx.x * P.npairs + p) * P.nh;
@@ -368,7 +417,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract_tc(Params P) {
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 4) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+    if (warp == kMmaWarp) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
 }
 
 }  // namespace tc
@@ -377,7 +426,7 @@ bool split_tc_available() { return true; }
 
 static size_t tc_smem_bytes(int rows) {
     return (size_t)tc::kMaxTiles * tc::kNCols * 128 * sizeof(double) + tc::kStages * 2 * tc::kNCols * tc::kKC * 4 +
-           (size_t)tc::kRing * rows * tc::kGS * sizeof(float) + 128;
+           (size_t)tc::kRing * rows * tc::kGS * sizeof(float) + 256;
 }
 
 // Geometry of the tensor-core contraction: one CTA per SM over a contiguous cell range.
