@@ -15,9 +15,11 @@
 //               no-swizzle K-major layout (the B operand).
 //   warps 8-15  epilogue: every kPeriod chunks (64 cells) read the accumulators with tcgen05.ld into FP32
 //               register sums (round-to-nearest), every kSpill periods add those into FP64 partials in
-//               shared memory; finally write the CTA's FP64 partials.  Warp 8 also allocates TMEM and its
-//               lane 0 issues the tcgen05.mma (A from TMEM, B from shared memory, D in TMEM) and
-//               tcgen05.commit of period q before it drains period q-1 (D is double buffered).
+//               shared memory; finally write the CTA's FP64 partials.  Warp 8 allocates TMEM.  Lane 0 of
+//               warps 8-11 issues the tcgen05.mma (A from TMEM, B from shared memory, D in TMEM) and the
+//               tcgen05.commit of one pair tile for period q before its warp drains period q-1 (D is
+//               double buffered).  The 128x32x8 MMAs are short, so one issuing thread cannot keep the
+//               tensor pipe busy; four issuers overlap their issue latency.
 // Precision: the tensor core's internal accumulation is not round-to-nearest, so its error grows with the
 // number of MMAs accumulated into one D; the 64-cell periods keep that chain at 24 MMAs.
 // TMEM (512 columns): D double buffer 2 x (4 tiles x 32 columns) at [0, 256); A ring = 2 stages x
@@ -42,7 +44,8 @@ constexpr int kNCols = 32;        // singles per tile (nh <= 32)
 constexpr int kGS = 20;           // floats per map row in the ring (16 + 4 pad: conflict-free LDS.128)
 constexpr int kProducerWarps = 8;
 constexpr int kProducers = 32 * kProducerWarps;
-constexpr int kMmaWarp = kProducerWarps;   // first epilogue warp; its lane 0 also issues the MMAs
+constexpr int kMmaWarp = kProducerWarps;   // first epilogue warp; allocates TMEM
+constexpr int kIssuers = 4;                // epilogue warps 8..11: lane 0 issues the MMAs of tile (warp - 8)
 constexpr int kEpilogue = 256;             // 8 epilogue warps
 constexpr int kThreads = kProducers + kEpilogue;
 constexpr unsigned kSpinLimit = 1u << 22;
@@ -201,9 +204,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract_tc(Params P) {
 
     for (int i = tid; i < P.ntiles * kNCols * 128; i += blockDim.x) acc64[i] = 0.0;
     if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) { mbar_init(&full[s], kProducers); mbar_init(&empty[s], 1); }
-        for (int d = 0; d < 2; ++d) { mbar_init(&dfull[d], 1); mbar_init(&dempty[d], kEpilogue); }
-        mbar_init(fin, 1);
+        for (int s = 0; s < kStages; ++s) { mbar_init(&full[s], kProducers); mbar_init(&empty[s], kIssuers); }
+        for (int d = 0; d < 2; ++d) { mbar_init(&dfull[d], kIssuers); mbar_init(&dempty[d], kEpilogue); }
+        mbar_init(fin, kIssuers);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -317,7 +320,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract_tc(Params P) {
         const int half = e >> 2;                   // tiles 2 half, 2 half + 1
         const int row = 32 * quarter + lane;
         const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
-        const bool issuer = (warp == kMmaWarp);
+        const int iidx = warp - kMmaWarp;
+        const bool issuer = iidx < kIssuers;
         float acc[2][kNCols];
 #pragma unroll
         for (int u = 0; u < 2; ++u)
@@ -369,7 +373,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract_tc(Params P) {
                 if (!mbar_wait(&full[s], (uint32_t)((c / kStages) & 1), abort_flag, P.err, 0)) { mma_ok = false; return; }
                 tc_fence_after();
                 const uint32_t bh = bstage0 + s * BSTAGE, bl = bh + 2048;
-                for (int t = 0; t < P.ntiles; ++t) {
+                for (int t = iidx; t < P.ntiles; t += kIssuers) {
                     const uint32_t dcol = tmem + 128u * d + 32u * t;
                     const uint32_t ah = A0 + 128u * s + 32u * t, al = ah + 16u;
 #pragma unroll
