@@ -99,6 +99,62 @@ int polybin_mode_counts(const polybin_ctx* ctx, double* counts);
  * polybin_pk (continuous normalisation).  Either output may be NULL to skip that statistic. */
 int polybin_bk_pk_ideal(polybin_ctx* ctx, const float* delta, int batch, double* bk_out, double* pk_out);
 
+/* ---- masked ("unwindowed") estimators, global line of sight ------------------------------------------------
+ * Data model (Sec. 2.3, eqs. data-model, pointing; pixel window m = 1, no noise): d = n delta with background
+ * density n(x) (the pointing matrix P = n).  Weighting S^-1 = w(x) (Sec. 2.4), e.g. FKP w = 1 / (1 + n P_FKP).
+ * Fields n, w, d and mocks are float32 DEVICE arrays [N0][N1][N2] owned by the caller.  Monte Carlo maps are
+ * unit Gaussian white noise (A = I) from Philox4x32-10 + Box-Muller: map `draw` of `stream` holds at flat cell
+ * i the value z_{i mod 4} of Philox block j = i / 4 with key (seed mod 2^32, seed / 2^32) and counter
+ * (j mod 2^32, j / 2^32, draw, stream); z0, z1 = sqrt(-2 ln u0) (cos, sin)(2 pi u1), z2, z3 likewise from
+ * u2, u3, u_q = (x_q + 1/2) 2^-32.  Streams 0 and 1 give the bispectrum Fisher pairs (a1, a2), stream 2 the
+ * power-spectrum Fisher draws.  Parameter index alpha: power spectrum (ell, b) ell-major, index
+ * (ell / 2) * n_kbins + b; bispectrum the closed triplets in polybin_get_triplets order. */
+
+enum { POLYBIN_FISHER_PK = 0, POLYBIN_FISHER_BK = 1 };
+
+/* w = 1 / (n P_FKP + 1) (Sec. 2.4, eq. Sinv-fkp), evaluated in FP64 and stored as float32 (device arrays). */
+int polybin_fkp_weights(polybin_ctx* ctx, const float* n_dev, double p_fkp, float* w_dev);
+
+/* The Monte Carlo map `draw` of `stream` (float32 device array [N]), as defined above. */
+int polybin_mc_draw(polybin_ctx* ctx, unsigned long long seed, int draw, int stream, float* out_dev);
+
+/* Monte Carlo Fisher matrix averaged over draws 0 .. n_mc-1 and its FP64 inverse (LU with partial pivoting on the
+ * GPU), cached in the context for polybin_pk_unwindowed / polybin_bk_unwindowed.
+ *   which = POLYBIN_FISHER_PK: F_ab = 1/2 <(P^T S^-T Q_a[S^-1 P a]) . Q^asym_b[a]> (Sec. 3.3.2, eq. fish-from-Q);
+ *   which = POLYBIN_FISHER_BK: F_ab = 1/24 <(Q_a[S^-1 P a1] - Q_a[S^-1 P a2]) . S^-1 P . (Q_b[a1] - Q_b[a2])>
+ *                              (Sec. 4.3.4, eqs. bk-fish-def, Q-bis-global), pixel units.
+ * fisher_out, fisher_inv_out: host [n_alpha][n_alpha] row major, may be NULL.  checkpoint_path (may be NULL): the
+ * running FP64 sum is saved after every draw and a matching file is resumed from (same grid, bins, mode, seed and
+ * mask; the result is bit-identical to an uninterrupted run); a corrupted or mismatched file gives POLYBIN_EINVAL. */
+int polybin_fisher(polybin_ctx* ctx, const float* n_dev, const float* w_dev, int n_mc, unsigned long long seed,
+                   int which, double* fisher_out, double* fisher_inv_out, const char* checkpoint_path);
+
+/* The per-draw Fisher terms of draws draw_begin .. draw_end-1 (host [draw_end - draw_begin][n_alpha][n_alpha]); the
+ * mean over all draws is the Fisher matrix.  Independent replicas can each compute a range of draws. */
+int polybin_fisher_draws(polybin_ctx* ctx, const float* n_dev, const float* w_dev, unsigned long long seed, int which,
+                         int draw_begin, int draw_end, double* per_draw_out);
+
+/* Install a Fisher matrix computed elsewhere (host [n_alpha][n_alpha]); its inverse is computed in FP64 on the GPU. */
+int polybin_set_fisher(polybin_ctx* ctx, int which, const double* fisher);
+
+/* Unwindowed P_ell (Sec. 3.2, eq. pk-estimator-def; no bias term in this data model):
+ * p_num_alpha = 1/2 (1/N) sum_{k in b} L_ell |FT[w d]|^2 (pixel units), p = F^-1 p_num, pk_out = p V / N
+ * (host [n_alpha]; needs polybin_fisher(POLYBIN_FISHER_PK) or polybin_set_fisher first, may be NULL).
+ * pnum_out: host [n_alpha] or NULL. */
+int polybin_pk_unwindowed(polybin_ctx* ctx, const float* d_dev, const float* w_dev, double* pk_out, double* pnum_out);
+
+/* Unwindowed bispectrum (Sec. 4.2, eq. bk-estimator-def, with the numerator of eq. b-numerator-practical):
+ * b_num_abc = (S_abc[w d] - lin_abc) / Delta_abc, lin_abc = mean over the n_mocks mocks of
+ * sum_x (g_a[u] g_b[v] g_c[v] + g_a[v] g_b[u] g_c[v] + g_a[v] g_b[v] g_c[u]), u = w d, v = w mock;
+ * b = F^-1 b_num, bk_out = b (V/N)^2 (host [n_triplets]; needs the BK Fisher, may be NULL).  mocks_dev: device
+ * [n_mocks][N] or NULL when n_mocks = 0.  bnum_out, lin_out: host [n_triplets] or NULL. */
+int polybin_bk_unwindowed(polybin_ctx* ctx, const float* d_dev, const float* w_dev, const float* mocks_dev, int n_mocks,
+                          double* bk_out, double* bnum_out, double* lin_out);
+
+/* X = A^-1 B in FP64 on the GPU (dense LU with partial pivoting).  A: host [n][n], B, X: host [n][nrhs], row major.
+ * POLYBIN_EINVAL if A is exactly singular. */
+int polybin_solve(polybin_ctx* ctx, const double* A, int n, const double* B, int nrhs, double* X);
+
 /* ---- instrumentation -------------------------------------------------------------------------------------- */
 
 /* Enable (on != 0) or disable per-stage timing.  When enabled, each pipeline stage is bracketed by CUDA events on

@@ -44,7 +44,22 @@ _SIGS = {
     "polybin_set_profiling": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "polybin_get_stage_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "polybin_launch_count": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong)]),
+    "polybin_fkp_weights": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p]),
+    "polybin_mc_draw": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_ulonglong, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
+    "polybin_fisher": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_ulonglong,
+                                      ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_char_p]),
+    "polybin_fisher_draws": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_ulonglong,
+                                            ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
+    "polybin_set_fisher": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "polybin_pk_unwindowed": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p]),
+    "polybin_bk_unwindowed": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "polybin_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                     ctypes.c_void_p]),
 }
+
+FISHER_PK, FISHER_BK = 0, 1
 
 STAGES = ("forward", "shells", "contract", "pk_bin")
 
@@ -183,6 +198,73 @@ class PolyBin:
         n = ctypes.c_longlong()
         self._check(self.lib.polybin_launch_count(self.ctx, ctypes.byref(n)), "polybin_launch_count")
         return n.value
+
+    # ---- masked estimators
+    def n_alpha(self, which: int) -> int:
+        return (self.lmax // 2 + 1) * self.nb if which == FISHER_PK else self.num_triplets()
+
+    def fkp_weights(self, n_dev, p_fkp: float):
+        import torch
+        w = torch.empty_like(n_dev, dtype=torch.float32)
+        self._check(self.lib.polybin_fkp_weights(self.ctx, _ptr(_f32(n_dev)), float(p_fkp), _ptr(w)),
+                    "polybin_fkp_weights")
+        return w
+
+    def mc_draw(self, seed: int, draw: int, stream: int, device="cuda"):
+        import torch
+        out = torch.empty(self.grid, dtype=torch.float32, device=device)
+        self._check(self.lib.polybin_mc_draw(self.ctx, int(seed), int(draw), int(stream), _ptr(out)), "polybin_mc_draw")
+        return out
+
+    def fisher(self, n_dev, w_dev, n_mc: int, seed: int, which: int, checkpoint: str | None = None):
+        na = self.n_alpha(which)
+        F = np.zeros((na, na))
+        Finv = np.zeros((na, na))
+        ck = checkpoint.encode() if checkpoint else None
+        self._check(self.lib.polybin_fisher(self.ctx, _ptr(_f32(n_dev)), _ptr(_f32(w_dev)), int(n_mc), int(seed),
+                                            int(which), _ptr(F), _ptr(Finv), ck), "polybin_fisher")
+        return F, Finv
+
+    def fisher_draws(self, n_dev, w_dev, seed: int, which: int, r0: int, r1: int):
+        na = self.n_alpha(which)
+        out = np.zeros((r1 - r0, na, na))
+        self._check(self.lib.polybin_fisher_draws(self.ctx, _ptr(_f32(n_dev)), _ptr(_f32(w_dev)), int(seed), int(which),
+                                                  int(r0), int(r1), _ptr(out)), "polybin_fisher_draws")
+        return out
+
+    def set_fisher(self, which: int, F):
+        F = np.ascontiguousarray(F, dtype=np.float64)
+        self._check(self.lib.polybin_set_fisher(self.ctx, int(which), _ptr(F)), "polybin_set_fisher")
+
+    def pk_unwindowed(self, d_dev, w_dev, with_estimate: bool = True):
+        na = self.n_alpha(FISHER_PK)
+        p = np.zeros(na)
+        pnum = np.zeros(na)
+        self._check(self.lib.polybin_pk_unwindowed(self.ctx, _ptr(_f32(d_dev)), _ptr(_f32(w_dev)),
+                                                   _ptr(p) if with_estimate else None, _ptr(pnum)),
+                    "polybin_pk_unwindowed")
+        return (p if with_estimate else None), pnum
+
+    def bk_unwindowed(self, d_dev, w_dev, mocks_dev=None, with_estimate: bool = True):
+        nt = self.num_triplets()
+        b = np.zeros(nt)
+        bnum = np.zeros(nt)
+        lin = np.zeros(nt)
+        nm = 0 if mocks_dev is None else int(mocks_dev.shape[0])
+        self._check(self.lib.polybin_bk_unwindowed(self.ctx, _ptr(_f32(d_dev)), _ptr(_f32(w_dev)),
+                                                   None if mocks_dev is None else _ptr(_f32(mocks_dev)), nm,
+                                                   _ptr(b) if with_estimate else None, _ptr(bnum), _ptr(lin)),
+                    "polybin_bk_unwindowed")
+        return (b if with_estimate else None), bnum, lin
+
+    def solve(self, A, B):
+        A = np.ascontiguousarray(A, dtype=np.float64)
+        B = np.ascontiguousarray(B, dtype=np.float64)
+        B2 = B.reshape(B.shape[0], -1)
+        X = np.zeros_like(B2)
+        self._check(self.lib.polybin_solve(self.ctx, _ptr(A), A.shape[0], _ptr(B2), B2.shape[1], _ptr(X)),
+                    "polybin_solve")
+        return X.reshape(B.shape)
 
     def mode_counts(self) -> np.ndarray:
         out = np.zeros(self.nb, dtype=np.float64)

@@ -91,8 +91,8 @@ template <> const double2* twiddles<double>(polybin_ctx* ctx, int axis) { return
 // ----------------------------------------------------------------------------------------------- pipelines
 
 // a1: pruned forward transform of one real field (optionally times m1 * m2) into the box.
-template <typename T>
-int run_forward(polybin_ctx* ctx, const float* in, const float* m1, const float* m2, C<T>* t1, C<T>* t2, C<T>* box) {
+template <typename T, typename TIN, typename TM>
+int run_forward(polybin_ctx* ctx, const TIN* in, const TM* m1, const TM* m2, C<T>* t1, C<T>* t2, C<T>* box) {
     const int N0 = ctx->N[0], N1 = ctx->N[1], N2 = ctx->N[2];
     const int Bz = ctx->gz.cnt, By = ctx->gy.cnt;
     const long nlines = (long)N0 * N1;
@@ -101,9 +101,9 @@ int run_forward(polybin_ctx* ctx, const float* in, const float* m1, const float*
     {
         const int LP = lines_per_cta<T>(N2);
         const size_t sm = 2 * (size_t)N2 * (LP + 1) * sizeof(C<T>);
-        if ((rc = set_smem<T>(ctx, (const void*)k_fwd_z<T, float>, sm))) return rc;
+        if ((rc = set_smem<T>(ctx, (const void*)k_fwd_z<T, TIN, TM>, sm))) return rc;
         const unsigned nblk = (unsigned)((nlines + 2 * LP - 1) / (2 * LP));
-        k_fwd_z<T, float><<<nblk, 256, sm, ctx->stream>>>(in, m1, m2, t1, nlines, Bz, ctx->plan[2], twiddles<T>(ctx, 2), LP);
+        k_fwd_z<T, TIN, TM><<<nblk, 256, sm, ctx->stream>>>(in, m1, m2, t1, nlines, Bz, ctx->plan[2], twiddles<T>(ctx, 2), LP);
         if ((rc = launch_check(ctx, "k_fwd_z"))) return rc;
     }
     {
@@ -136,9 +136,9 @@ int run_forward(polybin_ctx* ctx, const float* in, const float* m1, const float*
     return POLYBIN_OK;
 }
 
-// a2: shell maps g_b = IFT[Theta_b D] for all bins (box == nullptr: unit spectrum, giving t_b).
+// a2: shell maps g_b = IFT[Theta_b L_ell D] for all bins (box == nullptr: unit spectrum, giving t_b).
 template <typename T>
-int run_shells(polybin_ctx* ctx, const C<T>* box, C<T>* u1, C<T>* u2, T* g) {
+int run_shells(polybin_ctx* ctx, const C<T>* box, C<T>* u1, C<T>* u2, T* g, int ell) {
     const int N0 = ctx->N[0], N1 = ctx->N[1], N2 = ctx->N[2];
     const int nb = ctx->nb;
     int rc;
@@ -154,6 +154,7 @@ int run_shells(polybin_ctx* ctx, const C<T>* box, C<T>* u1, C<T>* u2, T* g) {
             b.it[i].out = u1 + bb.u1_off;
             b.it[i].rx = bb.rx; b.it[i].ry = bb.ry; b.it[i].rz = bb.rz;
             b.it[i].bin = i;
+            b.it[i].ell = ell;
             maxcols = std::max(maxcols, bb.ry.cnt * bb.rz.cnt);
         }
         dim3 grid((maxcols + TK - 1) / TK, nb, 1);
@@ -255,10 +256,14 @@ int run_pkbin(polybin_ctx* ctx, const C<T>* box, std::vector<double>& num) {
     return POLYBIN_OK;
 }
 
-template int run_forward<float>(polybin_ctx*, const float*, const float*, const float*, float2*, float2*, float2*);
-template int run_forward<double>(polybin_ctx*, const float*, const float*, const float*, double2*, double2*, double2*);
-template int run_shells<float>(polybin_ctx*, const float2*, float2*, float2*, float*);
-template int run_shells<double>(polybin_ctx*, const double2*, double2*, double2*, double*);
+template int run_forward<float, float, float>(polybin_ctx*, const float*, const float*, const float*, float2*, float2*, float2*);
+template int run_forward<double, float, float>(polybin_ctx*, const float*, const float*, const float*, double2*, double2*, double2*);
+template int run_forward<double, double, double>(polybin_ctx*, const double*, const double*, const double*, double2*, double2*, double2*);
+template int run_forward<double, double, float>(polybin_ctx*, const double*, const float*, const float*, double2*, double2*, double2*);
+template int run_pkbin<float>(polybin_ctx*, const float2*, std::vector<double>&);
+template int run_pkbin<double>(polybin_ctx*, const double2*, std::vector<double>&);
+template int run_shells<float>(polybin_ctx*, const float2*, float2*, float2*, float*, int);
+template int run_shells<double>(polybin_ctx*, const double2*, double2*, double2*, double*, int);
 template int run_contract<float>(polybin_ctx*, const float*, int, const float*, int, double*, size_t, double*);
 template int run_contract<double>(polybin_ctx*, const double*, int, const double*, int, double*, size_t, double*);
 
@@ -448,7 +453,7 @@ int ensure_triplets(polybin_ctx* ctx) {
         if ((rc = alloc_work_shells_double(ctx, tmp))) { free_work(tmp); return rc; }
         w = &tmp;
     }
-    rc = run_shells<double>(ctx, nullptr, (double2*)w->u1, (double2*)w->u2, (double*)w->g);
+    rc = run_shells<double>(ctx, nullptr, (double2*)w->u1, (double2*)w->u2, (double*)w->g, 0);
     if (!rc) rc = run_contract<double>(ctx, (const double*)w->g, ctx->nb, nullptr, ctx->nb, w->partial, w->partial_cap, w->mout);
     const int nb = ctx->nb, np = nb * (nb + 1) / 2;
     std::vector<double> T((size_t)np * nb);
@@ -614,13 +619,13 @@ static int bk_pk_t(polybin_ctx* ctx, const float* delta, int batch, double* bk_o
         const float* in;
         if ((rc = resolve_input(ctx, delta + (size_t)f * ctx->ncell, ctx->ncell, &in))) return rc;
         Work& w = ctx->w;
-        if ((rc = run_forward<T>(ctx, in, nullptr, nullptr, (C<T>*)w.t1, (C<T>*)w.t2, (C<T>*)w.box))) return rc;
+        if ((rc = run_forward<T, float, float>(ctx, in, (const float*)nullptr, (const float*)nullptr, (C<T>*)w.t1, (C<T>*)w.t2, (C<T>*)w.box))) return rc;
         if (pk_out) {
             if ((rc = run_pkbin<T>(ctx, (const C<T>*)w.box, num))) return rc;
             pk_normalise(ctx, num, pk_out + (size_t)f * ctx->nell * nb);
         }
         if (!bk_out) continue;
-        if ((rc = run_shells<T>(ctx, (const C<T>*)w.box, (C<T>*)w.u1, (C<T>*)w.u2, (T*)w.g))) return rc;
+        if ((rc = run_shells<T>(ctx, (const C<T>*)w.box, (C<T>*)w.u1, (C<T>*)w.u2, (T*)w.g, 0))) return rc;
         if ((rc = run_contract_any<T>(ctx, (const T*)w.g, nb, nullptr, nb, w.partial, w.partial_cap, w.mout))) return rc;
         PB_CUDA_OK(cudaMemcpyAsync(M.data(), w.mout, sizeof(double) * M.size(), cudaMemcpyDeviceToHost, ctx->stream));
         PB_CUDA_OK(cudaStreamSynchronize(ctx->stream));
@@ -644,8 +649,8 @@ static int bk_ideal_t(polybin_ctx* ctx, const float* delta, int batch, double* b
         const float* in;
         if ((rc = resolve_input(ctx, delta + (size_t)f * ctx->ncell, ctx->ncell, &in))) return rc;
         Work& w = ctx->w;
-        if ((rc = run_forward<T>(ctx, in, nullptr, nullptr, (C<T>*)w.t1, (C<T>*)w.t2, (C<T>*)w.box))) return rc;
-        if ((rc = run_shells<T>(ctx, (const C<T>*)w.box, (C<T>*)w.u1, (C<T>*)w.u2, (T*)w.g))) return rc;
+        if ((rc = run_forward<T, float, float>(ctx, in, (const float*)nullptr, (const float*)nullptr, (C<T>*)w.t1, (C<T>*)w.t2, (C<T>*)w.box))) return rc;
+        if ((rc = run_shells<T>(ctx, (const C<T>*)w.box, (C<T>*)w.u1, (C<T>*)w.u2, (T*)w.g, 0))) return rc;
         if ((rc = run_contract_any<T>(ctx, (const T*)w.g, nb, nullptr, nb, w.partial, w.partial_cap, w.mout))) return rc;
         PB_CUDA_OK(cudaMemcpyAsync(M.data(), w.mout, sizeof(double) * M.size(), cudaMemcpyDeviceToHost, ctx->stream));
         PB_CUDA_OK(cudaStreamSynchronize(ctx->stream));
@@ -675,7 +680,7 @@ static int pk_t(polybin_ctx* ctx, const float* delta, int batch, bool discrete, 
         const float* in;
         if ((rc = resolve_input(ctx, delta + (size_t)f * ctx->ncell, ctx->ncell, &in))) return rc;
         Work& w = ctx->w;
-        if ((rc = run_forward<T>(ctx, in, nullptr, nullptr, (C<T>*)w.t1, (C<T>*)w.t2, (C<T>*)w.box))) return rc;
+        if ((rc = run_forward<T, float, float>(ctx, in, (const float*)nullptr, (const float*)nullptr, (C<T>*)w.t1, (C<T>*)w.t2, (C<T>*)w.box))) return rc;
         if ((rc = run_pkbin<T>(ctx, (const C<T>*)w.box, num))) return rc;
         double* o = pk_out + (size_t)f * nell * nb;
         const double N = (double)ctx->ncell;
@@ -726,9 +731,9 @@ extern "C" int polybin_forward(polybin_ctx* ctx, const float* delta, void* spec_
     int rc;
     Work& w = ctx->w;
     if (ctx->prec == POLYBIN_FP64)
-        rc = run_forward<double>(ctx, delta, nullptr, nullptr, (double2*)w.t1, (double2*)w.t2, (double2*)spec_out);
+        rc = run_forward<double, float, float>(ctx, delta, (const float*)nullptr, (const float*)nullptr, (double2*)w.t1, (double2*)w.t2, (double2*)spec_out);
     else
-        rc = run_forward<float>(ctx, delta, nullptr, nullptr, (float2*)w.t1, (float2*)w.t2, (float2*)spec_out);
+        rc = run_forward<float, float, float>(ctx, delta, (const float*)nullptr, (const float*)nullptr, (float2*)w.t1, (float2*)w.t2, (float2*)spec_out);
     if (rc) return rc;
     PB_CUDA_OK(cudaStreamSynchronize(ctx->stream));
     return POLYBIN_OK;
@@ -739,9 +744,9 @@ extern "C" int polybin_shell_maps(polybin_ctx* ctx, const void* spec, void* g_ou
     int rc;
     Work& w = ctx->w;
     if (ctx->prec == POLYBIN_FP64)
-        rc = run_shells<double>(ctx, (const double2*)spec, (double2*)w.u1, (double2*)w.u2, (double*)g_out);
+        rc = run_shells<double>(ctx, (const double2*)spec, (double2*)w.u1, (double2*)w.u2, (double*)g_out, 0);
     else
-        rc = run_shells<float>(ctx, (const float2*)spec, (float2*)w.u1, (float2*)w.u2, (float*)g_out);
+        rc = run_shells<float>(ctx, (const float2*)spec, (float2*)w.u1, (float2*)w.u2, (float*)g_out, 0);
     if (rc) return rc;
     PB_CUDA_OK(cudaStreamSynchronize(ctx->stream));
     return POLYBIN_OK;

@@ -4,6 +4,7 @@
 namespace pb {
 
 void destroy_extras(polybin_ctx* ctx) {
+    destroy_unwindowed(ctx);
     if (ctx->d_err) cudaFree(ctx->d_err);
     ctx->d_err = nullptr;
 }

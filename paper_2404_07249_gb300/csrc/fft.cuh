@@ -150,9 +150,9 @@ __device__ C<T>* fft_lines(C<T>* src, C<T>* dst, int L, int ES, const FftPlan& p
 // z-pass, forward: pairs of real lines (lines 2p, 2p+1 of the flattened (x, y) index) packed as one
 // complex line, transformed, then split into the two Hermitian half-spectra; only kz < kout is stored.
 // Optional pointwise multipliers m1, m2 (same layout as the input) are applied on load.
-template <typename T, typename TIN>
-__global__ void __launch_bounds__(256) k_fwd_z(const TIN* __restrict__ in, const TIN* __restrict__ m1,
-                                               const TIN* __restrict__ m2, C<T>* __restrict__ out, long nlines,
+template <typename T, typename TIN, typename TM>
+__global__ void __launch_bounds__(256) k_fwd_z(const TIN* __restrict__ in, const TM* __restrict__ m1,
+                                               const TM* __restrict__ m2, C<T>* __restrict__ out, long nlines,
                                                int kout, FftPlan plan, const C<T>* __restrict__ tw, int LP) {
     extern __shared__ unsigned char smem_raw[];
     const int n = plan.n;
@@ -315,6 +315,7 @@ struct XInvItem {
     void* out;            // C<T>* [n0][ry.cnt * rz.cnt]
     AxisRange rx, ry, rz; // bin bounding box
     int bin;
+    int ell;              // Legendre weight L_ell(mu), mu = n_z / |n| (0: none)
 };
 struct XInvBatch {
     XInvItem it[kMaxItems];
@@ -347,10 +348,15 @@ __global__ void __launch_bounds__(256) k_inv_x_filter(XInvBatch batch, const C<T
         const int fx = item.rx.lo + i;
         const int s = fx * fx + fy * fy + fz * fz;
         if (s > smax || lut[s] != item.bin) continue;
-        C<T> v = mk<T>(scale, T(0));
+        T wgt = scale;
+        if (item.ell) {
+            const T mu2 = T(fz * fz) / T(s);
+            wgt *= item.ell == 2 ? T(0.5) * (T(3) * mu2 - T(1)) : (T(35) * mu2 * mu2 - T(30) * mu2 + T(3)) / T(8);
+        }
+        C<T> v = mk<T>(wgt, T(0));
         if (spec) {
             const C<T> d = spec[(long)(fx - gx.lo) * gyz + (long)(fy - gy.lo) * gz.cnt + (fz - gz.lo)];
-            v = mk<T>(d.x * scale, d.y * scale);
+            v = mk<T>(d.x * wgt, d.y * wgt);
         }
         b0[c + pos_of(fx, n) * TK] = v;
     }

@@ -65,8 +65,10 @@ inline bool solve_small(double A[3][4], int n, double* x) {
 
 ContractGeom contract_geom(int nb, int nh, long ncell);
 
-template <typename T> int run_forward(polybin_ctx*, const float*, const float*, const float*, C<T>*, C<T>*, C<T>*);
-template <typename T> int run_shells(polybin_ctx*, const C<T>*, C<T>*, C<T>*, T*);
+template <typename T, typename TIN, typename TM>
+int run_forward(polybin_ctx*, const TIN*, const TM*, const TM*, C<T>*, C<T>*, C<T>*);
+template <typename T> int run_shells(polybin_ctx*, const C<T>*, C<T>*, C<T>*, T*, int ell);
+template <typename T> int run_pkbin(polybin_ctx*, const C<T>*, std::vector<double>&);
 template <typename T> int run_contract(polybin_ctx*, const T*, int, const T*, int, double*, size_t, double*);
 // Contraction dispatch: the tensor-core kernel in POLYBIN_SPLIT_TF32X3 mode, the SIMT kernel otherwise.
 template <typename T> int run_contract_any(polybin_ctx*, const T*, int, const T*, int, double*, size_t, double*);
@@ -79,6 +81,7 @@ bool split_tc_available();
 ContractGeom contract_geom_tc(int ng, int nh, long ncell);
 int run_contract_tc(polybin_ctx*, const float*, int, const float*, int, double*, size_t, double*);
 void destroy_extras(polybin_ctx*);
+void destroy_unwindowed(polybin_ctx*);
 
 }  // namespace pb
 

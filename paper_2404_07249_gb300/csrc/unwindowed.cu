@@ -1,0 +1,889 @@
+// Masked ("unwindowed") estimators with a global line of sight: FKP weighting (Sec. 2.4, eq. Sinv-fkp), the
+// power-spectrum numerator and Monte Carlo Fisher matrix (Sec. 3.3, eqs. pk-num-fft, Q-alpha-global,
+// fish-from-Q), the bispectrum numerator with its Monte Carlo linear term (Sec. 4.3.2, eq.
+// b-numerator-practical), the bispectrum Q-derivatives and Monte Carlo Fisher matrix (Sec. 4.3.4, eqs.
+// Q-bis-global, bk-fish-def) and the FP64 solves x = F^-1 x_num (eqs. pk-estimator-def, bk-estimator-def).
+//
+// Data model: d = n delta (pixel window m = 1, no noise); S^-1 = w (diagonal); S^-1 P = w n.  Monte Carlo maps
+// are unit Gaussian white noise (A = I) from Philox4x32-10 + Box-Muller (Salmon et al., SC'11), generated on
+// the device with the same counter layout as the test oracle: map `draw` of `stream` has at flat cell i the
+// value z_{i mod 4} of block j = i / 4, key = (seed lo, seed hi), counter = (j lo, j hi, draw, stream).
+// Streams: 0, 1 = the pair (a1, a2) of the bispectrum Fisher; 2 = the power-spectrum Fisher draws.
+// Everything is in pixel units (cell volume 1); physical units: P = p V / N, B = b (V / N)^2.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "polybin_internal.h"
+
+namespace pb {
+namespace uw {
+
+// ---------------------------------------------------------------------------------------------- kernels
+
+// w = 1 / (n P_FKP + 1), evaluated in FP64 and stored in the working precision.
+template <typename T>
+__global__ void k_fkp(const float* __restrict__ n, double p0, T* __restrict__ w, long N) {
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x)
+        w[i] = (T)(1.0 / ((double)n[i] * p0 + 1.0));
+}
+
+__device__ __forceinline__ void philox_round(uint32_t& c0, uint32_t& c1, uint32_t& c2, uint32_t& c3, uint32_t k0,
+                                             uint32_t k1) {
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t hi0 = __umulhi(M0, c0), lo0 = M0 * c0;
+    const uint32_t hi1 = __umulhi(M1, c2), lo1 = M1 * c2;
+    const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+}
+
+// Gaussian white-noise map (Philox4x32-10 + Box-Muller in FP64).
+template <typename T>
+__global__ void k_draw(T* __restrict__ out, long N, unsigned long long seed, uint32_t draw, uint32_t stream) {
+    const long nblk = (N + 3) / 4;
+    for (long j = (long)blockIdx.x * blockDim.x + threadIdx.x; j < nblk; j += (long)gridDim.x * blockDim.x) {
+        uint32_t c0 = (uint32_t)j, c1 = (uint32_t)((unsigned long long)j >> 32), c2 = draw, c3 = stream;
+        uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+#pragma unroll
+        for (int r = 0; r < 10; ++r) {
+            if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+            philox_round(c0, c1, c2, c3, k0, k1);
+        }
+        const double t = 2.3283064365386963e-10;  // 2^-32
+        const double u0 = ((double)c0 + 0.5) * t, u1 = ((double)c1 + 0.5) * t;
+        const double u2 = ((double)c2 + 0.5) * t, u3 = ((double)c3 + 0.5) * t;
+        const double r01 = sqrt(-2.0 * log(u0)), r23 = sqrt(-2.0 * log(u2));
+        double s1, co1, s3, co3;
+        sincospi(2.0 * u1, &s1, &co1);
+        sincospi(2.0 * u3, &s3, &co3);
+        const double z[4] = {r01 * co1, r01 * s1, r23 * co3, r23 * s3};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const long i = 4 * j + q;
+            if (i < N) out[i] = (T)z[q];
+        }
+    }
+}
+
+// Binned cross products over the half spectrum: out[b][seg][ell] = sum_{modes m of bin b} coef_ell(m) Re(conj X A).
+template <typename T>
+__global__ void __launch_bounds__(256) k_cross_bin(const C<T>* __restrict__ X, const C<T>* __restrict__ A,
+                                                   const int* __restrict__ offs, const double* __restrict__ coef,
+                                                   long nmodes_total, const int* __restrict__ bin_start, int nell,
+                                                   int seg_len, double* __restrict__ partial) {
+    __shared__ double red[256 * 3];
+    const int b = blockIdx.x, seg = blockIdx.y;
+    const long beg = bin_start[b] + (long)seg * seg_len;
+    const long end = min((long)bin_start[b + 1], beg + seg_len);
+    double s[3] = {0.0, 0.0, 0.0};
+    for (long m = beg + threadIdx.x; m < end; m += blockDim.x) {
+        const C<T> x = X[offs[m]], a = A[offs[m]];
+        const double p = (double)x.x * (double)a.x + (double)x.y * (double)a.y;
+        for (int l = 0; l < nell; ++l) s[l] += coef[(long)l * nmodes_total + m] * p;
+    }
+    for (int l = 0; l < 3; ++l) red[l * 256 + threadIdx.x] = s[l];
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int l = 0; l < 3; ++l) red[l * 256 + threadIdx.x] += red[l * 256 + threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < nell) partial[((long)b * gridDim.y + seg) * nell + threadIdx.x] = red[threadIdx.x * 256];
+}
+
+// Q-derivative spectrum of one triplet (a, b, c) from the pair spectra of two fields (eq. Q-bis-global):
+//   out(k) = fac [ Theta_c (P1_ab - P2_ab) + Theta_a (P1_bc - P2_bc) + Theta_b (P1_ac - P2_ac) ](k),
+// fac = 2 / Delta_abc, over every entry of the box (zero outside bins a, b, c).
+template <typename T>
+__global__ void k_qcomb(const C<T>* __restrict__ P1, const C<T>* __restrict__ P2, long pab, long pbc, long pac,
+                        int a, int b, int c, T fac, AxisRange gx, AxisRange gy, AxisRange gz,
+                        const int16_t* __restrict__ lut, int smax, C<T>* __restrict__ out) {
+    const long nbox = (long)gx.cnt * gy.cnt * gz.cnt;
+    for (long o = (long)blockIdx.x * blockDim.x + threadIdx.x; o < nbox; o += (long)gridDim.x * blockDim.x) {
+        const int iz = (int)(o % gz.cnt);
+        const long r = o / gz.cnt;
+        const int iy = (int)(r % gy.cnt), ix = (int)(r / gy.cnt);
+        const int fx = gx.lo + ix, fy = gy.lo + iy, fz = gz.lo + iz;
+        const int s = fx * fx + fy * fy + fz * fz;
+        const int bin = (s <= smax) ? lut[s] : -1;
+        T re = T(0), im = T(0);
+        if (bin >= 0) {
+            if (bin == c) { const C<T> u = P1[pab + o], v = P2[pab + o]; re += u.x - v.x; im += u.y - v.y; }
+            if (bin == a) { const C<T> u = P1[pbc + o], v = P2[pbc + o]; re += u.x - v.x; im += u.y - v.y; }
+            if (bin == b) { const C<T> u = P1[pac + o], v = P2[pac + o]; re += u.x - v.x; im += u.y - v.y; }
+        }
+        out[o] = mk<T>(fac * re, fac * im);
+    }
+}
+
+// Compact copy of the binned modes of a box spectrum: out[m] = box[offs[m]].
+template <typename T>
+__global__ void k_gather(const C<T>* __restrict__ box, const int* __restrict__ offs, long M, C<T>* __restrict__ out) {
+    for (long m = (long)blockIdx.x * blockDim.x + threadIdx.x; m < M; m += (long)gridDim.x * blockDim.x)
+        out[m] = box[offs[m]];
+}
+
+// out[i][j] += scale * sum_m w_m Re(conj(Z[i][m]) Y[j][m])   (FP64 accumulation; 32 x 32 tile per CTA).
+template <typename T>
+__global__ void __launch_bounds__(256) k_gram(const C<T>* __restrict__ Z, const C<T>* __restrict__ Y,
+                                              const double* __restrict__ wm, int nA, int nB, long M, double scale,
+                                              double* __restrict__ out) {
+    __shared__ double sz[32][65];   // 64 used (re, im interleaved) + 1 pad: conflict-free row access
+    __shared__ double sy[32][65];
+    const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+    const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;   // ty in [0, 8): 4 rows each
+    double acc[4] = {0, 0, 0, 0};
+    for (long m0 = 0; m0 < M; m0 += 32) {
+        for (int q = threadIdx.x; q < 32 * 32; q += 256) {
+            const int r = q / 32, k = q % 32;
+            const long m = m0 + k;
+            C<T> z = mk<T>(T(0), T(0)), y = mk<T>(T(0), T(0));
+            double wk = 0.0;
+            if (m < M) {
+                wk = wm[m];
+                if (i0 + r < nA) z = Z[(long)(i0 + r) * M + m];
+                if (j0 + r < nB) y = Y[(long)(j0 + r) * M + m];
+            }
+            sz[r][2 * k] = wk * (double)z.x;
+            sz[r][2 * k + 1] = wk * (double)z.y;
+            sy[r][2 * k] = (double)y.x;
+            sy[r][2 * k + 1] = (double)y.y;
+        }
+        __syncthreads();
+        for (int k = 0; k < 64; ++k) {
+            const double yv = sy[tx][k];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[u] += sz[ty * 4 + u][k] * yv;
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int i = i0 + ty * 4 + u, j = j0 + tx;
+        if (i < nA && j < nB) out[(long)i * nB + j] += scale * acc[u];
+    }
+}
+
+// Dense FP64 LU with partial pivoting and solve, one CTA: A (n x n, row major) is overwritten by its factors,
+// B (n x nrhs, row major) by the solution.  info = 0, or k + 1 if the pivot of column k is exactly zero.
+__global__ void __launch_bounds__(1024) k_lu_solve(double* __restrict__ A, int n, double* __restrict__ B, int nrhs,
+                                                   int* __restrict__ info) {
+    __shared__ double sval[1024];
+    __shared__ int sidx[1024];
+    __shared__ int piv;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (tid == 0) *info = 0;
+    for (int k = 0; k < n; ++k) {
+        double best = -1.0;
+        int bi = k;
+        for (int i = k + tid; i < n; i += nt) {
+            const double v = fabs(A[(long)i * n + k]);
+            if (v > best) { best = v; bi = i; }
+        }
+        sval[tid] = best;
+        sidx[tid] = bi;
+        __syncthreads();
+        for (int w = nt / 2; w > 0; w >>= 1) {
+            if (tid < w && (sval[tid + w] > sval[tid] || (sval[tid + w] == sval[tid] && sidx[tid + w] < sidx[tid]))) {
+                sval[tid] = sval[tid + w];
+                sidx[tid] = sidx[tid + w];
+            }
+            __syncthreads();
+        }
+        if (tid == 0) {
+            piv = sidx[0];
+            if (sval[0] == 0.0 && *info == 0) *info = k + 1;
+        }
+        __syncthreads();
+        const int p = piv;
+        if (p != k) {
+            for (int j = tid; j < n; j += nt) {
+                const double t = A[(long)k * n + j]; A[(long)k * n + j] = A[(long)p * n + j]; A[(long)p * n + j] = t;
+            }
+            for (int j = tid; j < nrhs; j += nt) {
+                const double t = B[(long)k * nrhs + j]; B[(long)k * nrhs + j] = B[(long)p * nrhs + j]; B[(long)p * nrhs + j] = t;
+            }
+        }
+        __syncthreads();
+        const double d = A[(long)k * n + k];
+        if (d != 0.0)
+            for (int i = k + 1 + tid; i < n; i += nt) A[(long)i * n + k] /= d;
+        __syncthreads();
+        const int rows = n - k - 1, cols = n - k - 1;
+        for (long q = tid; q < (long)rows * cols; q += nt) {
+            const int i = k + 1 + (int)(q / cols), j = k + 1 + (int)(q % cols);
+            A[(long)i * n + j] -= A[(long)i * n + k] * A[(long)k * n + j];
+        }
+        for (long q = tid; q < (long)rows * nrhs; q += nt) {
+            const int i = k + 1 + (int)(q / nrhs), j = (int)(q % nrhs);
+            B[(long)i * nrhs + j] -= A[(long)i * n + k] * B[(long)k * nrhs + j];
+        }
+        __syncthreads();
+    }
+    // back substitution U x = y, column by column of the right-hand sides
+    for (int k = n - 1; k >= 0; --k) {
+        const double d = A[(long)k * n + k];
+        for (int j = tid; j < nrhs; j += nt) B[(long)k * nrhs + j] = d != 0.0 ? B[(long)k * nrhs + j] / d : NAN;
+        __syncthreads();
+        for (long q = tid; q < (long)k * nrhs; q += nt) {
+            const int i = (int)(q / nrhs), j = (int)(q % nrhs);
+            B[(long)i * nrhs + j] -= A[(long)i * n + k] * B[(long)k * nrhs + j];
+        }
+        __syncthreads();
+    }
+}
+
+// y = M x (FP64), M n x n row major.
+__global__ void k_gemv(const double* __restrict__ M, const double* __restrict__ x, int n, double* __restrict__ y) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = 0.0;
+    for (int j = 0; j < n; ++j) s += M[(long)i * n + j] * x[j];
+    y[i] = s;
+}
+
+}  // namespace uw
+
+// ---------------------------------------------------------------------------------------------- state
+
+struct UwState {
+    size_t elem = 0;
+    void* g2 = nullptr;       // second set of shell maps [nb][N]
+    void* xmap = nullptr;     // one real map [N]
+    void* a[2] = {nullptr, nullptr};  // Monte Carlo maps
+    void* spec[4] = {nullptr, nullptr, nullptr, nullptr};  // box spectra
+    void* pairs = nullptr;    // pair spectra [4][npairs][box]
+    void* qbox = nullptr;     // one box spectrum
+    void* zc = nullptr;       // compact [nt][M]
+    void* yc = nullptr;       // compact [nt][M]
+    void* v1 = nullptr;       // inverse-from-box intermediates [N0][By][Bz]
+    void* v2 = nullptr;       //                                [N0][N1][Bz]
+    double* dF = nullptr;     // device Fisher accumulator
+    double* dpart = nullptr;  // cross-bin partials
+    double* dvec = nullptr;
+    double* dvec2 = nullptr;
+    int* dinfo = nullptr;
+    std::vector<double> Fp, Fb, Fp_inv, Fb_inv;   // host copies
+    double* dFp_inv = nullptr;
+    double* dFb_inv = nullptr;
+    bool have_p = false, have_b = false;
+};
+
+static void uw_free(UwState* u) {
+    if (!u) return;
+    void* ptrs[] = {u->g2, u->xmap, u->a[0], u->a[1], u->spec[0], u->spec[1], u->spec[2], u->spec[3], u->pairs, u->qbox,
+                    u->zc, u->yc, u->v1, u->v2, u->dF, u->dpart, u->dvec, u->dvec2, u->dinfo, u->dFp_inv, u->dFb_inv};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete u;
+}
+
+void destroy_unwindowed(polybin_ctx* ctx) {
+    uw_free(static_cast<UwState*>(ctx->ext));
+    ctx->ext = nullptr;
+}
+
+template <typename T>
+static int uw_alloc(polybin_ctx* ctx, bool need_b) {
+    UwState* u = static_cast<UwState*>(ctx->ext);
+    if (!u) {
+        u = new (std::nothrow) UwState();
+        if (!u) return fail(ctx, POLYBIN_ENOMEM, "unwindowed: out of host memory");
+        ctx->ext = u;
+        u->elem = sizeof(T);
+    }
+    const long N = ctx->ncell;
+    const long nbox = (long)ctx->gx.cnt * ctx->gy.cnt * ctx->gz.cnt;
+    const int nb = ctx->nb, np = nb * (nb + 1) / 2;
+    auto need = [&](void** p, size_t bytes) -> int {
+        if (*p) return POLYBIN_OK;
+        cudaError_t e = cudaMalloc(p, bytes);
+        if (e != cudaSuccess) { *p = nullptr; return fail_cuda(ctx, e, "unwindowed workspace", __FILE__, __LINE__); }
+        return POLYBIN_OK;
+    };
+    int rc;
+    if ((rc = need(&u->xmap, sizeof(T) * N))) return rc;
+    if ((rc = need(&u->a[0], sizeof(T) * N))) return rc;
+    if ((rc = need(&u->a[1], sizeof(T) * N))) return rc;
+    for (int f = 0; f < 4; ++f)
+        if ((rc = need(&u->spec[f], sizeof(C<T>) * nbox))) return rc;
+    if ((rc = need(&u->g2, sizeof(T) * (size_t)nb * N))) return rc;
+    if ((rc = need((void**)&u->dpart, sizeof(double) * (size_t)nb * ctx->pk_nseg * 3))) return rc;
+    if ((rc = need((void**)&u->dinfo, sizeof(int)))) return rc;
+    if ((rc = need((void**)&u->dvec, sizeof(double) * 4096))) return rc;
+    if ((rc = need((void**)&u->dvec2, sizeof(double) * 4096))) return rc;
+    if (need_b) {
+        const size_t nt = ctx->Nabc.size();
+        if ((rc = need(&u->pairs, sizeof(C<T>) * (size_t)4 * np * nbox))) return rc;
+        if ((rc = need(&u->qbox, sizeof(C<T>) * nbox))) return rc;
+        if ((rc = need(&u->zc, sizeof(C<T>) * nt * std::max(ctx->nmodes, 1L)))) return rc;
+        if ((rc = need(&u->yc, sizeof(C<T>) * nt * std::max(ctx->nmodes, 1L)))) return rc;
+        if ((rc = need(&u->v1, sizeof(C<T>) * (size_t)ctx->N[0] * ctx->gy.cnt * ctx->gz.cnt))) return rc;
+        if ((rc = need(&u->v2, sizeof(C<T>) * (size_t)ctx->N[0] * ctx->N[1] * ctx->gz.cnt))) return rc;
+    }
+    return POLYBIN_OK;
+}
+
+static unsigned grid1d(long n) { return (unsigned)std::min<long>((n + 255) / 256, 152L * 16); }
+
+// Inverse transform of a box spectrum to a real map: x-pass, y-pass, z-pass (C2R) with the 1/N of the IFT,
+// and an optional pointwise multiplier on output.
+template <typename T>
+static int run_inverse_box(polybin_ctx* ctx, const C<T>* box, C<T>* v1, C<T>* v2, T* out, const T* mulout) {
+    const int N0 = ctx->N[0], N1 = ctx->N[1], N2 = ctx->N[2];
+    const int By = ctx->gy.cnt, Bz = ctx->gz.cnt;
+    int rc;
+    {
+        int tk = 16;
+        while (tk > 1 && 2 * (size_t)N0 * tk * sizeof(C<T>) > 64 * 1024) tk >>= 1;
+        const size_t sm = 2 * (size_t)N0 * tk * sizeof(C<T>);
+        cudaError_t e = cudaFuncSetAttribute((const void*)k_col<T, +1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return fail_cuda(ctx, e, "attr", __FILE__, __LINE__);
+        ColBatch b;
+        ColItem& it = b.it[0];
+        const int ncols = By * Bz;
+        it.in = box; it.out = v1;
+        it.in_os = 0; it.in_es = ncols; it.out_os = 0; it.out_es = ncols;
+        it.ncols = ncols; it.nouter = 1; it.rng = ctx->gx;
+        k_col<T, +1><<<dim3((ncols + tk - 1) / tk, 1, 1), 256, sm, ctx->stream>>>(b, ctx->plan[0],
+            (const C<T>*)(sizeof(T) == 4 ? ctx->d_tw_f[0] : ctx->d_tw_d[0]), tk);
+        ctx->launches++;
+    }
+    {
+        int tk = 16;
+        while (tk > 1 && 2 * (size_t)N1 * tk * sizeof(C<T>) > 64 * 1024) tk >>= 1;
+        const size_t sm = 2 * (size_t)N1 * tk * sizeof(C<T>);
+        cudaError_t e = cudaFuncSetAttribute((const void*)k_col<T, +1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return fail_cuda(ctx, e, "attr", __FILE__, __LINE__);
+        ColBatch b;
+        ColItem& it = b.it[0];
+        it.in = v1; it.out = v2;
+        it.in_os = (long)By * Bz; it.in_es = Bz; it.out_os = (long)N1 * Bz; it.out_es = Bz;
+        it.ncols = Bz; it.nouter = N0; it.rng = ctx->gy;
+        k_col<T, +1><<<dim3((Bz + tk - 1) / tk, N0, 1), 256, sm, ctx->stream>>>(b, ctx->plan[1],
+            (const C<T>*)(sizeof(T) == 4 ? ctx->d_tw_f[1] : ctx->d_tw_d[1]), tk);
+        ctx->launches++;
+    }
+    {
+        int lp = 16;
+        while (lp > 1 && 2 * (size_t)N2 * (lp + 1) * sizeof(C<T>) > 96 * 1024) lp >>= 1;
+        const size_t sm = 2 * (size_t)N2 * (lp + 1) * sizeof(C<T>);
+        cudaError_t e = cudaFuncSetAttribute((const void*)k_inv_z<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return fail_cuda(ctx, e, "attr", __FILE__, __LINE__);
+        ZInvBatch b;
+        b.it[0].in = v2; b.it[0].out = out; b.it[0].kin = Bz;
+        const long nlines = (long)N0 * N1;
+        k_inv_z<T><<<dim3((unsigned)((nlines + 2 * lp - 1) / (2 * lp)), 1, 1), 256, sm, ctx->stream>>>(
+            b, nlines, T(1.0 / (double)ctx->ncell), mulout, ctx->plan[2],
+            (const C<T>*)(sizeof(T) == 4 ? ctx->d_tw_f[2] : ctx->d_tw_d[2]), lp);
+        ctx->launches++;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail_cuda(ctx, e, "run_inverse_box", __FILE__, __LINE__);
+    (void)rc;
+    return POLYBIN_OK;
+}
+
+// Binned cross products (host result [nell][nb]) of two box spectra.
+template <typename T>
+static int run_cross_bin(polybin_ctx* ctx, const C<T>* X, const C<T>* A, double* dpart, std::vector<double>& out) {
+    const int nb = ctx->nb, nell = ctx->nell;
+    uw::k_cross_bin<T><<<dim3(nb, ctx->pk_nseg, 1), 256, 0, ctx->stream>>>(X, A, ctx->d_offs, ctx->d_coef, ctx->nmodes,
+                                                                            ctx->d_bin_start, nell, ctx->pk_seg_len, dpart);
+    ctx->launches++;
+    std::vector<double> part((size_t)nb * ctx->pk_nseg * nell);
+    PB_CUDA_OK(cudaGetLastError());
+    PB_CUDA_OK(cudaMemcpyAsync(part.data(), dpart, part.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    PB_CUDA_OK(cudaStreamSynchronize(ctx->stream));
+    out.assign((size_t)nell * nb, 0.0);
+    for (int b = 0; b < nb; ++b)
+        for (int s = 0; s < ctx->pk_nseg; ++s)
+            for (int l = 0; l < nell; ++l) out[(size_t)l * nb + b] += part[((size_t)b * ctx->pk_nseg + s) * nell + l];
+    return POLYBIN_OK;
+}
+
+// ---------------------------------------------------------------------------------------------- P Fisher
+
+// One Monte Carlo term of the P Fisher matrix (eq. fish-from-Q, global line of sight), host [na][na], na = nell*nb:
+// F[(l,b)][(l',b')] = 1/2 (1/N) sum_k conj(FT[s IFT[Theta_b L_l FT[s a]]]) Theta_b' L_l' FT[a],  s = w n.
+template <typename T>
+static int pk_fisher_draw(polybin_ctx* ctx, const float* n, const float* w, unsigned long long seed, int r,
+                          std::vector<double>& F) {
+    UwState* u = static_cast<UwState*>(ctx->ext);
+    Work& W = ctx->w;
+    const long N = ctx->ncell;
+    const int nb = ctx->nb, nell = ctx->nell, na = nell * nb;
+    int rc;
+    T* a = (T*)u->a[0];
+    uw::k_draw<T><<<grid1d((N + 3) / 4), 256, 0, ctx->stream>>>(a, N, seed, (uint32_t)r, 2u);
+    ctx->launches++;
+    C<T>* A = (C<T>*)u->spec[0];
+    C<T>* SA = (C<T>*)u->spec[1];
+    if ((rc = run_forward<T, T, float>(ctx, a, (const float*)nullptr, (const float*)nullptr, (C<T>*)W.t1, (C<T>*)W.t2, A))) return rc;
+    if ((rc = run_forward<T, T, float>(ctx, a, w, n, (C<T>*)W.t1, (C<T>*)W.t2, SA))) return rc;
+    F.assign((size_t)na * na, 0.0);
+    std::vector<double> cross;
+    T* q = (T*)u->g2;
+    for (int il = 0; il < nell; ++il) {
+        if ((rc = run_shells<T>(ctx, SA, (C<T>*)W.u1, (C<T>*)W.u2, q, 2 * il))) return rc;
+        for (int b = 0; b < nb; ++b) {
+            C<T>* X = (C<T>*)u->spec[2];
+            if ((rc = run_forward<T, T, float>(ctx, q + (size_t)b * N, w, n, (C<T>*)W.t1, (C<T>*)W.t2, X))) return rc;
+            if ((rc = run_cross_bin<T>(ctx, X, A, u->dpart, cross))) return rc;
+            const int alpha = il * nb + b;
+            for (int jl = 0; jl < nell; ++jl)
+                for (int b2 = 0; b2 < nb; ++b2) F[(size_t)alpha * na + jl * nb + b2] = 0.5 * cross[(size_t)jl * nb + b2] / (double)N;
+        }
+    }
+    return POLYBIN_OK;
+}
+
+// ---------------------------------------------------------------------------------------------- B Fisher
+
+// Pair spectra P_xy = FT[g_x g_y] (x <= y, lexicographic) of the shell maps of one box spectrum.
+template <typename T>
+static int pair_spectra(polybin_ctx* ctx, const C<T>* U, C<T>* out) {
+    UwState* u = static_cast<UwState*>(ctx->ext);
+    Work& W = ctx->w;
+    const long N = ctx->ncell;
+    const long nbox = (long)ctx->gx.cnt * ctx->gy.cnt * ctx->gz.cnt;
+    const int nb = ctx->nb;
+    int rc;
+    T* g = (T*)u->g2;
+    if ((rc = run_shells<T>(ctx, U, (C<T>*)W.u1, (C<T>*)W.u2, g, 0))) return rc;
+    int p = 0;
+    for (int x = 0; x < nb; ++x)
+        for (int y = x; y < nb; ++y, ++p)
+            if ((rc = run_forward<T, T, T>(ctx, g + (size_t)x * N, g + (size_t)y * N, (const T*)nullptr, (C<T>*)W.t1,
+                                           (C<T>*)W.t2, out + (size_t)p * nbox)))
+                return rc;
+    return POLYBIN_OK;
+}
+
+// One Monte Carlo term of the B Fisher matrix (eq. bk-fish-def, A = I), device accumulate into u->dF [nt][nt]:
+//   F_ab += (1/24) sum_x (Q_a[s a1] - Q_a[s a2]) s (Q_b[a1] - Q_b[a2]) = (1/24)(1/N) sum_k conj(Z_a) Y_b,
+// Z_a = FT[s IFT[Qt_a(s a1) - Qt_a(s a2)]], Y_b = Qt_b(a1) - Qt_b(a2), Qt from eq. Q-bis-global in k-space.
+template <typename T>
+static int bk_fisher_draw(polybin_ctx* ctx, const float* n, const float* w, unsigned long long seed, int r) {
+    UwState* u = static_cast<UwState*>(ctx->ext);
+    Work& W = ctx->w;
+    const long N = ctx->ncell;
+    const long nbox = (long)ctx->gx.cnt * ctx->gy.cnt * ctx->gz.cnt;
+    const int nb = ctx->nb, np = nb * (nb + 1) / 2;
+    const int nt = (int)ctx->Nabc.size();
+    const long M = ctx->nmodes;
+    int rc;
+    T* a1 = (T*)u->a[0];
+    T* a2 = (T*)u->a[1];
+    uw::k_draw<T><<<grid1d((N + 3) / 4), 256, 0, ctx->stream>>>(a1, N, seed, (uint32_t)r, 0u);
+    uw::k_draw<T><<<grid1d((N + 3) / 4), 256, 0, ctx->stream>>>(a2, N, seed, (uint32_t)r, 1u);
+    ctx->launches += 2;
+    // fields: 0 = s a1, 1 = s a2, 2 = a1, 3 = a2
+    const T* src[4] = {a1, a2, a1, a2};
+    C<T>* pairs = (C<T>*)u->pairs;
+    for (int f = 0; f < 4; ++f) {
+        const float* m1 = f < 2 ? w : nullptr;
+        const float* m2 = f < 2 ? n : nullptr;
+        if ((rc = run_forward<T, T, float>(ctx, src[f], m1, m2, (C<T>*)W.t1, (C<T>*)W.t2, (C<T>*)u->spec[f]))) return rc;
+        if ((rc = pair_spectra<T>(ctx, (const C<T>*)u->spec[f], pairs + (size_t)f * np * nbox))) return rc;
+    }
+    C<T>* Zc = (C<T>*)u->zc;
+    C<T>* Yc = (C<T>*)u->yc;
+    C<T>* q = (C<T>*)u->qbox;
+    for (int t = 0; t < nt; ++t) {
+        const int a = ctx->trip[3 * t], b = ctx->trip[3 * t + 1], c = ctx->trip[3 * t + 2];
+        const double dl = (a == b && b == c) ? 6.0 : ((a == b || b == c) ? 2.0 : 1.0);
+        const long pab = (long)pair_index(nb, a, b) * nbox, pbc = (long)pair_index(nb, b, c) * nbox,
+                   pac = (long)pair_index(nb, a, c) * nbox;
+        // Y_b: fields a1, a2 (compact binned modes)
+        uw::k_qcomb<T><<<grid1d(nbox), 256, 0, ctx->stream>>>(pairs + (size_t)2 * np * nbox, pairs + (size_t)3 * np * nbox,
+                                                              pab, pbc, pac, a, b, c, T(2.0 / dl), ctx->gx, ctx->gy,
+                                                              ctx->gz, ctx->d_lut, ctx->smax, q);
+        uw::k_gather<T><<<grid1d(M), 256, 0, ctx->stream>>>(q, ctx->d_offs, M, Yc + (size_t)t * M);
+        // Z_a: fields s a1, s a2 -> real map -> times s -> forward -> compact
+        uw::k_qcomb<T><<<grid1d(nbox), 256, 0, ctx->stream>>>(pairs, pairs + (size_t)np * nbox, pab, pbc, pac, a, b, c,
+                                                              T(2.0 / dl), ctx->gx, ctx->gy, ctx->gz, ctx->d_lut,
+                                                              ctx->smax, q);
+        ctx->launches += 3;
+        if ((rc = run_inverse_box<T>(ctx, q, (C<T>*)u->v1, (C<T>*)u->v2, (T*)u->xmap, (const T*)nullptr))) return rc;
+        if ((rc = run_forward<T, T, float>(ctx, (const T*)u->xmap, w, n, (C<T>*)W.t1, (C<T>*)W.t2, q))) return rc;
+        uw::k_gather<T><<<grid1d(M), 256, 0, ctx->stream>>>(q, ctx->d_offs, M, Zc + (size_t)t * M);
+        ctx->launches++;
+    }
+    dim3 g((nt + 31) / 32, (nt + 31) / 32, 1);
+    uw::k_gram<T><<<g, 256, 0, ctx->stream>>>(Zc, Yc, ctx->d_coef, nt, nt, M, 1.0 / (24.0 * (double)N), u->dF);
+    ctx->launches++;
+    PB_CUDA_OK(cudaGetLastError());
+    return POLYBIN_OK;
+}
+
+// ---------------------------------------------------------------------------------------------- solve
+
+// X = A^-1 B in FP64 on the device (A n x n, B n x nrhs, host row major); optionally also A^-1.
+static int gpu_solve(polybin_ctx* ctx, const double* A, int n, const double* B, int nrhs, double* X) {
+    double *dA = nullptr, *dB = nullptr;
+    int* dinfo = nullptr;
+    int rc = POLYBIN_OK;
+    cudaError_t e = cudaMalloc(&dA, sizeof(double) * (size_t)n * n);
+    if (e == cudaSuccess) e = cudaMalloc(&dB, sizeof(double) * (size_t)n * nrhs);
+    if (e == cudaSuccess) e = cudaMalloc(&dinfo, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dA, A, sizeof(double) * (size_t)n * n, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dB, B, sizeof(double) * (size_t)n * nrhs, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) {
+        uw::k_lu_solve<<<1, 1024, 0, ctx->stream>>>(dA, n, dB, nrhs, dinfo);
+        ctx->launches++;
+        e = cudaGetLastError();
+    }
+    int info = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(X, dB, sizeof(double) * (size_t)n * nrhs, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&info, dinfo, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) rc = fail_cuda(ctx, e, "gpu_solve", __FILE__, __LINE__);
+    else if (info) rc = fail(ctx, POLYBIN_EINVAL, "solve: matrix is singular (zero pivot in column %d)", info - 1);
+    if (dA) cudaFree(dA);
+    if (dB) cudaFree(dB);
+    if (dinfo) cudaFree(dinfo);
+    return rc;
+}
+
+// ---------------------------------------------------------------------------------------------- checkpoint
+
+static uint64_t fnv1a(const void* p, size_t n, uint64_t h = 1469598103934665603ULL) {
+    const unsigned char* c = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < n; ++i) { h ^= c[i]; h *= 1099511628211ULL; }
+    return h;
+}
+
+struct CkptHeader {
+    char magic[8];
+    int32_t which, nalpha;
+    int64_t done;
+    uint64_t seed, setup_hash, mask_hash;
+};
+
+static uint64_t setup_hash(const polybin_ctx* ctx, int which) {
+    uint64_t h = fnv1a(ctx->N, sizeof(ctx->N));
+    h = fnv1a(ctx->edges.data(), sizeof(double) * ctx->edges.size(), h);
+    h = fnv1a(&ctx->L, sizeof(ctx->L), h);
+    h = fnv1a(&ctx->lmax, sizeof(ctx->lmax), h);
+    h = fnv1a(&which, sizeof(which), h);
+    h = fnv1a(&ctx->prec, sizeof(ctx->prec), h);
+    return h;
+}
+
+static int mask_hash(polybin_ctx* ctx, const float* n, const float* w, uint64_t* out) {
+    std::vector<float> hn(ctx->ncell), hw(ctx->ncell);
+    PB_CUDA_OK(cudaMemcpyAsync(hn.data(), n, sizeof(float) * ctx->ncell, cudaMemcpyDeviceToHost, ctx->stream));
+    PB_CUDA_OK(cudaMemcpyAsync(hw.data(), w, sizeof(float) * ctx->ncell, cudaMemcpyDeviceToHost, ctx->stream));
+    PB_CUDA_OK(cudaStreamSynchronize(ctx->stream));
+    *out = fnv1a(hw.data(), sizeof(float) * hw.size(), fnv1a(hn.data(), sizeof(float) * hn.size()));
+    return POLYBIN_OK;
+}
+
+// Returns POLYBIN_OK and fills sum/done if a matching checkpoint exists (done = 0 if there is none);
+// POLYBIN_EINVAL if the file exists but is corrupted or belongs to another setup.
+static int ckpt_load(polybin_ctx* ctx, const char* path, const CkptHeader& want, std::vector<double>& sum, int64_t* done) {
+    *done = 0;
+    FILE* f = fopen(path, "rb");
+    if (!f) return POLYBIN_OK;
+    CkptHeader h;
+    const size_t na2 = (size_t)want.nalpha * want.nalpha;
+    std::vector<double> data(na2);
+    uint64_t check = 0;
+    const bool ok = fread(&h, sizeof(h), 1, f) == 1 && fread(data.data(), sizeof(double), na2, f) == na2 &&
+                    fread(&check, sizeof(check), 1, f) == 1;
+    fclose(f);
+    if (!ok || memcmp(h.magic, "PBFISH01", 8) != 0 || check != fnv1a(data.data(), sizeof(double) * na2, fnv1a(&h, sizeof(h))))
+        return fail(ctx, POLYBIN_EINVAL, "checkpoint %s is corrupted", path);
+    if (h.which != want.which || h.nalpha != want.nalpha || h.seed != want.seed || h.setup_hash != want.setup_hash ||
+        h.mask_hash != want.mask_hash)
+        return fail(ctx, POLYBIN_EINVAL, "checkpoint %s belongs to a different setup (bins, mask, seed or mode)", path);
+    sum = data;
+    *done = h.done;
+    return POLYBIN_OK;
+}
+
+static int ckpt_save(polybin_ctx* ctx, const char* path, CkptHeader h, const std::vector<double>& sum) {
+    std::string tmp = std::string(path) + ".tmp";
+    FILE* f = fopen(tmp.c_str(), "wb");
+    if (!f) return fail(ctx, POLYBIN_EINVAL, "cannot write checkpoint %s", tmp.c_str());
+    const uint64_t check = fnv1a(sum.data(), sizeof(double) * sum.size(), fnv1a(&h, sizeof(h)));
+    const bool ok = fwrite(&h, sizeof(h), 1, f) == 1 && fwrite(sum.data(), sizeof(double), sum.size(), f) == sum.size() &&
+                    fwrite(&check, sizeof(check), 1, f) == 1;
+    fclose(f);
+    if (!ok || rename(tmp.c_str(), path) != 0) return fail(ctx, POLYBIN_EINVAL, "cannot write checkpoint %s", path);
+    return POLYBIN_OK;
+}
+
+// ---------------------------------------------------------------------------------------------- drivers
+
+template <typename T>
+static int fisher_sum(polybin_ctx* ctx, const float* n, const float* w, unsigned long long seed, int which, int r0, int r1,
+                      std::vector<double>& sum, double* per_draw) {
+    UwState* u = static_cast<UwState*>(ctx->ext);
+    int rc;
+    const int na = which == 0 ? ctx->nell * ctx->nb : (int)ctx->Nabc.size();
+    if (sum.size() != (size_t)na * na) sum.assign((size_t)na * na, 0.0);
+    std::vector<double> F;
+    for (int r = r0; r < r1; ++r) {
+        if (which == 0) {
+            if ((rc = pk_fisher_draw<T>(ctx, n, w, seed, r, F))) return rc;
+        } else {
+            if (!u->dF) {
+                cudaError_t e = cudaMalloc(&u->dF, sizeof(double) * (size_t)na * na);
+                if (e != cudaSuccess) return fail_cuda(ctx, e, "cudaMalloc Fisher", __FILE__, __LINE__);
+            }
+            PB_CUDA_OK(cudaMemsetAsync(u->dF, 0, sizeof(double) * (size_t)na * na, ctx->stream));
+            if ((rc = bk_fisher_draw<T>(ctx, n, w, seed, r))) return rc;
+            F.resize((size_t)na * na);
+            PB_CUDA_OK(cudaMemcpyAsync(F.data(), u->dF, sizeof(double) * F.size(), cudaMemcpyDeviceToHost, ctx->stream));
+            PB_CUDA_OK(cudaStreamSynchronize(ctx->stream));
+        }
+        for (size_t i = 0; i < F.size(); ++i) sum[i] += F[i];
+        if (per_draw) std::memcpy(per_draw + (size_t)(r - r0) * na * na, F.data(), sizeof(double) * F.size());
+    }
+    return POLYBIN_OK;
+}
+
+template <typename T>
+static int fisher_t(polybin_ctx* ctx, const float* n, const float* w, int n_mc, unsigned long long seed, int which,
+                    double* fisher_out, double* fisher_inv_out, const char* ckpt) {
+    int rc;
+    if (which == 1 && (rc = ensure_triplets(ctx))) return rc;
+    if ((rc = uw_alloc<T>(ctx, which == 1))) return rc;
+    UwState* u = static_cast<UwState*>(ctx->ext);
+    const int na = which == 0 ? ctx->nell * ctx->nb : (int)ctx->Nabc.size();
+    std::vector<double> sum((size_t)na * na, 0.0);
+    int64_t done = 0;
+    CkptHeader h;
+    memcpy(h.magic, "PBFISH01", 8);
+    h.which = which; h.nalpha = na; h.done = 0; h.seed = seed; h.setup_hash = setup_hash(ctx, which); h.mask_hash = 0;
+    if (ckpt) {
+        if ((rc = mask_hash(ctx, n, w, &h.mask_hash))) return rc;
+        if ((rc = ckpt_load(ctx, ckpt, h, sum, &done))) return rc;
+        if (done > n_mc) return fail(ctx, POLYBIN_EINVAL, "checkpoint holds %lld draws, more than n_mc = %d", (long long)done, n_mc);
+    }
+    for (int r = (int)done; r < n_mc; ++r) {
+        if ((rc = fisher_sum<T>(ctx, n, w, seed, which, r, r + 1, sum, nullptr))) return rc;
+        if (ckpt) {
+            h.done = r + 1;
+            if ((rc = ckpt_save(ctx, ckpt, h, sum))) return rc;
+        }
+    }
+    std::vector<double> F(sum.size());
+    for (size_t i = 0; i < F.size(); ++i) F[i] = sum[i] / (double)n_mc;
+    std::vector<double> I((size_t)na * na, 0.0), Finv((size_t)na * na);
+    for (int i = 0; i < na; ++i) I[(size_t)i * na + i] = 1.0;
+    if ((rc = gpu_solve(ctx, F.data(), na, I.data(), na, Finv.data()))) return rc;
+    if (fisher_out) std::memcpy(fisher_out, F.data(), sizeof(double) * F.size());
+    if (fisher_inv_out) std::memcpy(fisher_inv_out, Finv.data(), sizeof(double) * Finv.size());
+    double** dinv = which == 0 ? &u->dFp_inv : &u->dFb_inv;
+    if (!*dinv) {
+        cudaError_t e = cudaMalloc(dinv, sizeof(double) * (size_t)na * na);
+        if (e != cudaSuccess) return fail_cuda(ctx, e, "cudaMalloc Finv", __FILE__, __LINE__);
+    }
+    PB_CUDA_OK(cudaMemcpyAsync(*dinv, Finv.data(), sizeof(double) * Finv.size(), cudaMemcpyHostToDevice, ctx->stream));
+    PB_CUDA_OK(cudaStreamSynchronize(ctx->stream));
+    if (which == 0) { u->Fp = F; u->Fp_inv = Finv; u->have_p = true; }
+    else { u->Fb = F; u->Fb_inv = Finv; u->have_b = true; }
+    return POLYBIN_OK;
+}
+
+// x = F^-1 v on the device (FP64).
+static int apply_inverse(polybin_ctx* ctx, const double* dinv, int na, const std::vector<double>& v, std::vector<double>& x) {
+    UwState* u = static_cast<UwState*>(ctx->ext);
+    double *dv = u->dvec, *dx = u->dvec2;
+    double *tmpv = nullptr, *tmpx = nullptr;
+    if (na > 4096) {
+        PB_CUDA_OK(cudaMalloc(&tmpv, sizeof(double) * na));
+        PB_CUDA_OK(cudaMalloc(&tmpx, sizeof(double) * na));
+        dv = tmpv; dx = tmpx;
+    }
+    x.assign(na, 0.0);
+    PB_CUDA_OK(cudaMemcpyAsync(dv, v.data(), sizeof(double) * na, cudaMemcpyHostToDevice, ctx->stream));
+    uw::k_gemv<<<(na + 127) / 128, 128, 0, ctx->stream>>>(dinv, dv, na, dx);
+    ctx->launches++;
+    PB_CUDA_OK(cudaGetLastError());
+    PB_CUDA_OK(cudaMemcpyAsync(x.data(), dx, sizeof(double) * na, cudaMemcpyDeviceToHost, ctx->stream));
+    PB_CUDA_OK(cudaStreamSynchronize(ctx->stream));
+    if (tmpv) cudaFree(tmpv);
+    if (tmpx) cudaFree(tmpx);
+    return POLYBIN_OK;
+}
+
+template <typename T>
+static int pk_unwindowed_t(polybin_ctx* ctx, const float* d, const float* w, double* pk_out, double* pnum_out) {
+    int rc;
+    if ((rc = uw_alloc<T>(ctx, false))) return rc;
+    UwState* u = static_cast<UwState*>(ctx->ext);
+    Work& W = ctx->w;
+    const int nb = ctx->nb, na = ctx->nell * nb;
+    if ((rc = run_forward<T, float, float>(ctx, d, w, (const float*)nullptr, (C<T>*)W.t1, (C<T>*)W.t2, (C<T>*)W.box))) return rc;
+    std::vector<double> num;
+    if ((rc = run_pkbin<T>(ctx, (const C<T>*)W.box, num))) return rc;
+    std::vector<double> pnum(na);
+    for (int i = 0; i < na; ++i) pnum[i] = 0.5 * num[i] / (double)ctx->ncell;
+    if (pnum_out) std::memcpy(pnum_out, pnum.data(), sizeof(double) * na);
+    if (!pk_out) return POLYBIN_OK;
+    if (!u->have_p) return fail(ctx, POLYBIN_ENOTREADY, "polybin_pk_unwindowed: run polybin_fisher(POLYBIN_FISHER_PK) first");
+    std::vector<double> x;
+    if ((rc = apply_inverse(ctx, u->dFp_inv, na, pnum, x))) return rc;
+    for (int i = 0; i < na; ++i) pk_out[i] = x[i] * ctx->vol / (double)ctx->ncell;
+    return POLYBIN_OK;
+}
+
+template <typename T>
+static int bk_unwindowed_t(polybin_ctx* ctx, const float* d, const float* w, const float* mocks, int n_mocks,
+                           double* bk_out, double* bnum_out, double* lin_out) {
+    int rc;
+    if ((rc = ensure_triplets(ctx))) return rc;
+    if ((rc = uw_alloc<T>(ctx, false))) return rc;
+    UwState* u = static_cast<UwState*>(ctx->ext);
+    Work& W = ctx->w;
+    const long N = ctx->ncell;
+    const int nb = ctx->nb, np = nb * (nb + 1) / 2;
+    const int nt = (int)ctx->Nabc.size();
+    // u = w d -> g[u] (kept in W.g)
+    if ((rc = run_forward<T, float, float>(ctx, d, w, (const float*)nullptr, (C<T>*)W.t1, (C<T>*)W.t2, (C<T>*)W.box))) return rc;
+    if ((rc = run_shells<T>(ctx, (const C<T>*)W.box, (C<T>*)W.u1, (C<T>*)W.u2, (T*)W.g, 0))) return rc;
+    std::vector<double> S((size_t)np * nb), lin(nt, 0.0), Mv((size_t)np * nb);
+    if ((rc = run_contract_any<T>(ctx, (const T*)W.g, nb, nullptr, nb, W.partial, W.partial_cap, W.mout))) return rc;
+    PB_CUDA_OK(cudaMemcpyAsync(S.data(), W.mout, sizeof(double) * S.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    PB_CUDA_OK(cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i < n_mocks; ++i) {
+        const float* mock = mocks + (size_t)i * N;
+        if ((rc = run_forward<T, float, float>(ctx, mock, w, (const float*)nullptr, (C<T>*)W.t1, (C<T>*)W.t2, (C<T>*)W.box))) return rc;
+        if ((rc = run_shells<T>(ctx, (const C<T>*)W.box, (C<T>*)W.u1, (C<T>*)W.u2, (T*)u->g2, 0))) return rc;
+        // M[(j<=k) over v][i over u] = sum_x g_j[v] g_k[v] g_i[u]
+        if ((rc = run_contract_any<T>(ctx, (const T*)u->g2, nb, (const T*)W.g, nb, W.partial, W.partial_cap, W.mout))) return rc;
+        PB_CUDA_OK(cudaMemcpyAsync(Mv.data(), W.mout, sizeof(double) * Mv.size(), cudaMemcpyDeviceToHost, ctx->stream));
+        PB_CUDA_OK(cudaStreamSynchronize(ctx->stream));
+        for (int t = 0; t < nt; ++t) {
+            const int a = ctx->trip[3 * t], b = ctx->trip[3 * t + 1], c = ctx->trip[3 * t + 2];
+            lin[t] += Mv[(size_t)pair_index(nb, b, c) * nb + a] + Mv[(size_t)pair_index(nb, a, c) * nb + b] +
+                      Mv[(size_t)pair_index(nb, a, b) * nb + c];
+        }
+    }
+    std::vector<double> bnum(nt);
+    for (int t = 0; t < nt; ++t) {
+        const int a = ctx->trip[3 * t], b = ctx->trip[3 * t + 1], c = ctx->trip[3 * t + 2];
+        const double dl = (a == b && b == c) ? 6.0 : ((a == b || b == c) ? 2.0 : 1.0);
+        if (n_mocks > 0) lin[t] /= n_mocks;
+        bnum[t] = (S[(size_t)pair_index(nb, a, b) * nb + c] - lin[t]) / dl;
+    }
+    if (bnum_out) std::memcpy(bnum_out, bnum.data(), sizeof(double) * nt);
+    if (lin_out) std::memcpy(lin_out, lin.data(), sizeof(double) * nt);
+    if (!bk_out) return POLYBIN_OK;
+    if (!u->have_b) return fail(ctx, POLYBIN_ENOTREADY, "polybin_bk_unwindowed: run polybin_fisher(POLYBIN_FISHER_BK) first");
+    std::vector<double> x;
+    if ((rc = apply_inverse(ctx, u->dFb_inv, nt, bnum, x))) return rc;
+    const double v2 = (ctx->vol / (double)N) * (ctx->vol / (double)N);
+    for (int t = 0; t < nt; ++t) bk_out[t] = x[t] * v2;
+    return POLYBIN_OK;
+}
+
+}  // namespace pb
+
+using namespace pb;
+
+static bool is_device_ptr(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) { cudaGetLastError(); return false; }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+extern "C" int polybin_fkp_weights(polybin_ctx* ctx, const float* n_dev, double p_fkp, float* w_dev) {
+    if (!ctx || !n_dev || !w_dev) return fail(ctx, POLYBIN_EINVAL, "polybin_fkp_weights: NULL argument");
+    if (!is_device_ptr(n_dev) || !is_device_ptr(w_dev)) return fail(ctx, POLYBIN_EINVAL, "polybin_fkp_weights: device pointers required");
+    uw::k_fkp<float><<<grid1d(ctx->ncell), 256, 0, ctx->stream>>>(n_dev, p_fkp, w_dev, ctx->ncell);
+    ctx->launches++;
+    PB_CUDA_OK(cudaGetLastError());
+    PB_CUDA_OK(cudaStreamSynchronize(ctx->stream));
+    return POLYBIN_OK;
+}
+
+extern "C" int polybin_mc_draw(polybin_ctx* ctx, unsigned long long seed, int draw, int stream, float* out_dev) {
+    if (!ctx || !out_dev || draw < 0 || stream < 0) return fail(ctx, POLYBIN_EINVAL, "polybin_mc_draw: bad argument");
+    uw::k_draw<float><<<grid1d((ctx->ncell + 3) / 4), 256, 0, ctx->stream>>>(out_dev, ctx->ncell, seed, (uint32_t)draw, (uint32_t)stream);
+    ctx->launches++;
+    PB_CUDA_OK(cudaGetLastError());
+    PB_CUDA_OK(cudaStreamSynchronize(ctx->stream));
+    return POLYBIN_OK;
+}
+
+static int check_uw_args(polybin_ctx* ctx, const float* a, const float* b, const char* what) {
+    if (!ctx || !a || !b) return fail(ctx, POLYBIN_EINVAL, "%s: NULL argument", what);
+    if (!is_device_ptr(a) || !is_device_ptr(b)) return fail(ctx, POLYBIN_EINVAL, "%s: device pointers required", what);
+    return POLYBIN_OK;
+}
+
+extern "C" int polybin_fisher(polybin_ctx* ctx, const float* n_dev, const float* w_dev, int n_mc, unsigned long long seed,
+                              int which, double* fisher_out, double* fisher_inv_out, const char* checkpoint_path) {
+    int rc = check_uw_args(ctx, n_dev, w_dev, "polybin_fisher");
+    if (rc) return rc;
+    if (n_mc < 1 || (which != 0 && which != 1)) return fail(ctx, POLYBIN_EINVAL, "polybin_fisher: n_mc >= 1, which in {0, 1}");
+    return ctx->prec == POLYBIN_FP64 ? fisher_t<double>(ctx, n_dev, w_dev, n_mc, seed, which, fisher_out, fisher_inv_out, checkpoint_path)
+                                     : fisher_t<float>(ctx, n_dev, w_dev, n_mc, seed, which, fisher_out, fisher_inv_out, checkpoint_path);
+}
+
+extern "C" int polybin_fisher_draws(polybin_ctx* ctx, const float* n_dev, const float* w_dev, unsigned long long seed,
+                                    int which, int draw_begin, int draw_end, double* per_draw_out) {
+    int rc = check_uw_args(ctx, n_dev, w_dev, "polybin_fisher_draws");
+    if (rc) return rc;
+    if (!per_draw_out || draw_begin < 0 || draw_end < draw_begin || (which != 0 && which != 1))
+        return fail(ctx, POLYBIN_EINVAL, "polybin_fisher_draws: bad argument");
+    if (which == 1 && (rc = ensure_triplets(ctx))) return rc;
+    std::vector<double> sum;
+    if (ctx->prec == POLYBIN_FP64) {
+        if ((rc = uw_alloc<double>(ctx, which == 1))) return rc;
+        return fisher_sum<double>(ctx, n_dev, w_dev, seed, which, draw_begin, draw_end, sum, per_draw_out);
+    }
+    if ((rc = uw_alloc<float>(ctx, which == 1))) return rc;
+    return fisher_sum<float>(ctx, n_dev, w_dev, seed, which, draw_begin, draw_end, sum, per_draw_out);
+}
+
+extern "C" int polybin_set_fisher(polybin_ctx* ctx, int which, const double* fisher) {
+    if (!ctx || !fisher || (which != 0 && which != 1)) return fail(ctx, POLYBIN_EINVAL, "polybin_set_fisher: bad argument");
+    int rc;
+    if (which == 1 && (rc = ensure_triplets(ctx))) return rc;
+    if ((rc = ctx->prec == POLYBIN_FP64 ? uw_alloc<double>(ctx, false) : uw_alloc<float>(ctx, false))) return rc;
+    UwState* u = static_cast<UwState*>(ctx->ext);
+    const int na = which == 0 ? ctx->nell * ctx->nb : (int)ctx->Nabc.size();
+    std::vector<double> F(fisher, fisher + (size_t)na * na), I((size_t)na * na, 0.0), Finv((size_t)na * na);
+    for (int i = 0; i < na; ++i) I[(size_t)i * na + i] = 1.0;
+    if ((rc = gpu_solve(ctx, F.data(), na, I.data(), na, Finv.data()))) return rc;
+    double** dinv = which == 0 ? &u->dFp_inv : &u->dFb_inv;
+    if (!*dinv) PB_CUDA_OK(cudaMalloc(dinv, sizeof(double) * (size_t)na * na));
+    PB_CUDA_OK(cudaMemcpyAsync(*dinv, Finv.data(), sizeof(double) * Finv.size(), cudaMemcpyHostToDevice, ctx->stream));
+    PB_CUDA_OK(cudaStreamSynchronize(ctx->stream));
+    if (which == 0) { u->Fp = F; u->Fp_inv = Finv; u->have_p = true; }
+    else { u->Fb = F; u->Fb_inv = Finv; u->have_b = true; }
+    return POLYBIN_OK;
+}
+
+extern "C" int polybin_pk_unwindowed(polybin_ctx* ctx, const float* d_dev, const float* w_dev, double* pk_out, double* pnum_out) {
+    int rc = check_uw_args(ctx, d_dev, w_dev, "polybin_pk_unwindowed");
+    if (rc) return rc;
+    return ctx->prec == POLYBIN_FP64 ? pk_unwindowed_t<double>(ctx, d_dev, w_dev, pk_out, pnum_out)
+                                     : pk_unwindowed_t<float>(ctx, d_dev, w_dev, pk_out, pnum_out);
+}
+
+extern "C" int polybin_bk_unwindowed(polybin_ctx* ctx, const float* d_dev, const float* w_dev, const float* mocks_dev,
+                                     int n_mocks, double* bk_out, double* bnum_out, double* lin_out) {
+    int rc = check_uw_args(ctx, d_dev, w_dev, "polybin_bk_unwindowed");
+    if (rc) return rc;
+    if (n_mocks < 0 || (n_mocks > 0 && (!mocks_dev || !is_device_ptr(mocks_dev))))
+        return fail(ctx, POLYBIN_EINVAL, "polybin_bk_unwindowed: mocks must be device memory when n_mocks > 0");
+    return ctx->prec == POLYBIN_FP64 ? bk_unwindowed_t<double>(ctx, d_dev, w_dev, mocks_dev, n_mocks, bk_out, bnum_out, lin_out)
+                                     : bk_unwindowed_t<float>(ctx, d_dev, w_dev, mocks_dev, n_mocks, bk_out, bnum_out, lin_out);
+}
+
+extern "C" int polybin_solve(polybin_ctx* ctx, const double* A, int n, const double* B, int nrhs, double* X) {
+    if (!ctx || !A || !B || !X || n < 1 || nrhs < 1) return fail(ctx, POLYBIN_EINVAL, "polybin_solve: bad argument");
+    return gpu_solve(ctx, A, n, B, nrhs, X);
+}

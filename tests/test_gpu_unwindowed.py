@@ -1,0 +1,195 @@
+"""GPU parity of the masked (unwindowed) estimators against the FP64 oracle, through the C-ABI.
+
+Setup: a 32^3 periodic box with a survey-like mask (shell with holes), FKP weights, a few k-bins.  The oracle
+and the GPU read the same float32 fields (n, w, d, mocks) and the same Philox draws (the oracle rounds its FP64
+draws to float32, as the GPU stores them).  Tolerances: Fisher matrices within 1e-6 of sqrt(F_aa F_bb) (FP32
+FFTs); numerators within 1e-6 of the largest |value|; F^-1 solves within 1e-9 relative (FP64 LU).
+"""
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import binning, ideal, unwindowed
+from paper_2404_07249_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+GRID = (32, 32, 32)
+BOX = 600.0
+KF = binning.kf_of(BOX)
+BK_EDGES = KF * np.array([1.0, 3.0, 5.0, 7.0, 9.0])
+PK_EDGES = KF * np.array([0.0, 2.0, 4.0, 6.0, 8.0, 10.0])
+SEED = 20240407
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_2404_07249_gb300 as pkg
+    from paper_2404_07249_gb300 import build
+    build.build()
+    pkg.load()
+    return pkg
+
+
+@pytest.fixture(scope="module")
+def fields():
+    geom = synth.SurveyGeometry(r_min=60.0, r_max=290.0, n_holes=4, hole_radius=30.0, n0=3.0e-4, r0=180.0, s2=2.0e4)
+    n = synth.survey_mask(GRID, (BOX,) * 3, 5, geom).astype(np.float32)
+    w = unwindowed.fkp_weight(n, 1.0e4).astype(np.float32)
+    d = (n * synth.gaussian_field(GRID, (BOX,) * 3, 11)).astype(np.float32)
+    mocks = np.stack([(n * synth.gaussian_field(GRID, (BOX,) * 3, 100 + i)) for i in range(2)]).astype(np.float32)
+    return n, w, d, mocks
+
+
+def _dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def _fisher_close(G, R, tol):
+    dg = np.sqrt(np.abs(np.diag(R)))
+    scale = np.outer(dg, dg)
+    return np.max(np.abs(G - R) / scale)
+
+
+def test_fkp_weights_and_draws(pkg, fields):
+    n, w, d, _ = fields
+    pb = pkg.PolyBin(GRID, BOX, PK_EDGES, lmax=2, prec="fp32")
+    wg = pb.fkp_weights(_dev(n), 1.0e4).cpu().numpy()
+    assert np.array_equal(wg, w)
+    for stream in (0, 1, 2):
+        a = pb.mc_draw(SEED, 3, stream).cpu().numpy().ravel()
+        ref = unwindowed.draw(GRID, SEED, 3, stream, np.float32).ravel()
+        assert np.max(np.abs(a - ref)) < 1e-5
+        assert np.mean(a == ref) > 0.999
+    pb.close()
+
+
+def test_pk_numerator_and_fisher_draws(pkg, fields):
+    n, w, d, _ = fields
+    pb = pkg.PolyBin(GRID, BOX, PK_EDGES, lmax=2, prec="fp32")
+    nb = len(PK_EDGES) - 1
+    bins = binning.bin_grid(GRID, BOX, PK_EDGES)
+    mu2 = binning.mu2_grid(GRID)
+    _, pnum = pb.pk_unwindowed(_dev(d), _dev(w), with_estimate=False)
+    ref = unwindowed.pk_numerator(d, w, bins, mu2, nb, [0, 2]).ravel()
+    assert np.max(np.abs(pnum - ref)) / np.max(np.abs(ref)) < 1e-6
+    Fd = pb.fisher_draws(_dev(n), _dev(w), SEED, 0, 0, 2)
+    for r in range(2):
+        a = unwindowed.draw(GRID, SEED, r, unwindowed.STREAM_P, np.float32)
+        R = unwindowed.pk_fisher_draw(a, n, w, bins, mu2, nb, [0, 2])
+        assert _fisher_close(Fd[r], R, 1e-6) < 1e-6
+    pb.close()
+
+
+def test_bk_fisher_draw(pkg, fields):
+    n, w, d, _ = fields
+    pb = pkg.PolyBin(GRID, BOX, BK_EDGES, prec="split")
+    abc, _ = pb.triplets()
+    trip = [tuple(t) for t in abc.tolist()]
+    nb = len(BK_EDGES) - 1
+    bins = binning.bin_grid(GRID, BOX, BK_EDGES)
+    Fd = pb.fisher_draws(_dev(n), _dev(w), SEED, 1, 0, 1)[0]
+    a1 = unwindowed.draw(GRID, SEED, 0, unwindowed.STREAM_B1, np.float32)
+    a2 = unwindowed.draw(GRID, SEED, 0, unwindowed.STREAM_B2, np.float32)
+    R = unwindowed.bk_fisher_draw(a1, a2, n, w, bins, nb, trip)
+    assert _fisher_close(Fd, R, 1e-6) < 1e-6
+    pb.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "split", "fp64"])
+def test_bk_numerator_with_linear_term(pkg, fields, prec):
+    n, w, d, mocks = fields
+    pb = pkg.PolyBin(GRID, BOX, BK_EDGES, prec=prec)
+    abc, _ = pb.triplets()
+    trip = [tuple(t) for t in abc.tolist()]
+    nb = len(BK_EDGES) - 1
+    bins = binning.bin_grid(GRID, BOX, BK_EDGES)
+    _, bnum, lin = pb.bk_unwindowed(_dev(d), _dev(w), _dev(mocks), with_estimate=False)
+    ref = unwindowed.bk_numerator(d, w, list(mocks), bins, nb, trip)
+    tol = 1e-6 if prec != "fp64" else 1e-11
+    assert np.max(np.abs(lin - ref["lin"])) / np.max(np.abs(ref["lin"])) < tol
+    assert np.max(np.abs(bnum - ref["b_num"])) / np.max(np.abs(ref["b_num"])) < tol
+    pb.close()
+
+
+def test_gpu_solve_matches_lapack(pkg, fields):
+    pb = pkg.PolyBin(GRID, BOX, PK_EDGES, lmax=2, prec="fp32")
+    rng = np.random.Generator(np.random.PCG64(9))
+    for n_ in (7, 100, 321):
+        A = rng.standard_normal((n_, n_)) + n_ ** 0.5 * np.eye(n_)
+        B = rng.standard_normal((n_, 3))
+        X = pb.solve(A, B)
+        ref = np.linalg.solve(A, B)
+        assert np.max(np.abs(X - ref)) / np.max(np.abs(ref)) < 1e-9
+        assert np.max(np.abs(A @ X - B)) < 1e-9 * np.max(np.abs(B)) * n_
+    pb.close()
+
+
+def test_unwindowed_pk_end_to_end_and_checkpoint(pkg, fields):
+    n, w, d, _ = fields
+    nb = len(PK_EDGES) - 1
+    bins = binning.bin_grid(GRID, BOX, PK_EDGES)
+    mu2 = binning.mu2_grid(GRID)
+    pb = pkg.PolyBin(GRID, BOX, PK_EDGES, lmax=2, prec="fp32")
+    F, Finv = pb.fisher(_dev(n), _dev(w), 3, SEED, 0)
+    Fref = unwindowed.pk_fisher(n, w, bins, mu2, nb, [0, 2], SEED, 3, np.float32)
+    assert _fisher_close(F, Fref, 1e-6) < 1e-6
+    assert np.max(np.abs(Finv @ F - np.eye(len(F)))) < 1e-9
+    p, pnum = pb.pk_unwindowed(_dev(d), _dev(w))
+    pnum_ref = unwindowed.pk_numerator(d, w, bins, mu2, nb, [0, 2]).ravel()
+    p_ref = unwindowed.solve(Fref, pnum_ref) * BOX ** 3 / d.size
+    assert np.max(np.abs(p - p_ref)) / np.max(np.abs(p_ref)) < 1e-5
+    # checkpoint: 2 draws, then resume to 3 in a fresh context -> identical to the uninterrupted run
+    with tempfile.TemporaryDirectory() as td:
+        ck = os.path.join(td, "fisher.ckpt")
+        pb2 = pkg.PolyBin(GRID, BOX, PK_EDGES, lmax=2, prec="fp32")
+        pb2.fisher(_dev(n), _dev(w), 2, SEED, 0, checkpoint=ck)
+        pb2.close()
+        pb3 = pkg.PolyBin(GRID, BOX, PK_EDGES, lmax=2, prec="fp32")
+        F3, _ = pb3.fisher(_dev(n), _dev(w), 3, SEED, 0, checkpoint=ck)
+        assert np.array_equal(F3, F)
+        # a different seed must not resume from this file; a corrupted file is rejected
+        with pytest.raises(pkg.PolybinError):
+            pb3.fisher(_dev(n), _dev(w), 3, SEED + 1, 0, checkpoint=ck)
+        raw = bytearray(open(ck, "rb").read())
+        raw[100] ^= 0xFF
+        open(ck, "wb").write(bytes(raw))
+        with pytest.raises(pkg.PolybinError):
+            pb3.fisher(_dev(n), _dev(w), 3, SEED, 0, checkpoint=ck)
+        pb3.close()
+    pb.close()
+
+
+def test_unwindowed_bk_end_to_end(pkg, fields):
+    n, w, d, mocks = fields
+    nb = len(BK_EDGES) - 1
+    bins = binning.bin_grid(GRID, BOX, BK_EDGES)
+    pb = pkg.PolyBin(GRID, BOX, BK_EDGES, prec="split")
+    abc, _ = pb.triplets()
+    trip = [tuple(t) for t in abc.tolist()]
+    F, Finv = pb.fisher(_dev(n), _dev(w), 2, SEED, 1)
+    Fref = unwindowed.bk_fisher(n, w, bins, nb, trip, SEED, 2, np.float32)
+    assert _fisher_close(F, Fref, 1e-6) < 1e-6
+    b, bnum, _ = pb.bk_unwindowed(_dev(d), _dev(w), _dev(mocks))
+    ref = unwindowed.bk_numerator(d, w, list(mocks), bins, nb, trip)
+    b_ref = unwindowed.solve(Fref, ref["b_num"]) * (BOX ** 3 / d.size) ** 2
+    assert np.max(np.abs(b - b_ref)) / np.max(np.abs(b_ref)) < 1e-4
+    pb.close()
+
+
+def test_fisher_ideal_limit(pkg):
+    """n = w = 1: the Monte Carlo B Fisher is centred on the ideal diagonal N_abc / (N Delta)."""
+    pb = pkg.PolyBin(GRID, BOX, BK_EDGES, prec="split")
+    abc, nabc = pb.triplets()
+    one = torch.ones(GRID, device="cuda")
+    F, _ = pb.fisher(one, one, 4, SEED, 1)
+    N = np.prod(GRID)
+    dl = np.array([binning.degeneracy(*t) for t in abc.tolist()])
+    ideal_diag = nabc / (N * dl)
+    ratio = np.diag(F) / ideal_diag
+    assert abs(np.median(ratio) - 1.0) < 0.2, ratio
+    pb.close()
