@@ -191,6 +191,27 @@ int polybin_shell_maps(polybin_ctx* ctx, const void* spec, void* g_out);
  * polybin_shell_maps.  m_out: host [n_g (n_g + 1) / 2][n_h] doubles.  n_g, n_h <= 64. */
 int polybin_contract(polybin_ctx* ctx, const void* g, int n_g, const void* h, int n_h, double* m_out);
 
+/* ---- allocation-free contraction -----------------------------------------------------------------------------
+ * The paper has no counterpart to this entry point; it serves callers that cannot allocate device memory (code
+ * running inside a caller-managed memory pool or arena, plugins whose host application owns every allocation,
+ * threads that must not call cudaMalloc/cudaFree because those can synchronise the device).
+ * It computes the same M[p][i] = sum_x g_{j_p}(x) g_{k_p}(x) h_i(x) as polybin_contract (FP32 SIMT kernel) without a
+ * context and without allocating: its scratch (FP64 per-block partial sums and the pair table) is a fixed
+ * file-scope device array of 2^21 doubles (16 MiB) plus 8 KiB, held by every GPU that loads the library until the
+ * process exits.
+ *   g: device float32 [n_g][ncell]; h: device float32 [n_h][ncell] or NULL (h = g); 1 <= n_g, n_h <= 64 and
+ *   n_g (n_g + 1) / 2 * n_h <= 2^21 (larger requests return POLYBIN_EINVAL).  m_out_dev: device float64
+ *   [n_g (n_g + 1) / 2][n_h], written on cuda_stream (a cudaStream_t; NULL = legacy default stream).
+ * Asynchronous: the call returns after enqueueing; synchronise the stream before reading m_out_dev.  The first call
+ * on a device looks up the scratch address (cudaGetSymbolAddress) and fills the pair table with a kernel: make
+ * that first call before any stream capture.  Every call on a device shares the scratch, which keeps the last
+ * call's contents (each call overwrites all it reads, so nothing needs clearing): calls that overlap on the GPU
+ * (other streams, or other host threads) race and must be serialised by the caller.
+ * Errors: polybin_contract_noalloc_error() describes the last failure on the calling host thread. */
+int polybin_contract_noalloc(const float* g, int n_g, const float* h, int n_h, long long ncell, double* m_out_dev,
+                             void* cuda_stream);
+const char* polybin_contract_noalloc_error(void);
+
 #ifdef __cplusplus
 }
 #endif
