@@ -96,33 +96,37 @@ int run_forward(polybin_ctx* ctx, const TIN* in, const TM* m1, const TM* m2, C<T
     const int N0 = ctx->N[0], N1 = ctx->N[1], N2 = ctx->N[2];
     const int Bz = ctx->gz.cnt, By = ctx->gy.cnt;
     const long nlines = (long)N0 * N1;
-    int rc;
+    int rc = POLYBIN_OK;
     StageTimer timer(ctx, kStageForward);
     {
         const int LP = lines_per_cta<T>(N2);
-        const size_t sm = 2 * (size_t)N2 * (LP + 1) * sizeof(C<T>);
-        if ((rc = set_smem<T>(ctx, (const void*)k_fwd_z<T, TIN, TM>, sm))) return rc;
+        const size_t sm = (2 * (size_t)N2 * (LP + 1) + N2) * sizeof(C<T>);
         const unsigned nblk = (unsigned)((nlines + 2 * LP - 1) / (2 * LP));
-        k_fwd_z<T, TIN, TM><<<nblk, 256, sm, ctx->stream>>>(in, m1, m2, t1, nlines, Bz, ctx->plan[2], twiddles<T>(ctx, 2), LP);
+        PB_WITH_NT(N2, NT, {
+            if ((rc = set_smem<T>(ctx, (const void*)k_fwd_z<T, TIN, TM, NT>, sm))) return rc;
+            k_fwd_z<T, TIN, TM, NT><<<nblk, 256, sm, ctx->stream>>>(in, m1, m2, t1, nlines, Bz, ctx->plan[2],
+                                                                    twiddles<T>(ctx, 2), LP);
+        })
         if ((rc = launch_check(ctx, "k_fwd_z"))) return rc;
     }
     {
         const int TK = cols_per_cta<T>(N1);
-        const size_t sm = 2 * (size_t)N1 * TK * sizeof(C<T>);
-        if ((rc = set_smem<T>(ctx, (const void*)k_col<T, -1>, sm))) return rc;
+        const size_t sm = (2 * (size_t)N1 * TK + N1) * sizeof(C<T>);
         ColBatch b;
         ColItem& it = b.it[0];
         it.in = t1; it.out = t2;
         it.in_os = (long)N1 * Bz; it.in_es = Bz; it.out_os = (long)By * Bz; it.out_es = Bz;
         it.ncols = Bz; it.nouter = N0; it.rng = ctx->gy;
         dim3 grid((Bz + TK - 1) / TK, N0, 1);
-        k_col<T, -1><<<grid, 256, sm, ctx->stream>>>(b, ctx->plan[1], twiddles<T>(ctx, 1), TK);
+        PB_WITH_NT(N1, NT, {
+            if ((rc = set_smem<T>(ctx, (const void*)k_col<T, -1, NT>, sm))) return rc;
+            k_col<T, -1, NT><<<grid, 256, sm, ctx->stream>>>(b, ctx->plan[1], twiddles<T>(ctx, 1), TK);
+        })
         if ((rc = launch_check(ctx, "k_col fwd y"))) return rc;
     }
     {
         const int TK = cols_per_cta<T>(N0);
-        const size_t sm = 2 * (size_t)N0 * TK * sizeof(C<T>);
-        if ((rc = set_smem<T>(ctx, (const void*)k_col<T, -1>, sm))) return rc;
+        const size_t sm = (2 * (size_t)N0 * TK + N0) * sizeof(C<T>);
         ColBatch b;
         ColItem& it = b.it[0];
         const int ncols = By * Bz;
@@ -130,7 +134,10 @@ int run_forward(polybin_ctx* ctx, const TIN* in, const TM* m1, const TM* m2, C<T
         it.in_os = 0; it.in_es = ncols; it.out_os = 0; it.out_es = ncols;
         it.ncols = ncols; it.nouter = 1; it.rng = ctx->gx;
         dim3 grid((ncols + TK - 1) / TK, 1, 1);
-        k_col<T, -1><<<grid, 256, sm, ctx->stream>>>(b, ctx->plan[0], twiddles<T>(ctx, 0), TK);
+        PB_WITH_NT(N0, NT, {
+            if ((rc = set_smem<T>(ctx, (const void*)k_col<T, -1, NT>, sm))) return rc;
+            k_col<T, -1, NT><<<grid, 256, sm, ctx->stream>>>(b, ctx->plan[0], twiddles<T>(ctx, 0), TK);
+        })
         if ((rc = launch_check(ctx, "k_col fwd x"))) return rc;
     }
     return POLYBIN_OK;
@@ -141,12 +148,11 @@ template <typename T>
 int run_shells(polybin_ctx* ctx, const C<T>* box, C<T>* u1, C<T>* u2, T* g, int ell) {
     const int N0 = ctx->N[0], N1 = ctx->N[1], N2 = ctx->N[2];
     const int nb = ctx->nb;
-    int rc;
+    int rc = POLYBIN_OK;
     StageTimer timer(ctx, kStageShells);
     {
         const int TK = cols_per_cta<T>(N0);
-        const size_t sm = 2 * (size_t)N0 * TK * sizeof(C<T>);
-        if ((rc = set_smem<T>(ctx, (const void*)k_inv_x_filter<T>, sm))) return rc;
+        const size_t sm = (2 * (size_t)N0 * TK + N0) * sizeof(C<T>);
         XInvBatch b;
         int maxcols = 0;
         for (int i = 0; i < nb; ++i) {
@@ -158,14 +164,17 @@ int run_shells(polybin_ctx* ctx, const C<T>* box, C<T>* u1, C<T>* u2, T* g, int 
             maxcols = std::max(maxcols, bb.ry.cnt * bb.rz.cnt);
         }
         dim3 grid((maxcols + TK - 1) / TK, nb, 1);
-        k_inv_x_filter<T><<<grid, 256, sm, ctx->stream>>>(b, box, ctx->gx, ctx->gy, ctx->gz, ctx->d_lut, ctx->smax,
-                                                           T(1.0 / (double)ctx->ncell), ctx->plan[0], twiddles<T>(ctx, 0), TK);
+        PB_WITH_NT(N0, NT, {
+            if ((rc = set_smem<T>(ctx, (const void*)k_inv_x_filter<T, NT>, sm))) return rc;
+            k_inv_x_filter<T, NT><<<grid, 256, sm, ctx->stream>>>(b, box, ctx->gx, ctx->gy, ctx->gz, ctx->d_lut, ctx->smax,
+                                                                  T(1.0 / (double)ctx->ncell), ctx->plan[0],
+                                                                  twiddles<T>(ctx, 0), TK);
+        })
         if ((rc = launch_check(ctx, "k_inv_x_filter"))) return rc;
     }
     {
         const int TK = cols_per_cta<T>(N1);
-        const size_t sm = 2 * (size_t)N1 * TK * sizeof(C<T>);
-        if ((rc = set_smem<T>(ctx, (const void*)k_col<T, +1>, sm))) return rc;
+        const size_t sm = (2 * (size_t)N1 * TK + N1) * sizeof(C<T>);
         ColBatch b;
         int maxc = 0;
         for (int i = 0; i < nb; ++i) {
@@ -178,13 +187,15 @@ int run_shells(polybin_ctx* ctx, const C<T>* box, C<T>* u1, C<T>* u2, T* g, int 
             maxc = std::max(maxc, bb.rz.cnt);
         }
         dim3 grid((maxc + TK - 1) / TK, N0, nb);
-        k_col<T, +1><<<grid, 256, sm, ctx->stream>>>(b, ctx->plan[1], twiddles<T>(ctx, 1), TK);
+        PB_WITH_NT(N1, NT, {
+            if ((rc = set_smem<T>(ctx, (const void*)k_col<T, +1, NT>, sm))) return rc;
+            k_col<T, +1, NT><<<grid, 256, sm, ctx->stream>>>(b, ctx->plan[1], twiddles<T>(ctx, 1), TK);
+        })
         if ((rc = launch_check(ctx, "k_col inv y"))) return rc;
     }
     {
         const int LP = lines_per_cta<T>(N2);
-        const size_t sm = 2 * (size_t)N2 * (LP + 1) * sizeof(C<T>);
-        if ((rc = set_smem<T>(ctx, (const void*)k_inv_z<T>, sm))) return rc;
+        const size_t sm = (2 * (size_t)N2 * (LP + 1) + N2) * sizeof(C<T>);
         ZInvBatch b;
         for (int i = 0; i < nb; ++i) {
             const BinBox& bb = ctx->bbox[i];
@@ -194,7 +205,11 @@ int run_shells(polybin_ctx* ctx, const C<T>* box, C<T>* u1, C<T>* u2, T* g, int 
         }
         const long nlines = (long)N0 * N1;
         dim3 grid((unsigned)((nlines + 2 * LP - 1) / (2 * LP)), nb, 1);
-        k_inv_z<T><<<grid, 256, sm, ctx->stream>>>(b, nlines, T(1), (const T*)nullptr, ctx->plan[2], twiddles<T>(ctx, 2), LP);
+        PB_WITH_NT(N2, NT, {
+            if ((rc = set_smem<T>(ctx, (const void*)k_inv_z<T, NT>, sm))) return rc;
+            k_inv_z<T, NT><<<grid, 256, sm, ctx->stream>>>(b, nlines, T(1), (const T*)nullptr, ctx->plan[2],
+                                                          twiddles<T>(ctx, 2), LP);
+        })
         if ((rc = launch_check(ctx, "k_inv_z"))) return rc;
     }
     return POLYBIN_OK;

@@ -146,21 +146,102 @@ __device__ C<T>* fft_lines(C<T>* src, C<T>* dst, int L, int ES, const FftPlan& p
     return src;
 }
 
+
+// ------------------------------------------------------------------------------------------------
+// Compile-time specialisation for power-of-two lengths (64 .. 1024): radices, strides and line counts are
+// constants, so the index arithmetic is shifts and masks and every radix loop is fully unrolled.
+template <typename T> __host__ __device__ constexpr int lines_per_cta_of(int n) {
+    int lp = 16;
+    while (lp > 1 && 2 * (long)n * (lp + 1) * (long)sizeof(C<T>) > 96 * 1024) lp >>= 1;
+    return lp;
+}
+template <typename T> __host__ __device__ constexpr int cols_per_cta_of(int n) {
+    int tk = 16;
+    while (tk > 1 && 2 * (long)n * tk * (long)sizeof(C<T>) > 64 * 1024) tk >>= 1;
+    return tk;
+}
+__host__ __device__ constexpr int p2_radix(int n, int pass) {
+    int m = n;
+    for (int p = 0; p < pass; ++p) m /= (m % 8 == 0) ? 8 : ((m % 4 == 0) ? 4 : 2);
+    return m <= 1 ? 1 : ((m % 8 == 0) ? 8 : ((m % 4 == 0) ? 4 : 2));
+}
+__host__ __device__ constexpr int p2_passes(int n) {
+    int c = 0;
+    while (p2_radix(n, c) > 1) ++c;
+    return c;
+}
+__host__ __device__ constexpr bool ct_length(int n) { return n == 64 || n == 128 || n == 256 || n == 512 || n == 1024; }
+
+template <typename T, int DIR, int N, int L, int ES, int NTHR, int PASS, int NS>
+__device__ __forceinline__ C<T>* fft_ct_pass(C<T>* src, C<T>* dst, const C<T>* __restrict__ tw, int tid) {
+    if constexpr (PASS == p2_passes(N)) {
+        return src;
+    } else {
+        constexpr int R = p2_radix(N, PASS);
+        constexpr int NBF = N / R;
+        constexpr int TSTR = N / (NS * R);
+        constexpr int TOTAL = NBF * L;
+#pragma unroll 2
+        for (int w = tid; w < TOTAL; w += NTHR) {
+            const int l = w % L;
+            const int j = w / L;
+            const int k = j % NS;
+            C<T> v[8];
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[r] = src[l + (j + r * NBF) * ES];
+            if constexpr (NS > 1) {
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    const C<T> t = tw[r * k * TSTR];
+                    v[r] = DIR < 0 ? mul<T>(v[r], t) : mulc<T>(v[r], t);
+                }
+            }
+            dft<T, DIR>(v, R);
+            const int base = (j - k) * R + k;
+#pragma unroll
+            for (int q = 0; q < R; ++q) dst[l + (base + q * NS) * ES] = v[q];
+        }
+        __syncthreads();
+        return fft_ct_pass<T, DIR, N, L, ES, NTHR, PASS + 1, NS * R>(dst, src, tw, tid);
+    }
+}
+
+// Dispatch: compile-time version when NT > 0, run-time plan otherwise.
+template <typename T, int DIR, int NT, int LT, int ET>
+__device__ __forceinline__ C<T>* fft_any(C<T>* src, C<T>* dst, int L, int ES, const FftPlan& p,
+                                         const C<T>* __restrict__ tw, int tid, int nthr) {
+    if constexpr (NT > 0) {
+        return fft_ct_pass<T, DIR, NT, LT, ET, 256, 0, 1>(src, dst, tw, tid);
+    } else {
+        return fft_lines<T, DIR>(src, dst, L, ES, p, tw, tid, nthr);
+    }
+}
+
+// Twiddles e^{-2 pi i m / n} staged into shared memory (after a __syncthreads they are visible to the CTA).
+template <typename T>
+__device__ __forceinline__ void stage_twiddles(C<T>* dst, const C<T>* __restrict__ tw, int n, int tid, int nthr) {
+    for (int i = tid; i < n; i += nthr) dst[i] = tw[i];
+}
+
 // ------------------------------------------------------------------------------------------------
 // z-pass, forward: pairs of real lines (lines 2p, 2p+1 of the flattened (x, y) index) packed as one
 // complex line, transformed, then split into the two Hermitian half-spectra; only kz < kout is stored.
 // Optional pointwise multipliers m1, m2 (same layout as the input) are applied on load.
-template <typename T, typename TIN, typename TM>
+template <typename T, typename TIN, typename TM, int NT = 0>
 __global__ void __launch_bounds__(256) k_fwd_z(const TIN* __restrict__ in, const TM* __restrict__ m1,
                                                const TM* __restrict__ m2, C<T>* __restrict__ out, long nlines,
-                                               int kout, FftPlan plan, const C<T>* __restrict__ tw, int LP) {
+                                               int kout, FftPlan plan, const C<T>* __restrict__ twg, int LPrt) {
     extern __shared__ unsigned char smem_raw[];
-    const int n = plan.n;
+    constexpr int LT = NT > 0 ? lines_per_cta_of<T>(NT) : 0;
+    const int n = NT > 0 ? NT : plan.n;
+    const int LP = NT > 0 ? LT : LPrt;
     const int ES = LP + 1;
     C<T>* b0 = reinterpret_cast<C<T>*>(smem_raw);
     C<T>* b1 = b0 + (size_t)n * ES;
+    C<T>* tw = b1 + (size_t)n * ES;
     const long line0 = (long)blockIdx.x * 2 * LP;
     const int tid = threadIdx.x, nthr = blockDim.x;
+    stage_twiddles<T>(tw, twg, n, tid, nthr);
     T* bs = reinterpret_cast<T*>(b0);
     for (int idx = tid; idx < 2 * LP * n; idx += nthr) {
         const int r = idx / n, e = idx - r * n;
@@ -175,7 +256,7 @@ __global__ void __launch_bounds__(256) k_fwd_z(const TIN* __restrict__ in, const
         bs[2 * ((r >> 1) + e * ES) + (r & 1)] = v;
     }
     __syncthreads();
-    C<T>* z = fft_lines<T, -1>(b0, b1, LP, ES, plan, tw, tid, nthr);
+    C<T>* z = fft_any<T, -1, NT, LT, LT + 1>(b0, b1, LP, ES, plan, tw, tid, nthr);
     for (int idx = tid; idx < LP * kout; idx += nthr) {
         const int l = idx / kout, k = idx - l * kout;
         const long gl = line0 + 2 * l;
@@ -203,20 +284,24 @@ struct ZInvBatch {
     ZInvItem it[kMaxItems];
 };
 
-template <typename T>
+template <typename T, int NT = 0>
 __global__ void __launch_bounds__(256) k_inv_z(ZInvBatch batch, long nlines, T scale, const T* __restrict__ mulout,
-                                               FftPlan plan, const C<T>* __restrict__ tw, int LP) {
+                                               FftPlan plan, const C<T>* __restrict__ twg, int LPrt) {
     extern __shared__ unsigned char smem_raw[];
+    constexpr int LT = NT > 0 ? lines_per_cta_of<T>(NT) : 0;
     const ZInvItem item = batch.it[blockIdx.y];
     const C<T>* __restrict__ in = static_cast<const C<T>*>(item.in);
     T* __restrict__ out = static_cast<T*>(item.out);
     const int kin = item.kin;
-    const int n = plan.n;
+    const int n = NT > 0 ? NT : plan.n;
+    const int LP = NT > 0 ? LT : LPrt;
     const int ES = LP + 1;
     C<T>* b0 = reinterpret_cast<C<T>*>(smem_raw);
     C<T>* b1 = b0 + (size_t)n * ES;
+    C<T>* tw = b1 + (size_t)n * ES;
     const long line0 = (long)blockIdx.x * 2 * LP;
     const int tid = threadIdx.x, nthr = blockDim.x;
+    stage_twiddles<T>(tw, twg, n, tid, nthr);
     for (int idx = tid; idx < LP * n; idx += nthr) b0[idx % LP + (idx / LP) * ES] = mk<T>(T(0), T(0));
     __syncthreads();
     for (int idx = tid; idx < LP * kin; idx += nthr) {
@@ -234,7 +319,7 @@ __global__ void __launch_bounds__(256) k_inv_z(ZInvBatch batch, long nlines, T s
         }
     }
     __syncthreads();
-    C<T>* z = fft_lines<T, +1>(b0, b1, LP, ES, plan, tw, tid, nthr);
+    C<T>* z = fft_any<T, +1, NT, LT, LT + 1>(b0, b1, LP, ES, plan, tw, tid, nthr);
     for (int idx = tid; idx < 2 * LP * n; idx += nthr) {
         const int r = idx / n, e = idx - r * n;
         const long gl = line0 + r;
@@ -263,11 +348,13 @@ struct ColBatch {
     ColItem it[kMaxItems];
 };
 
-template <typename T, int DIR>
-__global__ void __launch_bounds__(256) k_col(ColBatch batch, FftPlan plan, const C<T>* __restrict__ tw, int TK) {
+template <typename T, int DIR, int NT = 0>
+__global__ void __launch_bounds__(256) k_col(ColBatch batch, FftPlan plan, const C<T>* __restrict__ twg, int TKrt) {
     extern __shared__ unsigned char smem_raw[];
+    constexpr int TT = NT > 0 ? cols_per_cta_of<T>(NT) : 0;
+    const int TK = NT > 0 ? TT : TKrt;
     const ColItem item = batch.it[blockIdx.z];
-    const int n = plan.n;
+    const int n = NT > 0 ? NT : plan.n;
     const int c0 = blockIdx.x * TK;
     const int o = blockIdx.y;
     if (c0 >= item.ncols || o >= item.nouter) return;
@@ -276,7 +363,9 @@ __global__ void __launch_bounds__(256) k_col(ColBatch batch, FftPlan plan, const
     C<T>* __restrict__ out = static_cast<C<T>*>(item.out) + (long)o * item.out_os + c0;
     C<T>* b0 = reinterpret_cast<C<T>*>(smem_raw);
     C<T>* b1 = b0 + (size_t)n * TK;
+    C<T>* tw = b1 + (size_t)n * TK;
     const int tid = threadIdx.x, nthr = blockDim.x;
+    stage_twiddles<T>(tw, twg, n, tid, nthr);
     if (DIR < 0) {
         for (int idx = tid; idx < n * TK; idx += nthr) {
             const int c = idx % TK, i = idx / TK;
@@ -291,7 +380,7 @@ __global__ void __launch_bounds__(256) k_col(ColBatch batch, FftPlan plan, const
         }
     }
     __syncthreads();
-    C<T>* z = fft_lines<T, DIR>(b0, b1, TK, TK, plan, tw, tid, nthr);
+    C<T>* z = fft_any<T, DIR, NT, TT, TT>(b0, b1, TK, TK, plan, tw, tid, nthr);
     if (DIR < 0) {
         for (int idx = tid; idx < item.rng.cnt * TK; idx += nthr) {
             const int c = idx % TK, i = idx / TK;
@@ -321,21 +410,25 @@ struct XInvBatch {
     XInvItem it[kMaxItems];
 };
 
-template <typename T>
+template <typename T, int NT = 0>
 __global__ void __launch_bounds__(256) k_inv_x_filter(XInvBatch batch, const C<T>* __restrict__ spec,
                                                       AxisRange gx, AxisRange gy, AxisRange gz,
                                                       const int16_t* __restrict__ lut, int smax, T scale,
-                                                      FftPlan plan, const C<T>* __restrict__ tw, int TK) {
+                                                      FftPlan plan, const C<T>* __restrict__ twg, int TKrt) {
     extern __shared__ unsigned char smem_raw[];
+    constexpr int TT = NT > 0 ? cols_per_cta_of<T>(NT) : 0;
+    const int TK = NT > 0 ? TT : TKrt;
     const XInvItem item = batch.it[blockIdx.y];
-    const int n = plan.n;
+    const int n = NT > 0 ? NT : plan.n;
     const int ncols = item.ry.cnt * item.rz.cnt;
     const int c0 = blockIdx.x * TK;
     if (c0 >= ncols) return;
     const int nc = min(TK, ncols - c0);
     C<T>* b0 = reinterpret_cast<C<T>*>(smem_raw);
     C<T>* b1 = b0 + (size_t)n * TK;
+    C<T>* tw = b1 + (size_t)n * TK;
     const int tid = threadIdx.x, nthr = blockDim.x;
+    stage_twiddles<T>(tw, twg, n, tid, nthr);
     for (int idx = tid; idx < n * TK; idx += nthr) b0[idx] = mk<T>(T(0), T(0));
     __syncthreads();
     const long gyz = (long)gy.cnt * gz.cnt;
@@ -361,7 +454,7 @@ __global__ void __launch_bounds__(256) k_inv_x_filter(XInvBatch batch, const C<T
         b0[c + pos_of(fx, n) * TK] = v;
     }
     __syncthreads();
-    C<T>* z = fft_lines<T, +1>(b0, b1, TK, TK, plan, tw, tid, nthr);
+    C<T>* z = fft_any<T, +1, NT, TT, TT>(b0, b1, TK, TK, plan, tw, tid, nthr);
     C<T>* __restrict__ out = static_cast<C<T>*>(item.out);
     for (int idx = tid; idx < n * TK; idx += nthr) {
         const int c = idx % TK, i = idx / TK;
@@ -369,4 +462,17 @@ __global__ void __launch_bounds__(256) k_inv_x_filter(XInvBatch batch, const C<T
     }
 }
 
+}  // namespace pb
+
+namespace pb {
+// Host-side dispatch of a launch over the compile-time lengths (NT = 0: run-time plan).
+#define PB_WITH_NT(n, NTV, ...)                              \
+    switch (n) {                                             \
+        case 64: { constexpr int NTV = 64; __VA_ARGS__ } break;   \
+        case 128: { constexpr int NTV = 128; __VA_ARGS__ } break; \
+        case 256: { constexpr int NTV = 256; __VA_ARGS__ } break; \
+        case 512: { constexpr int NTV = 512; __VA_ARGS__ } break; \
+        case 1024: { constexpr int NTV = 1024; __VA_ARGS__ } break; \
+        default: { constexpr int NTV = 0; __VA_ARGS__ } break;    \
+    }
 }  // namespace pb

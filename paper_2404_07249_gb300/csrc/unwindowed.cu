@@ -337,55 +337,57 @@ template <typename T>
 static int run_inverse_box(polybin_ctx* ctx, const C<T>* box, C<T>* v1, C<T>* v2, T* out, const T* mulout) {
     const int N0 = ctx->N[0], N1 = ctx->N[1], N2 = ctx->N[2];
     const int By = ctx->gy.cnt, Bz = ctx->gz.cnt;
-    int rc;
+    const C<T>* tw0 = (const C<T>*)(sizeof(T) == 4 ? ctx->d_tw_f[0] : ctx->d_tw_d[0]);
+    const C<T>* tw1 = (const C<T>*)(sizeof(T) == 4 ? ctx->d_tw_f[1] : ctx->d_tw_d[1]);
+    const C<T>* tw2 = (const C<T>*)(sizeof(T) == 4 ? ctx->d_tw_f[2] : ctx->d_tw_d[2]);
+    cudaError_t e = cudaSuccess;
     {
-        int tk = 16;
-        while (tk > 1 && 2 * (size_t)N0 * tk * sizeof(C<T>) > 64 * 1024) tk >>= 1;
-        const size_t sm = 2 * (size_t)N0 * tk * sizeof(C<T>);
-        cudaError_t e = cudaFuncSetAttribute((const void*)k_col<T, +1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return fail_cuda(ctx, e, "attr", __FILE__, __LINE__);
+        const int tk = cols_per_cta_of<T>(N0);
+        const size_t sm = (2 * (size_t)N0 * tk + N0) * sizeof(C<T>);
         ColBatch b;
         ColItem& it = b.it[0];
         const int ncols = By * Bz;
         it.in = box; it.out = v1;
         it.in_os = 0; it.in_es = ncols; it.out_os = 0; it.out_es = ncols;
         it.ncols = ncols; it.nouter = 1; it.rng = ctx->gx;
-        k_col<T, +1><<<dim3((ncols + tk - 1) / tk, 1, 1), 256, sm, ctx->stream>>>(b, ctx->plan[0],
-            (const C<T>*)(sizeof(T) == 4 ? ctx->d_tw_f[0] : ctx->d_tw_d[0]), tk);
+        PB_WITH_NT(N0, NT, {
+            e = cudaFuncSetAttribute((const void*)k_col<T, +1, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e != cudaSuccess) return fail_cuda(ctx, e, "attr", __FILE__, __LINE__);
+            k_col<T, +1, NT><<<dim3((ncols + tk - 1) / tk, 1, 1), 256, sm, ctx->stream>>>(b, ctx->plan[0], tw0, tk);
+        })
         ctx->launches++;
     }
     {
-        int tk = 16;
-        while (tk > 1 && 2 * (size_t)N1 * tk * sizeof(C<T>) > 64 * 1024) tk >>= 1;
-        const size_t sm = 2 * (size_t)N1 * tk * sizeof(C<T>);
-        cudaError_t e = cudaFuncSetAttribute((const void*)k_col<T, +1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return fail_cuda(ctx, e, "attr", __FILE__, __LINE__);
+        const int tk = cols_per_cta_of<T>(N1);
+        const size_t sm = (2 * (size_t)N1 * tk + N1) * sizeof(C<T>);
         ColBatch b;
         ColItem& it = b.it[0];
         it.in = v1; it.out = v2;
         it.in_os = (long)By * Bz; it.in_es = Bz; it.out_os = (long)N1 * Bz; it.out_es = Bz;
         it.ncols = Bz; it.nouter = N0; it.rng = ctx->gy;
-        k_col<T, +1><<<dim3((Bz + tk - 1) / tk, N0, 1), 256, sm, ctx->stream>>>(b, ctx->plan[1],
-            (const C<T>*)(sizeof(T) == 4 ? ctx->d_tw_f[1] : ctx->d_tw_d[1]), tk);
+        PB_WITH_NT(N1, NT, {
+            e = cudaFuncSetAttribute((const void*)k_col<T, +1, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e != cudaSuccess) return fail_cuda(ctx, e, "attr", __FILE__, __LINE__);
+            k_col<T, +1, NT><<<dim3((Bz + tk - 1) / tk, N0, 1), 256, sm, ctx->stream>>>(b, ctx->plan[1], tw1, tk);
+        })
         ctx->launches++;
     }
     {
-        int lp = 16;
-        while (lp > 1 && 2 * (size_t)N2 * (lp + 1) * sizeof(C<T>) > 96 * 1024) lp >>= 1;
-        const size_t sm = 2 * (size_t)N2 * (lp + 1) * sizeof(C<T>);
-        cudaError_t e = cudaFuncSetAttribute((const void*)k_inv_z<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return fail_cuda(ctx, e, "attr", __FILE__, __LINE__);
+        const int lp = lines_per_cta_of<T>(N2);
+        const size_t sm = (2 * (size_t)N2 * (lp + 1) + N2) * sizeof(C<T>);
         ZInvBatch b;
         b.it[0].in = v2; b.it[0].out = out; b.it[0].kin = Bz;
         const long nlines = (long)N0 * N1;
-        k_inv_z<T><<<dim3((unsigned)((nlines + 2 * lp - 1) / (2 * lp)), 1, 1), 256, sm, ctx->stream>>>(
-            b, nlines, T(1.0 / (double)ctx->ncell), mulout, ctx->plan[2],
-            (const C<T>*)(sizeof(T) == 4 ? ctx->d_tw_f[2] : ctx->d_tw_d[2]), lp);
+        PB_WITH_NT(N2, NT, {
+            e = cudaFuncSetAttribute((const void*)k_inv_z<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e != cudaSuccess) return fail_cuda(ctx, e, "attr", __FILE__, __LINE__);
+            k_inv_z<T, NT><<<dim3((unsigned)((nlines + 2 * lp - 1) / (2 * lp)), 1, 1), 256, sm, ctx->stream>>>(
+                b, nlines, T(1.0 / (double)ctx->ncell), mulout, ctx->plan[2], tw2, lp);
+        })
         ctx->launches++;
     }
-    cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     if (e != cudaSuccess) return fail_cuda(ctx, e, "run_inverse_box", __FILE__, __LINE__);
-    (void)rc;
     return POLYBIN_OK;
 }
 
