@@ -7,23 +7,25 @@
 // product is accumulated as hi_a hi_b + hi_a lo_b + lo_a hi_b (the lo_a lo_b term, ~2^-22 relative, is
 // dropped).
 //
-// Warp roles (512 threads, one CTA per SM):
-//   warps 0-7   producers (two per scheduler): stream the map tiles into a shared-memory ring with cp.async,
-//               form the pair products (a thread owns one TMEM lane, i.e. one row of two of the pair tiles),
-//               split them and write them into TMEM with tcgen05.st (the A operand never touches shared
-//               memory); threads 0-127 also convert the singles tile to hi/lo TF32 in the canonical
-//               no-swizzle K-major layout (the B operand).
-//   warps 8-15  epilogue: every kPeriod chunks (64 cells) read the accumulators with tcgen05.ld into FP32
+// Work split: a CTA takes one contiguous range of cells and one row group of two 128-row pair tiles (256
+// pairs); two CTAs run on each SM (the grid covers 2 x 152 CTAs over row groups and cell ranges), so two
+// independent producer/MMA pipelines overlap each other's handshake latency.
+//
+// Warp roles (256 threads per CTA):
+//   warps 0-3   producers: stream the map tiles into a shared-memory ring with cp.async, form the pair
+//               products (a thread owns one TMEM lane, i.e. one row of both pair tiles), split them and write
+//               them into TMEM with tcgen05.st (the A operand never touches shared memory), and convert the
+//               singles tile to hi/lo TF32 in the canonical no-swizzle K-major layout (the B operand).
+//   warps 4-7   epilogue: every kPeriod chunks (64 cells) read the accumulators with tcgen05.ld into FP32
 //               register sums (round-to-nearest), every kSpill periods add those into FP64 partials in
-//               shared memory; finally write the CTA's FP64 partials.  Warp 8 allocates TMEM.  Lane 0 of
-//               warps 8-11 issues the tcgen05.mma (A from TMEM, B from shared memory, D in TMEM) and the
-//               tcgen05.commit of one pair tile for period q before its warp drains period q-1 (D is
-//               double buffered).  The 128x32x8 MMAs are short, so one issuing thread cannot keep the
-//               tensor pipe busy; four issuers overlap their issue latency.
+//               shared memory; finally write the CTA's FP64 partials.  Warp 4 allocates TMEM.  Lane 0 of
+//               warps 4 and 5 issues the tcgen05.mma (A from TMEM, B from shared memory, D in TMEM) and the
+//               tcgen05.commit of one pair tile for period q before its warp drains period q-1 (D is double
+//               buffered); the 128x32x8 MMAs are short, so one issuing thread per tile keeps more in flight.
 // Precision: the tensor core's internal accumulation is not round-to-nearest, so its error grows with the
 // number of MMAs accumulated into one D; the 64-cell periods keep that chain at 24 MMAs.
-// TMEM (512 columns): D double buffer 2 x (4 tiles x 32 columns) at [0, 256); A ring = 2 stages x
-// (4 tiles x (16 hi + 16 lo)) at [256, 512).  Every mbarrier wait is bounded; on timeout the CTA raises an
+// TMEM (256 columns per CTA): D double buffer 2 x (2 tiles x 32 columns) at [0, 128); A ring = 2 stages x
+// (2 tiles x (16 hi + 16 lo)) at [128, 256).  Every mbarrier wait is bounded; on timeout the CTA raises an
 // error flag and exits after draining its own asynchronous work.
 #include <cuda_runtime.h>
 
@@ -39,15 +41,17 @@ constexpr int kStages = 2;        // A/B pipeline depth
 constexpr int kRing = 4;          // map-tile ring (prefetch distance 3)
 constexpr int kPeriod = 4;        // chunks per tensor-memory accumulation period (64 cells)
 constexpr int kSpill = 32;        // periods per FP32 register accumulation before the FP64 update (2048 cells)
-constexpr int kMaxTiles = 4;      // pair tiles of 128 rows (npairs <= 512)
+constexpr int kMaxTiles = 4;      // pair tiles of 128 rows over all row groups (npairs <= 512)
+constexpr int kTiles = 2;         // pair tiles per CTA (a row group of 256 pairs); two CTAs per SM
 constexpr int kNCols = 32;        // singles per tile (nh <= 32)
 constexpr int kGS = 20;           // floats per map row in the ring (16 + 4 pad: conflict-free LDS.128)
-constexpr int kProducerWarps = 8;
+constexpr int kProducerWarps = 4;
 constexpr int kProducers = 32 * kProducerWarps;
 constexpr int kMmaWarp = kProducerWarps;   // first epilogue warp; allocates TMEM
-constexpr int kIssuers = 4;                // epilogue warps 8..11: lane 0 issues the MMAs of tile (warp - 8)
-constexpr int kEpilogue = 256;             // 8 epilogue warps
+constexpr int kIssuers = kTiles;           // epilogue warps 4, 5: lane 0 issues the MMAs of tile (warp - 4)
+constexpr int kEpilogue = 128;             // 4 epilogue warps
 constexpr int kThreads = kProducers + kEpilogue;
+constexpr int kTmemCols = 256;             // D 2 x (2 tiles x 32) at [0, 128); A 2 stages x (2 tiles x 32) at [128, 256)
 constexpr unsigned kSpinLimit = 1u << 22;
 
 struct Params {
@@ -163,11 +167,11 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                  : "memory");
 }
 
-// Named-barrier AND-vote over the 256 producer threads (barrier 1): every producer gets the same answer.
+// Named-barrier AND-vote over the 128 producer threads (barrier 1): every producer gets the same answer.
 __device__ __forceinline__ bool producers_all(bool v) {
     uint32_t r;
     asm volatile(
-        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.and.pred q, 1, 256, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.and.pred q, 1, 128, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
         : "=r"(r)
         : "r"((uint32_t)v)
         : "memory");
@@ -179,10 +183,10 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_b
                  : "memory");
 }
 
-__global__ void __launch_bounds__(kThreads, 1) k_contract_tc(Params P) {
+__global__ void __launch_bounds__(kThreads, 2) k_contract_tc(Params P) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    double* acc64 = reinterpret_cast<double*>(smem);                                   // [tiles][32][128]
-    unsigned char* bbase = smem + (size_t)kMaxTiles * kNCols * 128 * sizeof(double);   // B stages
+    double* acc64 = reinterpret_cast<double*>(smem);                                   // [kTiles][32][128]
+    unsigned char* bbase = smem + (size_t)kTiles * kNCols * 128 * sizeof(double);      // B stages
     const int BSTAGE = 2 * kNCols * kKC * 4;                                            // hi + lo, 4 KB
     float* ring = reinterpret_cast<float*>(bbase + kStages * BSTAGE);                   // [kRing][rows][kGS]
     const int rows = P.ng + (P.h != P.g ? P.nh : 0);
@@ -198,11 +202,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract_tc(Params P) {
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     const long cbeg = (long)blockIdx.x * P.cells_cta;
+    const int rg = blockIdx.y;                                  // row group: pair tiles 2 rg, 2 rg + 1
+    const int ntl = min(kTiles, P.ntiles - kTiles * rg);        // tiles of this CTA
     const long cend = min(P.ncell, cbeg + P.cells_cta);
     const int nchunks = cbeg < cend ? (int)((cend - cbeg + kKC - 1) / kKC) : 0;
     const int nperiods = (nchunks + kPeriod - 1) / kPeriod;
 
-    for (int i = tid; i < P.ntiles * kNCols * 128; i += blockDim.x) acc64[i] = 0.0;
+    for (int i = tid; i < kTiles * kNCols * 128; i += blockDim.x) acc64[i] = 0.0;
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) { mbar_init(&full[s], kProducers); mbar_init(&empty[s], kIssuers); }
         for (int d = 0; d < 2; ++d) { mbar_init(&dfull[d], kIssuers); mbar_init(&dempty[d], kEpilogue); }
@@ -211,27 +217,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract_tc(Params P) {
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == kMmaWarp) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot)));
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_u32(tmem_slot)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = *tmem_slot;        // D buffer d, tile t at column 128 d + 32 t
-    const uint32_t A0 = tmem + 256;          // A stage s, tile t: hi at 256 + 128 s + 32 t, lo at +16
+    const uint32_t tmem = *tmem_slot;        // D buffer d, tile t at column 64 d + 32 t
+    const uint32_t A0 = tmem + 128;          // A stage s, tile t: hi at 128 + 64 s + 32 t, lo at +16
 
     if (warp < kProducerWarps) {
         // ------------------------------------------------------------------ producers
         const bool hsep = P.h != P.g;
-        const int quarter = warp & 3, half = warp >> 2;
+        const int quarter = warp & 3;
         const int row = 32 * quarter + lane;
         const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
-        int pj[2], pk[2];
+        int pj[kTiles], pk[kTiles];
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            const int t = 2 * half + u;
-            const int p = 128 * t + row;
-            if (t < P.ntiles && p < P.npairs) { short2 jk = P.pairs[p]; pj[u] = jk.x; pk[u] = jk.y; }
+        for (int u = 0; u < kTiles; ++u) {
+            const int p = 128 * (kTiles * rg + u) + row;
+            if (u < ntl && p < P.npairs) { short2 jk = P.pairs[p]; pj[u] = jk.x; pk[u] = jk.y; }
             else { pj[u] = -1; pk[u] = -1; }
         }
         auto issue = [&](int c) {
@@ -265,9 +270,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract_tc(Params P) {
             const float* tile = ring + (size_t)(c % kRing) * rows * kGS;
             // A operand: pair products split into TF32 hi and FP32 remainder (read as TF32 by the MMA), into TMEM
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int t = 2 * half + u;
-                if (t >= P.ntiles) break;
+            for (int u = 0; u < kTiles; ++u) {
+                const int t = u;
+                if (t >= ntl) break;
                 uint32_t hi[kKC], lo[kKC];
                 if (pj[u] >= 0) {
                     const float4* a = reinterpret_cast<const float4*>(tile + pj[u] * kGS);
@@ -284,7 +289,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract_tc(Params P) {
 #pragma unroll
                     for (int q = 0; q < kKC; ++q) { hi[q] = 0u; lo[q] = 0u; }
                 }
-                const uint32_t col = 256u + 128u * s + 32u * t;
+                const uint32_t col = 128u + 64u * s + 32u * t;
                 tmem_st16(tmem + lane_base + col, hi);
                 tmem_st16(tmem + lane_base + col + 16u, lo);
             }
@@ -315,23 +320,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract_tc(Params P) {
         if (!ok) *abort_flag = 1;
     } else {
         // ------------------------------------------------------------------ epilogue (+ MMA issue in warp 8)
-        const int e = warp - kProducerWarps;       // 0..7
         const int quarter = warp & 3;              // TMEM lane quarter this warp may access
-        const int half = e >> 2;                   // tiles 2 half, 2 half + 1
         const int row = 32 * quarter + lane;
         const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
         const int iidx = warp - kMmaWarp;
         const bool issuer = iidx < kIssuers;
-        float acc[2][kNCols];
+        float acc[kTiles][kNCols];
 #pragma unroll
-        for (int u = 0; u < 2; ++u)
+        for (int u = 0; u < kTiles; ++u)
 #pragma unroll
             for (int i = 0; i < kNCols; ++i) acc[u][i] = 0.f;
         auto spill = [&]() {
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int t = 2 * half + u;
-                if (t >= P.ntiles) break;
+            for (int u = 0; u < kTiles; ++u) {
+                const int t = u;
+                if (t >= ntl) break;
 #pragma unroll
                 for (int i = 0; i < kNCols; ++i) {
                     acc64[(t * kNCols + i) * 128 + row] += (double)acc[u][i];
@@ -345,11 +348,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract_tc(Params P) {
             if (!mbar_wait(&dfull[d], (uint32_t)((q >> 1) & 1), abort_flag, P.err, issuer ? 0 : 1)) return false;
             tc_fence_after();
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int t = 2 * half + u;
-                if (t >= P.ntiles) break;
+            for (int u = 0; u < kTiles; ++u) {
+                const int t = u;
+                if (t >= ntl) break;
                 uint32_t v[kNCols];
-                tmem_ld32(tmem + lane_base + 128u * d + 32u * t, v);
+                tmem_ld32(tmem + lane_base + 64u * d + 32u * t, v);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
                 for (int i = 0; i < kNCols; ++i) acc[u][i] += __uint_as_float(v[i]);
@@ -373,9 +376,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract_tc(Params P) {
                 if (!mbar_wait(&full[s], (uint32_t)((c / kStages) & 1), abort_flag, P.err, 0)) { mma_ok = false; return; }
                 tc_fence_after();
                 const uint32_t bh = bstage0 + s * BSTAGE, bl = bh + 2048;
-                for (int t = iidx; t < P.ntiles; t += kIssuers) {
-                    const uint32_t dcol = tmem + 128u * d + 32u * t;
-                    const uint32_t ah = A0 + 128u * s + 32u * t, al = ah + 16u;
+                for (int t = iidx; t < ntl; t += kIssuers) {
+                    const uint32_t dcol = tmem + 64u * d + 32u * t;
+                    const uint32_t ah = A0 + 64u * s + 32u * t, al = ah + 16u;
 #pragma unroll
                     for (int ks = 0; ks < kKC / 8; ++ks) {
                         const uint64_t dbh = sdesc(bh + ks * 256, 128, 512);
@@ -409,10 +412,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract_tc(Params P) {
             for (int q = 0; q < nperiods && ok; ++q) ok = drain(q);
         }
         spill();
-        for (int u = 0; u < 2; ++u) {
-            const int t = 2 * half + u;
-            if (t >= P.ntiles) break;
-            const int p = 128 * t + row;
+        for (int u = 0; u < kTiles; ++u) {
+            const int t = u;
+            if (t >= ntl) break;
+            const int p = 128 * (kTiles * rg + t) + row;
             if (p >= P.npairs) continue;
             double* out = P.partial + ((size_t)blockIdx.x * P.npairs + p) * P.nh;
             for (int i = 0; i < P.nh; ++i) out[i] = acc64[(t * kNCols + i) * 128 + row];
@@ -421,7 +424,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract_tc(Params P) {
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == kMmaWarp) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+    if (warp == kMmaWarp) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
 }
 
 }  // namespace tc
@@ -429,7 +432,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_contract_tc(Params P) {
 bool split_tc_available() { return true; }
 
 static size_t tc_smem_bytes(int rows) {
-    return (size_t)tc::kMaxTiles * tc::kNCols * 128 * sizeof(double) + tc::kStages * 2 * tc::kNCols * tc::kKC * 4 +
+    return (size_t)tc::kTiles * tc::kNCols * 128 * sizeof(double) + tc::kStages * 2 * tc::kNCols * tc::kKC * 4 +
            (size_t)tc::kRing * rows * tc::kGS * sizeof(float) + 256;
 }
 
@@ -438,9 +441,10 @@ ContractGeom contract_geom_tc(int ng, int nh, long ncell) {
     ContractGeom G;
     G.nb = ng; G.nh = nh; G.npairs = ng * (ng + 1) / 2;
     G.rt = G.ct = 0; G.rows_cta = 128; G.nhp = tc::kNCols;
-    G.ngroups = (G.npairs + 127) / 128;
+    G.ngroups = (G.npairs + 127) / 128;                 // pair tiles; a CTA takes kTiles of them
+    const int nrg = (G.ngroups + tc::kTiles - 1) / tc::kTiles;
     const long nchunk = (ncell + tc::kKC - 1) / tc::kKC;
-    const long ncta = std::max(1L, std::min(152L, nchunk));
+    const long ncta = std::max(1L, std::min(304L / nrg, nchunk));   // two CTAs per SM over all row groups
     G.cells_cta = ((ncell + ncta - 1) / ncta + tc::kKC - 1) / tc::kKC * tc::kKC;
     G.ncb = (int)((ncell + G.cells_cta - 1) / G.cells_cta);
     return G;
@@ -470,7 +474,8 @@ int run_contract_tc(polybin_ctx* ctx, const float* g, int ng, const float* h, in
     P.err = ctx->d_err;
     {
         StageTimer timer(ctx, kStageContract);
-        tc::k_contract_tc<<<G.ncb, tc::kThreads, sm, ctx->stream>>>(P);
+        const int nrg = (G.ngroups + tc::kTiles - 1) / tc::kTiles;
+        tc::k_contract_tc<<<dim3(G.ncb, nrg, 1), tc::kThreads, sm, ctx->stream>>>(P);
         ctx->launches += 1;
         e = cudaGetLastError();
         if (e != cudaSuccess) return fail_cuda(ctx, e, "k_contract_tc", __FILE__, __LINE__);
