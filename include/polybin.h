@@ -81,6 +81,14 @@ int polybin_get_triplets(polybin_ctx* ctx, int* abc, double* n_abc);
  * F = N_abc / (N Delta) in pixel units, so Delta cancels).  bk_out: host [batch][n_triplets]. */
 int polybin_bk_ideal(polybin_ctx* ctx, const float* delta, int batch, double* bk_out);
 
+/* Ideal bispectra of n_fields fields on possibly different grids (e.g. a batch of 96^3, 128^3 and 160^3
+ * realisations).  ctxs[i] is the context of field i (fields on one grid share a context; all contexts must use
+ * one stream, that of ctxs[0]); fields[i]: device float32 [N0][N1][N2] of ctxs[i]; bk_out[i]: host
+ * [n_triplets(ctxs[i])], as polybin_bk_ideal.  The whole batch is captured into one CUDA graph and replayed
+ * with a single graph launch; the graph is cached in ctxs[0] for repeated calls with the same contexts and
+ * field pointers (a call with other arguments re-captures).  Profiling must be off. */
+int polybin_bk_ideal_multi(polybin_ctx* const* ctxs, const float* const* fields, int n_fields, double* const* bk_out);
+
 /* ---- power spectrum (Sec. 3.4.1) ------------------------------------------------------------------------- */
 
 /* Ideal P_ell (ell = 0, 2, .., l_max) with the continuous-limit Fisher normalisation (eq. fish-ideal-continuous):

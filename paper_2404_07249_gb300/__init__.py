@@ -55,6 +55,7 @@ _SIGS = {
                                              ctypes.c_void_p]),
     "polybin_bk_unwindowed": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                              ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "polybin_bk_ideal_multi": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "polybin_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
                                      ctypes.c_void_p]),
 }
@@ -304,6 +305,22 @@ class PolyBin:
         self._check(self.lib.polybin_contract(self.ctx, _ptr(g_dev), ng, None if h_dev is None else _ptr(h_dev), nh,
                                               _ptr(out)), "polybin_contract")
         return out
+
+
+def bk_ideal_multi(pbs, fields):
+    """Ideal bispectra of fields on several grids in one CUDA-graph launch (polybin_bk_ideal_multi).
+    pbs[i]: the PolyBin of field i (one stream for all); fields[i]: device float32 tensor."""
+    lib = load()
+    n = len(pbs)
+    ctxs = (ctypes.c_void_p * n)(*[pb.ctx.value for pb in pbs])
+    fs = [_f32(f) for f in fields]
+    fptr = (ctypes.c_void_p * n)(*[f.data_ptr() for f in fs])
+    outs = [np.zeros(pb.num_triplets()) for pb in pbs]
+    optr = (ctypes.c_void_p * n)(*[o.ctypes.data for o in outs])
+    rc = lib.polybin_bk_ideal_multi(ctxs, fptr, n, optr)
+    if rc != 0:
+        raise PolybinError(f"polybin_bk_ideal_multi: {rc}: {lib.polybin_last_error(pbs[0].ctx).decode()}")
+    return outs
 
 
 def pair_list(n: int):

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -542,6 +543,8 @@ extern "C" int polybin_init(polybin_ctx** out, const int grid[3], const double b
 
     polybin_ctx* ctx = new (std::nothrow) polybin_ctx();
     if (!ctx) return fail(nullptr, POLYBIN_ENOMEM, "polybin_init: out of host memory");
+    static std::atomic<unsigned long long> next_uid{1};
+    ctx->uid = next_uid.fetch_add(1);
     for (int a = 0; a < 3; ++a) ctx->N[a] = grid[a];
     ctx->ncell = (long)grid[0] * grid[1] * grid[2];
     ctx->L = boxsize[0];

@@ -431,6 +431,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_contract_tc(Params P) {
 
 bool split_tc_available() { return true; }
 
+int ensure_err_flag(polybin_ctx* ctx) {
+    if (ctx->d_err) return POLYBIN_OK;
+    cudaError_t e = cudaMalloc(&ctx->d_err, sizeof(int));
+    if (e != cudaSuccess) return fail_cuda(ctx, e, "cudaMalloc err flag", __FILE__, __LINE__);
+    e = cudaMemset(ctx->d_err, 0, sizeof(int));
+    if (e != cudaSuccess) return fail_cuda(ctx, e, "cudaMemset err flag", __FILE__, __LINE__);
+    return POLYBIN_OK;
+}
+
 static size_t tc_smem_bytes(int rows) {
     return (size_t)tc::kTiles * tc::kNCols * 128 * sizeof(double) + tc::kStages * 2 * tc::kNCols * tc::kKC * 4 +
            (size_t)tc::kRing * rows * tc::kGS * sizeof(float) + 256;
@@ -456,10 +465,8 @@ int run_contract_tc(polybin_ctx* ctx, const float* g, int ng, const float* h, in
     ContractGeom G = contract_geom_tc(ng, nh, ctx->ncell);
     if ((size_t)G.ncb * G.npairs * G.nh > partial_cap) return fail(ctx, POLYBIN_EINVAL, "contract_tc: partial buffer too small");
     if (ctx->ncell % 4) return fail(ctx, POLYBIN_EINVAL, "contract_tc: the number of cells must be a multiple of 4");
-    if (!ctx->d_err) {
-        cudaError_t e = cudaMalloc(&ctx->d_err, sizeof(int));
-        if (e != cudaSuccess) return fail_cuda(ctx, e, "cudaMalloc err flag", __FILE__, __LINE__);
-    }
+    int rc0 = ensure_err_flag(ctx);
+    if (rc0) return rc0;
     cudaError_t e = cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream);
     if (e != cudaSuccess) return fail_cuda(ctx, e, "cudaMemsetAsync", __FILE__, __LINE__);
     const int rows = ng + (h != g ? nh : 0);
@@ -485,6 +492,7 @@ int run_contract_tc(polybin_ctx* ctx, const float* g, int ng, const float* h, in
         e = cudaGetLastError();
         if (e != cudaSuccess) return fail_cuda(ctx, e, "k_reduce_partials", __FILE__, __LINE__);
     }
+    if (ctx->capturing) return POLYBIN_OK;   // the caller reads the error flag after the graph has run
     int herr = 0;
     e = cudaMemcpyAsync(&herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);

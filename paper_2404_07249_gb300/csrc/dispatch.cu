@@ -5,6 +5,7 @@ namespace pb {
 
 void destroy_extras(polybin_ctx* ctx) {
     destroy_unwindowed(ctx);
+    destroy_multi(ctx);
     if (ctx->d_err) cudaFree(ctx->d_err);
     ctx->d_err = nullptr;
 }

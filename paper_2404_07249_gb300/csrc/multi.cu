@@ -1,0 +1,134 @@
+// Batched ideal bispectra over fields on (possibly) different grids: the whole batch -- per field the pruned
+// forward transform, the shell maps, the triplet contraction and the copy of its result to pinned host memory --
+// is captured once into a CUDA graph on the stream of the first context and replayed with a single graph launch.
+// The graph is cached in the first context, keyed by the context ids and field pointers of the call.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <vector>
+
+#include "polybin_internal.h"
+
+namespace pb {
+
+struct MultiCache {
+    std::vector<unsigned long long> key;
+    cudaGraphExec_t exec = nullptr;
+    double* host = nullptr;                 // pinned: contraction results of every field
+    std::vector<size_t> off;                // per-field offset into host
+};
+
+void destroy_multi(polybin_ctx* ctx) {
+    MultiCache* m = static_cast<MultiCache*>(ctx->multi);
+    if (!m) return;
+    if (m->exec) cudaGraphExecDestroy(m->exec);
+    if (m->host) cudaFreeHost(m->host);
+    delete m;
+    ctx->multi = nullptr;
+}
+
+template <typename T>
+static int capture_field(polybin_ctx* c, const float* field, double* host_dst) {
+    int rc;
+    Work& w = c->w;
+    const int nb = c->nb, np = nb * (nb + 1) / 2;
+    if ((rc = run_forward<T, float, float>(c, field, (const float*)nullptr, (const float*)nullptr, (C<T>*)w.t1, (C<T>*)w.t2,
+                                           (C<T>*)w.box)))
+        return rc;
+    if ((rc = run_shells<T>(c, (const C<T>*)w.box, (C<T>*)w.u1, (C<T>*)w.u2, (T*)w.g, 0))) return rc;
+    if ((rc = run_contract_any<T>(c, (const T*)w.g, nb, nullptr, nb, w.partial, w.partial_cap, w.mout))) return rc;
+    cudaError_t e = cudaMemcpyAsync(host_dst, w.mout, sizeof(double) * (size_t)np * nb, cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return fail_cuda(c, e, "capture copy", __FILE__, __LINE__);
+    return POLYBIN_OK;
+}
+
+}  // namespace pb
+
+using namespace pb;
+
+extern "C" int polybin_bk_ideal_multi(polybin_ctx* const* ctxs, const float* const* fields, int n_fields,
+                                      double* const* bk_out) {
+    if (!ctxs || !fields || !bk_out || n_fields < 1 || !ctxs[0])
+        return fail(nullptr, POLYBIN_EINVAL, "polybin_bk_ideal_multi: bad argument");
+    polybin_ctx* c0 = ctxs[0];
+    int rc;
+    std::vector<unsigned long long> key;
+    key.reserve(2 * (size_t)n_fields + 1);
+    key.push_back((unsigned long long)n_fields);
+    for (int i = 0; i < n_fields; ++i) {
+        polybin_ctx* c = ctxs[i];
+        if (!c || !fields[i] || !bk_out[i]) return fail(c0, POLYBIN_EINVAL, "polybin_bk_ideal_multi: NULL entry %d", i);
+        if (c->stream != c0->stream) return fail(c0, POLYBIN_EINVAL, "polybin_bk_ideal_multi: contexts must share one stream");
+        if (c->profiling) return fail(c0, POLYBIN_EINVAL, "polybin_bk_ideal_multi: disable profiling first");
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, fields[i]) != cudaSuccess || at.type != cudaMemoryTypeDevice) {
+            cudaGetLastError();
+            return fail(c0, POLYBIN_EINVAL, "polybin_bk_ideal_multi: field %d must be device memory", i);
+        }
+        if ((rc = ensure_triplets(c))) return rc;
+        if ((rc = ensure_err_flag(c))) return rc;
+        key.push_back(c->uid);
+        key.push_back((unsigned long long)(uintptr_t)fields[i]);
+    }
+    MultiCache* m = static_cast<MultiCache*>(c0->multi);
+    if (!m || m->key != key) {
+        destroy_multi(c0);
+        m = new (std::nothrow) MultiCache();
+        if (!m) return fail(c0, POLYBIN_ENOMEM, "polybin_bk_ideal_multi: out of host memory");
+        c0->multi = m;
+        m->key = key;
+        size_t total = 0;
+        for (int i = 0; i < n_fields; ++i) {
+            m->off.push_back(total);
+            total += (size_t)ctxs[i]->nb * (ctxs[i]->nb + 1) / 2 * ctxs[i]->nb;
+        }
+        {
+            polybin_ctx* ctx = c0;
+            PB_CUDA_OK(cudaHostAlloc((void**)&m->host, sizeof(double) * total, cudaHostAllocDefault));
+        }
+        cudaStream_t st = c0->stream;
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return fail_cuda(c0, e, "cudaStreamBeginCapture", __FILE__, __LINE__);
+        for (int i = 0; i < n_fields; ++i) ctxs[i]->capturing = true;
+        rc = POLYBIN_OK;
+        for (int i = 0; i < n_fields && !rc; ++i) {
+            polybin_ctx* c = ctxs[i];
+            rc = c->prec == POLYBIN_FP64 ? capture_field<double>(c, fields[i], m->host + m->off[i])
+                                         : capture_field<float>(c, fields[i], m->host + m->off[i]);
+            if (rc && c != c0) c0->err = c->err;
+        }
+        for (int i = 0; i < n_fields; ++i) ctxs[i]->capturing = false;
+        e = cudaStreamEndCapture(st, &graph);
+        if (rc) {
+            if (graph) cudaGraphDestroy(graph);
+            destroy_multi(c0);
+            return rc;
+        }
+        if (e != cudaSuccess) { destroy_multi(c0); return fail_cuda(c0, e, "cudaStreamEndCapture", __FILE__, __LINE__); }
+        e = cudaGraphInstantiate(&m->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) { destroy_multi(c0); return fail_cuda(c0, e, "cudaGraphInstantiate", __FILE__, __LINE__); }
+    }
+    cudaError_t e = cudaGraphLaunch(m->exec, c0->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c0->stream);
+    if (e != cudaSuccess) return fail_cuda(c0, e, "cudaGraphLaunch", __FILE__, __LINE__);
+    for (int i = 0; i < n_fields; ++i) {
+        polybin_ctx* c = ctxs[i];
+        int herr = 0;
+        {
+            polybin_ctx* ctx = c0;
+            PB_CUDA_OK(cudaMemcpy(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+        }
+        if (herr) return fail(c0, POLYBIN_ETIMEOUT, "polybin_bk_ideal_multi: a pipeline wait timed out (field %d)", i);
+        const int nb = c->nb;
+        const double* M = m->host + m->off[i];
+        const double pref = c->vol * c->vol / ((double)c->ncell * (double)c->ncell * (double)c->ncell);
+        const size_t nt = c->Nabc.size();
+        for (size_t t = 0; t < nt; ++t) {
+            const int a = c->trip[3 * t], b = c->trip[3 * t + 1], cc = c->trip[3 * t + 2];
+            bk_out[i][t] = pref * M[(size_t)pair_index(nb, a, b) * nb + cc] / c->Tabc[t];
+        }
+    }
+    return POLYBIN_OK;
+}

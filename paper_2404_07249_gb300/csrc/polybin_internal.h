@@ -82,6 +82,8 @@ ContractGeom contract_geom_tc(int ng, int nh, long ncell);
 int run_contract_tc(polybin_ctx*, const float*, int, const float*, int, double*, size_t, double*);
 void destroy_extras(polybin_ctx*);
 void destroy_unwindowed(polybin_ctx*);
+void destroy_multi(polybin_ctx*);
+int ensure_err_flag(polybin_ctx*);
 
 }  // namespace pb
 
@@ -137,6 +139,11 @@ struct polybin_ctx {
 
     // device error flag of the kernels with bounded waits
     int* d_err = nullptr;
+    // stream capture in progress: kernels are enqueued without host synchronisation or read-backs
+    bool capturing = false;
+    // unique id (contexts at a reused address get a new id) and the cached multi-field graph
+    unsigned long long uid = 0;
+    void* multi = nullptr;
 
     // extension slots (unwindowed estimators)
     void* ext = nullptr;
