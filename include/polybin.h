@@ -84,9 +84,10 @@ int polybin_bk_ideal(polybin_ctx* ctx, const float* delta, int batch, double* bk
 /* Ideal bispectra of n_fields fields on possibly different grids (e.g. a batch of 96^3, 128^3 and 160^3
  * realisations).  ctxs[i] is the context of field i (fields on one grid share a context; all contexts must use
  * one stream, that of ctxs[0]); fields[i]: device float32 [N0][N1][N2] of ctxs[i]; bk_out[i]: host
- * [n_triplets(ctxs[i])], as polybin_bk_ideal.  The whole batch is captured into one CUDA graph and replayed
- * with a single graph launch; the graph is cached in ctxs[0] for repeated calls with the same contexts and
- * field pointers (a call with other arguments re-captures).  Profiling must be off. */
+ * [n_triplets(ctxs[i])], as polybin_bk_ideal.  The whole batch is captured into one CUDA graph on a private
+ * stream and replayed with a single graph launch, ordered after the work already queued on the contexts' stream;
+ * the graph is cached in ctxs[0] for repeated calls with the same contexts and field pointers (a call with other
+ * arguments re-captures).  Profiling must be off. */
 int polybin_bk_ideal_multi(polybin_ctx* const* ctxs, const float* const* fields, int n_fields, double* const* bk_out);
 
 /* ---- power spectrum (Sec. 3.4.1) ------------------------------------------------------------------------- */

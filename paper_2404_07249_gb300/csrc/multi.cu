@@ -1,6 +1,7 @@
 // Batched ideal bispectra over fields on (possibly) different grids: the whole batch -- per field the pruned
 // forward transform, the shell maps, the triplet contraction and the copy of its result to pinned host memory --
-// is captured once into a CUDA graph on the stream of the first context and replayed with a single graph launch.
+// is captured once into a CUDA graph on a private stream and replayed there with a single graph launch, ordered
+// after the work already queued on the contexts' stream.
 // The graph is cached in the first context, keyed by the context ids and field pointers of the call.
 #include <cuda_runtime.h>
 
@@ -13,6 +14,8 @@ namespace pb {
 
 struct MultiCache {
     std::vector<unsigned long long> key;
+    cudaStream_t cap = nullptr;             // private stream: capture and replay (the legacy stream cannot capture)
+    cudaEvent_t ev = nullptr;
     cudaGraphExec_t exec = nullptr;
     double* host = nullptr;                 // pinned: contraction results of every field
     std::vector<size_t> off;                // per-field offset into host
@@ -23,6 +26,8 @@ void destroy_multi(polybin_ctx* ctx) {
     if (!m) return;
     if (m->exec) cudaGraphExecDestroy(m->exec);
     if (m->host) cudaFreeHost(m->host);
+    if (m->ev) cudaEventDestroy(m->ev);
+    if (m->cap) cudaStreamDestroy(m->cap);
     delete m;
     ctx->multi = nullptr;
 }
@@ -86,11 +91,21 @@ extern "C" int polybin_bk_ideal_multi(polybin_ctx* const* ctxs, const float* con
             polybin_ctx* ctx = c0;
             PB_CUDA_OK(cudaHostAlloc((void**)&m->host, sizeof(double) * total, cudaHostAllocDefault));
         }
-        cudaStream_t st = c0->stream;
+        {
+            polybin_ctx* ctx = c0;
+            PB_CUDA_OK(cudaStreamCreateWithFlags(&m->cap, cudaStreamNonBlocking));
+            PB_CUDA_OK(cudaEventCreateWithFlags(&m->ev, cudaEventDisableTiming));
+        }
+        cudaStream_t st = m->cap;
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
-        if (e != cudaSuccess) return fail_cuda(c0, e, "cudaStreamBeginCapture", __FILE__, __LINE__);
-        for (int i = 0; i < n_fields; ++i) ctxs[i]->capturing = true;
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            destroy_multi(c0);
+            return fail_cuda(c0, e, "cudaStreamBeginCapture", __FILE__, __LINE__);
+        }
+        std::vector<cudaStream_t> saved(n_fields);
+        for (int i = 0; i < n_fields; ++i) { saved[i] = ctxs[i]->stream; ctxs[i]->stream = st; ctxs[i]->capturing = true; }
         rc = POLYBIN_OK;
         for (int i = 0; i < n_fields && !rc; ++i) {
             polybin_ctx* c = ctxs[i];
@@ -98,8 +113,9 @@ extern "C" int polybin_bk_ideal_multi(polybin_ctx* const* ctxs, const float* con
                                          : capture_field<float>(c, fields[i], m->host + m->off[i]);
             if (rc && c != c0) c0->err = c->err;
         }
-        for (int i = 0; i < n_fields; ++i) ctxs[i]->capturing = false;
+        for (int i = 0; i < n_fields; ++i) { ctxs[i]->capturing = false; ctxs[i]->stream = saved[i]; }
         e = cudaStreamEndCapture(st, &graph);
+        if (rc || e != cudaSuccess) cudaGetLastError();
         if (rc) {
             if (graph) cudaGraphDestroy(graph);
             destroy_multi(c0);
@@ -110,8 +126,11 @@ extern "C" int polybin_bk_ideal_multi(polybin_ctx* const* ctxs, const float* con
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) { destroy_multi(c0); return fail_cuda(c0, e, "cudaGraphInstantiate", __FILE__, __LINE__); }
     }
-    cudaError_t e = cudaGraphLaunch(m->exec, c0->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c0->stream);
+    // fence: the graph starts after the work already queued on the caller's stream
+    cudaError_t e = cudaEventRecord(m->ev, c0->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(m->cap, m->ev, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(m->exec, m->cap);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->cap);
     if (e != cudaSuccess) return fail_cuda(c0, e, "cudaGraphLaunch", __FILE__, __LINE__);
     for (int i = 0; i < n_fields; ++i) {
         polybin_ctx* c = ctxs[i];
