@@ -179,6 +179,11 @@ int polybin_get_stage_times(polybin_ctx* ctx, double* ms, long long* calls, int 
 /* Number of kernels this context has launched so far. */
 int polybin_launch_count(const polybin_ctx* ctx, long long* n);
 
+/* Failure-detection self-test: a kernel waits on an mbarrier phase that nothing completes, using the same bounded
+ * poll as the tensor-core pipeline; the wait gives up after 2^14 polls and sets the device error flag, the kernel
+ * returns and the context stays usable.  *timed_out = 1 when the bounded wait gave up (the expected outcome). */
+int polybin_selftest_wait(polybin_ctx* ctx, int* timed_out);
+
 /* ---- individual steps, for testing and composition (device pointers only) --------------------------------- */
 
 /* Dimensions [Bx][By][Bz] of the pruned half-spectrum box: all wave numbers n with |n_x|, |n_y| <= m and

@@ -56,6 +56,7 @@ _SIGS = {
     "polybin_bk_unwindowed": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                              ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "polybin_bk_ideal_multi": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "polybin_selftest_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
     "polybin_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
                                      ctypes.c_void_p]),
 }
@@ -194,6 +195,12 @@ class PolyBin:
         self._check(self.lib.polybin_get_stage_times(self.ctx, _ptr(ms), _ptr(calls), int(reset)),
                     "polybin_get_stage_times")
         return {n: (float(ms[i]), int(calls[i])) for i, n in enumerate(STAGES)}
+
+    def selftest_wait(self) -> bool:
+        """True when the bounded device-side wait gave up as designed (see polybin_selftest_wait)."""
+        t = ctypes.c_int(0)
+        self._check(self.lib.polybin_selftest_wait(self.ctx, ctypes.byref(t)), "polybin_selftest_wait")
+        return t.value == 1
 
     def launch_count(self) -> int:
         n = ctypes.c_longlong()

@@ -427,6 +427,20 @@ __global__ void __launch_bounds__(kThreads, 2) k_contract_tc(Params P) {
     if (warp == kMmaWarp) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
 }
 
+// Self-test of the bounded waits: one thread waits on an mbarrier phase that nothing completes; the wait gives up
+// after `limit` polls and raises the error flag, as a stalled pipeline would, and the kernel returns normally.
+__global__ void k_wait_selftest(int* err, unsigned limit) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        unsigned it = 0;
+        for (; it < limit; ++it)
+            if (mbar_try(&bar, 0)) break;
+        if (it == limit) atomicExch(err, 1);
+    }
+}
+
 }  // namespace tc
 
 bool split_tc_available() { return true; }
@@ -502,3 +516,16 @@ int run_contract_tc(polybin_ctx* ctx, const float* g, int ng, const float* h, in
 }
 
 }  // namespace pb
+
+extern "C" int polybin_selftest_wait(polybin_ctx* ctx, int* timed_out) {
+    if (!ctx || !timed_out) return pb::fail(ctx, POLYBIN_EINVAL, "polybin_selftest_wait: NULL argument");
+    int rc = pb::ensure_err_flag(ctx);
+    if (rc) return rc;
+    PB_CUDA_OK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
+    pb::tc::k_wait_selftest<<<1, 32, 0, ctx->stream>>>(ctx->d_err, 1u << 14);
+    ctx->launches++;
+    PB_CUDA_OK(cudaGetLastError());
+    PB_CUDA_OK(cudaMemcpyAsync(timed_out, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    PB_CUDA_OK(cudaStreamSynchronize(ctx->stream));
+    return POLYBIN_OK;
+}
