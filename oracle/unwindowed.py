@@ -67,11 +67,12 @@ def pk_fisher_draw(a, n, w, bins, mu2, nb, ells) -> np.ndarray:
     SA = _fft.fftn(s * a)
     alphas = alpha_list_p(nb, ells)
     Lw = {ell: binning.legendre(ell, mu2) for ell in ells}
-    Y = np.stack([np.where(bins == b, Lw[ell] * A, 0.0).ravel() for ell, b in alphas])
+    sel = bins >= 0          # Y_beta vanishes outside the binned modes: the dot product runs over those only
+    Y = np.stack([np.where(bins == b, Lw[ell] * A, 0.0)[sel] for ell, b in alphas])
     X = np.empty_like(Y)
     for i, (ell, b) in enumerate(alphas):
         q = _fft.ifftn(np.where(bins == b, Lw[ell] * SA, 0.0)).real
-        X[i] = _fft.fftn(s * q).ravel()
+        X[i] = _fft.fftn(s * q)[sel]
     return 0.5 * (np.conj(X) @ Y.T).real / N
 
 
