@@ -156,6 +156,74 @@ def run_reference(args) -> None:
     print(json.dumps(line), flush=True)
 
 
+def _time(fn, reps=1):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        fn()
+    torch.cuda.synchronize()
+    return (time.perf_counter() - t0) / reps
+
+
+def other_workloads(pkg, synth, stream, dev) -> dict:
+    """Throughput of the remaining standard workloads (host-timed around synchronising C-ABI calls)."""
+    import torch
+    out = {}
+    # 64^3 GRF: plain FP64 path, B (8 bins) and P_ell (16 bins, ell 0,2,4)
+    w = synth.WORKLOADS[1]
+    f = torch.from_numpy(synth.workload_field(1, 0)).to(dev)
+    pbb = pkg.PolyBin(w.grid, w.box, w.bk_edges, prec="fp64", stream=stream.cuda_stream)
+    pbp = pkg.PolyBin(w.grid, w.box, w.pk_edges, lmax=4, prec="fp64", stream=stream.cuda_stream)
+    pbb.num_triplets()
+    tb = _time(lambda: pbb.bk_ideal(f), 5)
+    tp = _time(lambda: pbp.pk(f), 5)
+    out["grf64_fp64"] = {"bk_per_s": 1 / tb, "pk_per_s": 1 / tp, "n_triplets": pbb.num_triplets()}
+    pbb.close(); pbp.close()
+    # 256^3 lognormal, 20 bins, split-TF32
+    w = synth.WORKLOADS[2]
+    f = torch.from_numpy(synth.workload_field(2, 0)).to(dev)
+    pb = pkg.PolyBin(w.grid, w.box, w.bk_edges, prec="split", stream=stream.cuda_stream)
+    pb.num_triplets()
+    t = _time(lambda: pb.bk_ideal(f), 5)
+    out["lognormal256_split"] = {"bk_per_s": 1 / t, "n_triplets": pb.num_triplets()}
+    pb.close()
+    del f
+    # 64 fields of 96^3 / 128^3 / 160^3, 12 bins, one CUDA graph
+    w = synth.WORKLOADS[4]
+    grids = [(g, g, g) for g in w.grids]
+    pbs = {g: pkg.PolyBin(g, w.box, w.bk_edges, prec="split", stream=stream.cuda_stream) for g in grids}
+    order = [grids[i % len(grids)] for i in range(w.n_fields)]
+    fields = [torch.from_numpy(synth.workload_field(4, i)).to(dev) for i in range(w.n_fields)]
+    t = _time(lambda: pkg.bk_ideal_multi([pbs[g] for g in order], fields), 3)
+    out["lognormal_batch64_split_graph"] = {"fields_per_s": w.n_fields / t, "graph_launches_per_batch": 1}
+    for pb in pbs.values():
+        pb.close()
+    del fields
+    # masked 256^3: P and B Monte Carlo Fisher (per draw / draw pair) and the unwindowed estimates
+    w = synth.WORKLOADS[5]
+    n = synth.survey_mask(w.grid, (w.box,) * 3, 5000).astype(np.float32)
+    nd = torch.from_numpy(n).to(dev)
+    pbp = pkg.PolyBin(w.grid, w.box, w.pk_edges, lmax=4, prec="split", stream=stream.cuda_stream)
+    wd = pbp.fkp_weights(nd, w.extra["P0"])
+    dG = torch.from_numpy((n * synth.workload_field(5, 0)).astype(np.float32)).to(dev)
+    tfp = _time(lambda: pbp.fisher_draws(nd, wd, 1, 0, 0, 1), 1)
+    pbp.fisher(nd, wd, 2, 1, 0)
+    tpu = _time(lambda: pbp.pk_unwindowed(dG, wd), 3)
+    pbp.close()
+    pbb = pkg.PolyBin(w.grid, w.box, w.bk_edges, prec="split", stream=stream.cuda_stream)
+    nt = pbb.num_triplets()
+    tfb = _time(lambda: pbb.fisher_draws(nd, wd, 1, 1, 0, 1), 1)
+    mocks = torch.stack([torch.from_numpy((n * synth.workload_field(5, 1 + i)).astype(np.float32)) for i in range(2)]).to(dev)
+    pbb.fisher(nd, wd, 1, 1, 1)
+    tbu = _time(lambda: pbb.bk_unwindowed(dG, wd, mocks), 1)
+    pbb.close()
+    out["masked256_split"] = {"pk_fisher_s_per_draw": tfp, "bk_fisher_s_per_draw_pair": tfb, "n_triplets": nt,
+                              "pk_unwindowed_s": tpu, "bk_unwindowed_s_with_2_mocks": tbu}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -166,6 +234,8 @@ def main():
     ap.add_argument("--config", type=int, default=3)
     ap.add_argument("--fp64-steps", type=int, default=1, help="steps of the FP64 GPU comparator (0 = skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--all-configs", action="store_true",
+                    help="also time the other workloads (64^3 FP64, 256^3, batched uneven grids, masked 256^3)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -318,6 +388,10 @@ def main():
 
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(args.config, field, edges, box)
+    if args.all_configs and world == 1:
+        del d
+        torch.cuda.empty_cache()
+        line["other_workloads"] = other_workloads(pkg, synth, stream, dev)
     pb.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
