@@ -166,13 +166,14 @@ int polybin_solve(polybin_ctx* ctx, const double* A, int n, const double* B, int
 
 /* ---- instrumentation -------------------------------------------------------------------------------------- */
 
-/* Enable (on != 0) or disable per-stage timing.  When enabled, each pipeline stage is bracketed by CUDA events on
- * the context stream and the host waits for the closing event, so stages are timed exactly but back to back
- * calls lose their overlap; leave it off for throughput measurements. */
+/* Enable (on != 0) or disable per-stage timing.  When enabled, each pipeline stage is bracketed by a pair of CUDA
+ * events on the context stream.  Recording does not block the host: the elapsed times are read back when
+ * polybin_get_stage_times is called, or when 64 brackets have accumulated.  Stages enqueued during a stream
+ * capture are not timed.  The first enable creates 128 events (POLYBIN_ECUDA if that fails). */
 int polybin_set_profiling(polybin_ctx* ctx, int on);
 
 /* Accumulated device milliseconds and call counts of the stages since the last reset (reset != 0 clears them
- * after reading).  Stage order: 0 forward transform (a1), 1 shell filter + inverse transforms (a2),
+ * after reading); waits for the stop events of brackets still in flight.  Stage order: 0 forward transform (a1), 1 shell filter + inverse transforms (a2),
  * 2 triplet contraction (a3), 3 P_ell binning (a4).  ms and calls: host arrays of 4 (calls may be NULL). */
 int polybin_get_stage_times(polybin_ctx* ctx, double* ms, long long* calls, int reset);
 

@@ -592,6 +592,10 @@ extern "C" void polybin_destroy(polybin_ctx* ctx) {
     for (void* p : ptrs)
         if (p) cudaFree(p);
     destroy_extras(ctx);
+    if (ctx->tev[0]) {
+        harvest_stage_times(ctx);
+        for (cudaEvent_t ev : ctx->tev) cudaEventDestroy(ev);
+    }
     delete ctx;
 }
 
@@ -797,9 +801,15 @@ extern "C" int polybin_bk_pk_ideal(polybin_ctx* ctx, const float* delta, int bat
 
 extern "C" int polybin_set_profiling(polybin_ctx* ctx, int on) {
     if (!ctx) return fail(ctx, POLYBIN_EINVAL, "polybin_set_profiling: NULL context");
-    if (on && !ctx->ev[0]) {
-        PB_CUDA_OK(cudaEventCreate(&ctx->ev[0]));
-        PB_CUDA_OK(cudaEventCreate(&ctx->ev[1]));
+    if (on && !ctx->tev[0]) {
+        for (int i = 0; i < 2 * polybin_ctx::kTimerSlots; ++i) {
+            cudaError_t e = cudaEventCreate(&ctx->tev[i]);
+            if (e != cudaSuccess) {
+                for (int j = 0; j < i; ++j) cudaEventDestroy(ctx->tev[j]);
+                for (int j = 0; j < i; ++j) ctx->tev[j] = nullptr;
+                return fail_cuda(ctx, e, "cudaEventCreate", __FILE__, __LINE__);
+            }
+        }
     }
     ctx->profiling = on != 0;
     return POLYBIN_OK;
@@ -807,6 +817,7 @@ extern "C" int polybin_set_profiling(polybin_ctx* ctx, int on) {
 
 extern "C" int polybin_get_stage_times(polybin_ctx* ctx, double* ms, long long* calls, int reset) {
     if (!ctx || !ms) return fail(ctx, POLYBIN_EINVAL, "polybin_get_stage_times: NULL argument");
+    harvest_stage_times(ctx);
     for (int s = 0; s < kNumStages; ++s) {
         ms[s] = ctx->stage_ms[s];
         if (calls) calls[s] = ctx->stage_calls[s];

@@ -130,12 +130,18 @@ struct polybin_ctx {
     std::vector<int> trip;
     std::vector<double> Tabc, Nabc;
 
-    // instrumentation: kernel launches issued, and (when enabled) per-stage device time from CUDA events
+    // instrumentation: kernel launches issued, and (when enabled) per-stage device time from CUDA events.
+    // Stage brackets are recorded without blocking into tev (start, stop pairs) and read back lazily: when the
+    // slots run out, or when the caller asks for the times.
     long launches = 0;
     bool profiling = false;
     double stage_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     long stage_calls[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    cudaEvent_t ev[2] = {nullptr, nullptr};
+    static constexpr int kTimerSlots = 64;
+    cudaEvent_t tev[2 * kTimerSlots] = {};
+    int tstage[kTimerSlots] = {};
+    int tused = 0;        // slots recorded since the last read-back
+    bool topen = false;   // a stage bracket is open (brackets do not nest)
 
     // device error flag of the kernels with bounded waits
     int* d_err = nullptr;
@@ -151,21 +157,36 @@ struct polybin_ctx {
 
 namespace pb {
 enum Stage { kStageForward = 0, kStageShells = 1, kStageContract = 2, kStagePk = 3, kNumStages = 4 };
-// Brackets a pipeline stage with CUDA events on the context stream when profiling is enabled.
+// Adds the elapsed times of the recorded stage brackets to stage_ms / stage_calls (waits for their stop events).
+inline void harvest_stage_times(polybin_ctx* ctx) {
+    for (int i = 0; i < ctx->tused; ++i) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(ctx->tev[2 * i + 1]) == cudaSuccess &&
+            cudaEventElapsedTime(&ms, ctx->tev[2 * i], ctx->tev[2 * i + 1]) == cudaSuccess) {
+            ctx->stage_ms[ctx->tstage[i]] += ms;
+            ctx->stage_calls[ctx->tstage[i]] += 1;
+        }
+    }
+    ctx->tused = 0;
+}
+
+// Brackets a pipeline stage with CUDA events on the context stream when profiling is enabled.  Recording does not
+// block the host; stream captures are not bracketed.
 struct StageTimer {
     polybin_ctx* ctx;
-    int stage;
-    StageTimer(polybin_ctx* c, int s) : ctx(c), stage(s) {
-        if (ctx->profiling) cudaEventRecord(ctx->ev[0], ctx->stream);
+    int slot = -1;
+    StageTimer(polybin_ctx* c, int s) : ctx(c) {
+        if (!ctx->profiling || ctx->capturing || ctx->topen || !ctx->tev[0]) return;
+        if (ctx->tused == polybin_ctx::kTimerSlots) harvest_stage_times(ctx);
+        slot = ctx->tused++;
+        ctx->tstage[slot] = s;
+        ctx->topen = true;
+        cudaEventRecord(ctx->tev[2 * slot], ctx->stream);
     }
     ~StageTimer() {
-        if (!ctx->profiling) return;
-        float ms = 0.f;
-        cudaEventRecord(ctx->ev[1], ctx->stream);
-        if (cudaEventSynchronize(ctx->ev[1]) == cudaSuccess && cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]) == cudaSuccess) {
-            ctx->stage_ms[stage] += ms;
-            ctx->stage_calls[stage] += 1;
-        }
+        if (slot < 0) return;
+        cudaEventRecord(ctx->tev[2 * slot + 1], ctx->stream);
+        ctx->topen = false;
     }
 };
 }  // namespace pb
