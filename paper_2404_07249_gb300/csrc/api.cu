@@ -495,7 +495,18 @@ int ensure_triplets(polybin_ctx* ctx) {
                     ctx->Nabc.push_back(cnt);
                 }
             }
+    const size_t nt = ctx->Nabc.size();
+    std::vector<int> m(std::max(nt, (size_t)1), 0);
+    for (size_t t = 0; t < nt; ++t)
+        m[t] = pair_index(nb, ctx->trip[3 * t], ctx->trip[3 * t + 1]) * nb + ctx->trip[3 * t + 2];
+    polybin_ctx* c = ctx;
+    PB_CUDA_OK_C(cudaMalloc(&c->d_S, sizeof(double) * m.size()));
+    PB_CUDA_OK_C(cudaMalloc(&c->d_trip_m, sizeof(int) * m.size()));
+    PB_CUDA_OK_C(cudaMemcpy(c->d_trip_m, m.data(), sizeof(int) * m.size(), cudaMemcpyHostToDevice));
     ctx->trip_ready = true;
+    // the tensor-core plan is built now, outside any later stream capture
+    if (ctx->prec == POLYBIN_SPLIT_TF32X3 && nt > 0 && tc_shape_ok(ctx, (const float*)ctx->w.g, nb, nullptr, nb))
+        return prepare_triplet_tc(ctx);
     return POLYBIN_OK;
 }
 
@@ -633,9 +644,9 @@ static void pk_normalise(const polybin_ctx* ctx, const std::vector<double>& num,
 template <typename T>
 static int bk_pk_t(polybin_ctx* ctx, const float* delta, int batch, double* bk_out, double* pk_out) {
     int rc;
-    const int nb = ctx->nb, np = nb * (nb + 1) / 2;
+    const int nb = ctx->nb;
     const size_t nt = ctx->Nabc.size();
-    std::vector<double> M((size_t)np * nb), num;
+    std::vector<double> S(std::max(nt, (size_t)1)), num;
     const double pref = ctx->vol * ctx->vol / ((double)ctx->ncell * (double)ctx->ncell * (double)ctx->ncell);
     for (int f = 0; f < batch; ++f) {
         const float* in;
@@ -646,16 +657,12 @@ static int bk_pk_t(polybin_ctx* ctx, const float* delta, int batch, double* bk_o
             if ((rc = run_pkbin<T>(ctx, (const C<T>*)w.box, num))) return rc;
             pk_normalise(ctx, num, pk_out + (size_t)f * ctx->nell * nb);
         }
-        if (!bk_out) continue;
+        if (!bk_out || nt == 0) continue;
         if ((rc = run_shells<T>(ctx, (const C<T>*)w.box, (C<T>*)w.u1, (C<T>*)w.u2, (T*)w.g, 0))) return rc;
-        if ((rc = run_contract_any<T>(ctx, (const T*)w.g, nb, nullptr, nb, w.partial, w.partial_cap, w.mout))) return rc;
-        PB_CUDA_OK(cudaMemcpyAsync(M.data(), w.mout, sizeof(double) * M.size(), cudaMemcpyDeviceToHost, ctx->stream));
+        if ((rc = run_triplet_sums<T>(ctx, (const T*)w.g, ctx->d_S))) return rc;
+        PB_CUDA_OK(cudaMemcpyAsync(S.data(), ctx->d_S, sizeof(double) * nt, cudaMemcpyDeviceToHost, ctx->stream));
         PB_CUDA_OK(cudaStreamSynchronize(ctx->stream));
-        for (size_t t = 0; t < nt; ++t) {
-            const int a = ctx->trip[3 * t], b = ctx->trip[3 * t + 1], c = ctx->trip[3 * t + 2];
-            const double S = M[(size_t)pair_index(nb, a, b) * nb + c];
-            bk_out[(size_t)f * nt + t] = pref * S / ctx->Tabc[t];
-        }
+        for (size_t t = 0; t < nt; ++t) bk_out[(size_t)f * nt + t] = pref * S[t] / ctx->Tabc[t];
     }
     return POLYBIN_OK;
 }
@@ -663,24 +670,20 @@ static int bk_pk_t(polybin_ctx* ctx, const float* delta, int batch, double* bk_o
 template <typename T>
 static int bk_ideal_t(polybin_ctx* ctx, const float* delta, int batch, double* bk_out) {
     int rc;
-    const int nb = ctx->nb, np = nb * (nb + 1) / 2;
     const size_t nt = ctx->Nabc.size();
-    std::vector<double> M((size_t)np * nb);
+    std::vector<double> S(std::max(nt, (size_t)1));
     const double pref = ctx->vol * ctx->vol / ((double)ctx->ncell * (double)ctx->ncell * (double)ctx->ncell);
+    if (nt == 0) return POLYBIN_OK;
     for (int f = 0; f < batch; ++f) {
         const float* in;
         if ((rc = resolve_input(ctx, delta + (size_t)f * ctx->ncell, ctx->ncell, &in))) return rc;
         Work& w = ctx->w;
         if ((rc = run_forward<T, float, float>(ctx, in, (const float*)nullptr, (const float*)nullptr, (C<T>*)w.t1, (C<T>*)w.t2, (C<T>*)w.box))) return rc;
         if ((rc = run_shells<T>(ctx, (const C<T>*)w.box, (C<T>*)w.u1, (C<T>*)w.u2, (T*)w.g, 0))) return rc;
-        if ((rc = run_contract_any<T>(ctx, (const T*)w.g, nb, nullptr, nb, w.partial, w.partial_cap, w.mout))) return rc;
-        PB_CUDA_OK(cudaMemcpyAsync(M.data(), w.mout, sizeof(double) * M.size(), cudaMemcpyDeviceToHost, ctx->stream));
+        if ((rc = run_triplet_sums<T>(ctx, (const T*)w.g, ctx->d_S))) return rc;
+        PB_CUDA_OK(cudaMemcpyAsync(S.data(), ctx->d_S, sizeof(double) * nt, cudaMemcpyDeviceToHost, ctx->stream));
         PB_CUDA_OK(cudaStreamSynchronize(ctx->stream));
-        for (size_t t = 0; t < nt; ++t) {
-            const int a = ctx->trip[3 * t], b = ctx->trip[3 * t + 1], c = ctx->trip[3 * t + 2];
-            const double S = M[(size_t)pair_index(nb, a, b) * nb + c];
-            bk_out[(size_t)f * nt + t] = pref * S / ctx->Tabc[t];
-        }
+        for (size_t t = 0; t < nt; ++t) bk_out[(size_t)f * nt + t] = pref * S[t] / ctx->Tabc[t];
     }
     return POLYBIN_OK;
 }

@@ -1,82 +1,109 @@
 // Tensor-core (tcgen05, sm_103a) triplet contraction with 3-term split-TF32 products.
 //
-// Computes M[p][i] = sum_x P_p(x) h_i(x), P_p = g_j g_k for pairs p = (j <= k), as the GEMM
-// D[128-row pair tile][32 singles] += A[pairs][cells] . B[singles][cells]^T over the cells of each CTA
-// (Sec. 4.3.1, eq. beta-def: the real-space sum of the separable bispectrum; with h = g, S_abc for all
-// a <= b and all c).  Each value v is split as v = hi + lo with hi = rna_tf32(v), lo = v - hi, and the
-// product is accumulated as hi_a hi_b + hi_a lo_b + lo_a hi_b (the lo_a lo_b term, ~2^-22 relative, is
-// dropped).
+// Computes sums M[(j, k)][i] = sum_x g_j(x) g_k(x) h_i(x) over the cells x (Sec. 4.3.1, eq. beta-def: the
+// real-space sum of the separable bispectrum; with h = g the entry of pair (b, c) and single a is S_abc).  The work
+// is a set of 128-row tiles: every row is one pair (j, k) and every tile has a window of W singles
+// [s0, s0 + W), W in {16, 32}.  For the ideal bispectrum only the pairs and singles of closed triplets enter:
+// the triplet a <= b <= c is read from pair (b, c) and single a, which prunes the 465 pairs x 30 singles of a
+// 30-bin binning to 255 pairs in two tiles with windows of 16 and 32 singles.
 //
-// Work split: a CTA takes one contiguous range of cells and one row group of two 128-row pair tiles (256
-// pairs); two CTAs run on each SM (the grid covers 2 x 152 CTAs over row groups and cell ranges), so two
-// independent producer/MMA pipelines overlap each other's handshake latency.
+// Arithmetic: every value v is split as v = hi + lo, hi = v rounded to TF32 (nearest, ties away from zero),
+// lo = v - hi in FP32 (read by the MMA as TF32).  Per tile and K = 8 cells two MMAs run, on independent
+// accumulators:  D_m[:, 0:2W] += A_hi . [B_hi | B_lo]^T  (N = 2W: hi*hi in columns < W, hi*lo in columns >= W) and
+// D_l[:, 0:W] += A_lo . B_hi^T  (N = W); the lo*lo term (~2^-22 relative) is dropped.  A = pair products (g_j g_k in
+// FP32, then split), B = singles.  The tensor core's internal accumulation is not round-to-nearest, so D restarts
+// every 64 cells (8 MMAs per accumulator column); the epilogue adds D into FP32 registers (round-to-nearest) and
+// those into FP64 shared memory every 2048 cells.  Cross-CTA sums are FP64 in a fixed order (deterministic).
 //
-// Warp roles (256 threads per CTA):
-//   warps 0-3   producers: stream the map tiles into a shared-memory ring with cp.async, form the pair
-//               products (a thread owns one TMEM lane, i.e. one row of both pair tiles), split them and write
-//               them into TMEM with tcgen05.st (the A operand never touches shared memory), and convert the
-//               singles tile to hi/lo TF32 in the canonical no-swizzle K-major layout (the B operand).
-//   warps 4-7   epilogue: every kPeriod chunks (64 cells) read the accumulators with tcgen05.ld into FP32
-//               register sums (round-to-nearest), every kSpill periods add those into FP64 partials in
-//               shared memory; finally write the CTA's FP64 partials.  Warp 4 allocates TMEM.  Lane 0 of
-//               warps 4 and 5 issues the tcgen05.mma (A from TMEM, B from shared memory, D in TMEM) and the
-//               tcgen05.commit of one pair tile for period q before its warp drains period q-1 (D is double
-//               buffered); the 128x32x8 MMAs are short, so one issuing thread per tile keeps more in flight.
-// Precision: the tensor core's internal accumulation is not round-to-nearest, so its error grows with the
-// number of MMAs accumulated into one D; the 64-cell periods keep that chain at 24 MMAs.
-// TMEM (256 columns per CTA): D double buffer 2 x (2 tiles x 32 columns) at [0, 128); A ring = 2 stages x
-// (2 tiles x (16 hi + 16 lo)) at [128, 256).  Every mbarrier wait is bounded; on timeout the CTA raises an
-// error flag and exits after draining its own asynchronous work.
+// Measured on this part (and shaping the design): one thread issues a tcgen05.mma per ~50-120 cycles whatever its
+// size; consecutive MMAs into the same accumulator columns complete ~150 cycles apart, so independent accumulators
+// and wide N per instruction matter more than the tensor core's peak rate; tensor memory (512 columns) is shared by
+// the accumulators (one buffer, D_m + D_l = 3W columns a tile) and the ring of A stages (64 columns a tile a stage).
+//
+// One CTA per SM over a contiguous range of cells, in stages of 32 cells (one TMA ring slot); warp roles:
+//   warp 0       TMEM allocation; lane 0 streams the maps with TMA (cp.async.bulk.tensor, 32 cells x all maps per
+//                load, 128-byte swizzle) into an 8-slot shared-memory ring.
+//   warps 1-8    producers, two groups of four warps; group g makes cells 16g..16g+15 of every stage, so the two
+//                groups overlap each other's load and store latencies.  A thread owns one TMEM lane, i.e. one row
+//                of every tile: it forms the pair products, splits them (packed FP32 pairs) and writes hi / lo
+//                straight into tensor memory (tcgen05.st: the A operand never touches shared memory), and converts
+//                its share of every tile's window of singles into the hi / lo B operand (canonical no-swizzle
+//                K-major layout) in shared memory.
+//   warps 9-11   MMA issue: warp 9 + t waits for the stage (all lanes, converged) and its lane 0 issues tile t's
+//                MMAs and commits them to the stage's release barrier.
+//   warps 12-15  epilogue: after every period read D with tcgen05.ld (each warp its TMEM lane quarter), release
+//                it to the issuers, accumulate.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
 
 #include "polybin_internal.h"
 
 namespace pb {
 namespace tc {
 
-constexpr int kKC = 16;           // cells per chunk (two K=8 MMA steps)
-constexpr int kStages = 2;        // A/B pipeline depth
-constexpr int kRing = 4;          // map-tile ring (prefetch distance 3)
-constexpr int kPeriod = 4;        // chunks per tensor-memory accumulation period (64 cells)
-constexpr int kSpill = 32;        // periods per FP32 register accumulation before the FP64 update (2048 cells)
-constexpr int kMaxTiles = 4;      // pair tiles of 128 rows over all row groups (npairs <= 512)
-constexpr int kTiles = 2;         // pair tiles per CTA (a row group of 256 pairs); two CTAs per SM
-constexpr int kNCols = 32;        // singles per tile (nh <= 32)
-constexpr int kGS = 20;           // floats per map row in the ring (16 + 4 pad: conflict-free LDS.128)
-constexpr int kProducerWarps = 4;
-constexpr int kProducers = 32 * kProducerWarps;
-constexpr int kMmaWarp = kProducerWarps;   // first epilogue warp; allocates TMEM
-constexpr int kIssuers = kTiles;           // epilogue warps 4, 5: lane 0 issues the MMAs of tile (warp - 4)
-constexpr int kEpilogue = 128;             // 4 epilogue warps
-constexpr int kThreads = kProducers + kEpilogue;
-constexpr int kTmemCols = 256;             // D 2 x (2 tiles x 32) at [0, 128); A 2 stages x (2 tiles x 32) at [128, 256)
+constexpr int kSlotCells = 32;     // cells per TMA box row (128 bytes)
+constexpr int kRingSlots = 8;
+constexpr int kKC = 32;            // cells per A stage = one ring slot (four K = 8 MMA steps)
+constexpr int kMaxAStages = 6;
+constexpr int kPeriod = 2;         // A stages per TMEM accumulation period (64 cells)
+constexpr int kSpill = 32;         // periods per FP32 register sum (2048 cells)
+constexpr int kDBuf = 1;           // accumulator buffers (1: the issuers wait for the epilogue between periods)
+constexpr int kMaxTiles = 3;       // tiles per CTA
+constexpr int kMaxUnits = 3;       // 16-column output units per CTA (16 FP32 sums each, in registers)
+constexpr int kMaxGroups = 4;      // row groups (grid.y)
+constexpr int kProdGroups = 2;     // producer warp groups; group g makes half g (16 cells) of every stage
+constexpr int kProdWarps = 4 * kProdGroups;
+constexpr int kIssWarps = kMaxTiles;   // lane 0 of warp t issues the MMAs of tile t
+constexpr int kEpiWarps = 4;
+constexpr int kWarps = 1 + kProdWarps + kIssWarps + kEpiWarps;
+constexpr int kThreads = 32 * kWarps;
+constexpr int kMinSmem = 120 * 1024;   // one CTA per SM (the CTA allocates all 512 TMEM columns)
 constexpr unsigned kSpinLimit = 1u << 22;
 
+struct GroupDesc {
+    int tile0;                 // first tile (row table index / 128)
+    int ntiles, nunits, nA;    // tiles, 16-column units, A stages
+    int unit_base;             // first unit of this group in the partial layout
+    int d_cols;                // TMEM columns of one accumulator buffer (kDBuf buffers at 0, d_cols, ...)
+    int a_col0;                // first TMEM column of the A ring
+    int bstage_bytes;          // B operand bytes per A stage (all windows)
+    int tile_w[kMaxTiles];
+    int dm_col[kMaxTiles];     // TMEM column of tile t's hi*[hi | lo] accumulator (2W columns)
+    int dl_col[kMaxTiles];     // TMEM column of tile t's lo*hi accumulator (W columns)
+    int tile_s0[kMaxTiles];    // first single of tile t's window
+    int tile_boff[kMaxTiles];  // byte offset of tile t's B block within a B stage (2W rows x 32 cells)
+    int unit_tile[kMaxUnits], unit_c[kMaxUnits];
+};
+
 struct Params {
-    const float* g;
-    const float* h;        // may equal g
-    long ncell;
-    long cells_cta;
-    int ng, nh, npairs, ntiles;
-    const short2* pairs;
-    double* partial;       // [gridDim.x][npairs][nh]
-    int* err;              // set to 1 on a timed-out wait
+    long ncell, cells_cta;
+    int ng, nh, hsep, h_row0;  // maps in the slot; singles; singles from the h part; first h row in a slot
+    int slot_bytes, off_b, off_acc, off_bar;
+    int total_units;
+    const short2* rows;        // [tiles][128] pairs (j, k); (-1, -1) pads
+    double* partial;           // [gridDim.x][total_units][16][128]
+    int* err;
+    GroupDesc grp[kMaxGroups];
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
-
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
 }
-
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar)) : "memory");
 }
-
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -87,58 +114,108 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait; returns false (and raises the abort flag) if the phase did not complete in time or another
-// role aborted.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err,
-                                          int backoff) {
+// Non-blocking test of a phase (no suspension): the fast path of the waits below when the phase is already done.
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait of one thread; false (and the abort flag raised) on timeout or when another role aborted.
+__device__ __forceinline__ bool thread_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err) {
+    if (mbar_test(bar, parity)) return true;
     for (unsigned it = 0; it < kSpinLimit; ++it) {
         if (mbar_try(bar, parity)) return true;
         if (*abort_flag) return false;
-        if (backoff) __nanosleep(64);
     }
     *abort_flag = 1;
     atomicExch(err, 1);
+    return false;
+}
+// Bounded wait used while shutting down (no abort check): lets in-flight asynchronous work land.
+__device__ __forceinline__ void drain_wait(uint64_t* bar, uint32_t parity, int* err) {
+    for (unsigned it = 0; it < kSpinLimit; ++it)
+        if (mbar_try(bar, parity)) return;
+    atomicExch(err, 1);
+}
+// Bounded wait of a whole warp with a warp-uniform outcome (the warp then runs .sync.aligned instructions).
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err) {
+    if (__all_sync(0xffffffffu, mbar_test(bar, parity))) return true;
+    for (unsigned it = 0; it < kSpinLimit; ++it) {
+        const bool done = mbar_try(bar, parity);
+        if (__all_sync(0xffffffffu, done)) return true;
+        if (__any_sync(0xffffffffu, *abort_flag != 0)) return false;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        *abort_flag = 1;
+        atomicExch(err, 1);
+    }
+    __syncwarp();
     return false;
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ uint32_t to_tf32(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+// Packed FP32 pairs (two floats in one 64-bit register; sm_100+ f32x2 arithmetic).
+__device__ __forceinline__ uint64_t f2pack(float a, float b) {
+    return (uint64_t)__float_as_uint(a) | ((uint64_t)__float_as_uint(b) << 32);
+}
+__device__ __forceinline__ uint64_t mul_x2(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
     return r;
 }
-
-// v = hi + lo with hi = rna_tf32(v) and lo = v - hi exact in FP32; the MMA reads lo's leading 11 bits.
-__device__ __forceinline__ void split2(float v, uint32_t& hi, uint32_t& lo) {
-    hi = to_tf32(v);
-    lo = __float_as_uint(v - __uint_as_float(hi));
+__device__ __forceinline__ uint64_t sub_x2(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+// Two values at once: v = hi + lo with hi = v rounded to TF32 (nearest, ties away from zero: add half a unit of the
+// 10-bit mantissa, bit 12, and clear the 13 low bits; a carry moves into the exponent as it should) and lo = v - hi
+// in FP32.  lo is symmetric about zero, so the tensor core's truncation of lo to TF32 is unbiased.  (When v is a
+// product, the compiler may fuse the multiply into the subtraction; lo then also carries the product's rounding
+// error, which only makes hi + lo closer to the exact product.)
+__device__ __forceinline__ void split_x2(uint64_t v, uint64_t& hi, uint64_t& lo) {
+    const uint32_t h0 = ((uint32_t)v + 0x1000u) & 0xFFFFE000u;
+    const uint32_t h1 = ((uint32_t)(v >> 32) + 0x1000u) & 0xFFFFE000u;
+    hi = (uint64_t)h0 | ((uint64_t)h1 << 32);
+    lo = sub_x2(v, hi);
 }
 
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* v) {
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t* v) {
     asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15, %16};" ::"r"(taddr),
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
         "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
-        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
-        : "memory");
+        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]),
+        "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]),
+        "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31]));
 }
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* v) {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
         : "r"(taddr)
         : "memory");
 }
+// tcgen05.wait::ld with the loaded registers as operands, so that no use of them is scheduled before the wait.
+__device__ __forceinline__ void tmem_wait_ld16(uint32_t* v) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]),
+                   "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15])
+                 :
+                 : "memory");
+}
 
-// Shared-memory matrix descriptor, no swizzle (canonical K-major "interleaved" layout): core matrices of
-// 8 rows x 16 bytes; LBO = byte distance between core matrices adjacent in K, SBO = between 8-row groups.
+// Shared-memory matrix descriptor, no swizzle (canonical K-major layout): core matrices of 8 rows x 16 bytes;
+// LBO = byte distance between core matrices adjacent in K, SBO = between 8-row groups.
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
@@ -148,7 +225,7 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t
     return d;                 // base offset 0, layout type 0 (no swizzle)
 }
 
-// Instruction descriptor: kind::tf32, D = F32, A = B = TF32, both K-major, M = 128, N = 32.
+// Instruction descriptor: kind::tf32, D = F32, A = B = TF32, both K-major.
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
@@ -161,270 +238,368 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint32_t a_tmem, uint6
         "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accum)
         : "memory");
 }
-
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");
 }
 
-// Named-barrier AND-vote over the 128 producer threads (barrier 1): every producer gets the same answer.
-__device__ __forceinline__ bool producers_all(bool v) {
-    uint32_t r;
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
     asm volatile(
-        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.and.pred q, 1, 128, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
-        : "=r"(r)
-        : "r"((uint32_t)v)
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
         : "memory");
-    return r != 0;
 }
 
-__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
-                 : "memory");
+// 16-byte chunk `ch` (0..7) of map row `r` in a ring slot written by TMA with the 128-byte swizzle: within every
+// 1024-byte block the chunk index is XORed with the row index modulo 8.
+__device__ __forceinline__ const float4* ring_chunk(const unsigned char* slot, int r, int ch) {
+    return reinterpret_cast<const float4*>(slot + r * 128 + ((ch ^ (r & 7)) << 4));
 }
 
-__global__ void __launch_bounds__(kThreads, 2) k_contract_tc(Params P) {
-    extern __shared__ __align__(1024) unsigned char smem[];
-    double* acc64 = reinterpret_cast<double*>(smem);                                   // [kTiles][32][128]
-    unsigned char* bbase = smem + (size_t)kTiles * kNCols * 128 * sizeof(double);      // B stages
-    const int BSTAGE = 2 * kNCols * kKC * 4;                                            // hi + lo, 4 KB
-    float* ring = reinterpret_cast<float*>(bbase + kStages * BSTAGE);                   // [kRing][rows][kGS]
-    const int rows = P.ng + (P.h != P.g ? P.nh : 0);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(ring + (size_t)kRing * rows * kGS);
-    uint64_t* full = bars;                  // [kStages]   producers -> MMA
-    uint64_t* empty = bars + kStages;       // [kStages]   MMA commit -> producers
-    uint64_t* dfull = bars + 2 * kStages;   // [2]         MMA commit -> epilogue
-    uint64_t* dempty = dfull + 2;           // [2]         epilogue -> MMA
-    uint64_t* fin = dempty + 2;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
+// Epilogue of NU output units (a compile-time count keeps the FP32 sums in registers): halfway through every
+// period read this warp's TMEM lane quarter of the previous period's accumulators with tcgen05.ld, release the D
+// buffer, add into the FP32 sums; every kSpill periods add those into the FP64 sums in shared memory (FP64 is slow
+// on this part, so only there); finally write this CTA's FP64 partials.
+template <int NU>
+__device__ __forceinline__ void epilogue(const GroupDesc& G, const Params& P, uint32_t tmem, double* acc64,
+                                         uint64_t* d_full, uint64_t* d_empty, volatile int* abort_flag, int nper,
+                                         int warp, int lane) {
+    const int q = warp & 3;
+    const int row = 32 * q + lane;
+    const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+    const int ntiles = G.ntiles;
+    uint32_t cols[NU][3];     // hi*hi, hi*lo and lo*hi of unit u
+#pragma unroll
+    for (int u = 0; u < NU; ++u) {
+        const int t = G.unit_tile[u], cu = G.unit_c[u];
+        cols[u][0] = (uint32_t)(G.dm_col[t] + cu);
+        cols[u][1] = (uint32_t)(G.dm_col[t] + G.tile_w[t] + cu);
+        cols[u][2] = (uint32_t)(G.dl_col[t] + cu);
+    }
+    const uint32_t d_cols = (uint32_t)G.d_cols;
+    int* const err = P.err;
+    double* const out = P.partial + ((size_t)blockIdx.x * P.total_units + G.unit_base) * 2048;
+
+    float acc[NU][16];
+#pragma unroll
+    for (int u = 0; u < NU; ++u)
+#pragma unroll
+        for (int j = 0; j < 16; ++j) acc[u][j] = 0.f;
+    bool ok = true;
+    for (int per = 0; per < nper && ok; ++per) {
+        const int db = per % kDBuf;
+        for (int t = 0; t < ntiles && ok; ++t)
+            ok = warp_wait(&d_full[db * kMaxTiles + t], (uint32_t)((per / kDBuf) & 1), abort_flag, err);
+        if (!ok) break;
+        tc_fence_after();
+        const uint32_t dbase = tmem + lane_base + (uint32_t)db * d_cols;
+#pragma unroll
+        for (int u = 0; u < NU; ++u)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                uint32_t v[16];
+                tmem_ld16(dbase + cols[u][k], v);
+                tmem_wait_ld16(v);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) acc[u][j] += __uint_as_float(v[j]);
+            }
+        tc_fence_before();
+        mbar_arrive(&d_empty[db]);
+        if ((per + 1) % kSpill == 0) {
+#pragma unroll
+            for (int u = 0; u < NU; ++u)
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    acc64[(u * 16 + j) * 128 + row] += (double)acc[u][j];
+                    acc[u][j] = 0.f;
+                }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < NU; ++u)
+#pragma unroll
+        for (int j = 0; j < 16; ++j) acc64[(u * 16 + j) * 128 + row] += (double)acc[u][j];
+    for (int i = 0; i < NU * 16; ++i) out[(size_t)i * 128 + row] = acc64[i * 128 + row];
+}
+
+
+// Producer warp of group gp = (warp - 1) / 4: cells 16 gp .. 16 gp + 15 of every 32-cell stage, for NT tiles (a
+// compile-time count: every tile's products live in their own registers, so the next tile's arithmetic does not
+// wait for the previous tile's TMEM store to read its registers).  A thread owns TMEM lane 32 (warp % 4) + lane,
+// i.e. row `row` of every tile.  The 64 columns of a tile's stage block are [hi 16 | lo 16] of half 0, then of half
+// 1; a thread writes its half with one 32-column TMEM store per tile.
+constexpr int kMaxItems = 2;   // B items per producer thread: 4 W items a tile per group, W summed <= 48 -> <= 192 / 128
+
+template <int NT>
+__device__ __forceinline__ void producer(const GroupDesc& G, const Params& P, uint32_t tmem, const unsigned char* ring,
+                                         unsigned char* bst, uint64_t* slot_full, uint64_t* slot_empty,
+                                         uint64_t* a_full, uint64_t* a_empty, volatile int* abort_flag, int nstages,
+                                         int warp, int lane) {
+    const int gp = (warp - 1) >> 2;
+    const int q = warp & 3;
+    const int row = 32 * q + lane;
+    const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+    const int nA = G.nA, a_col0 = G.a_col0, slot_bytes = P.slot_bytes, bstage_bytes = G.bstage_bytes;
+    int* const err = P.err;
+    int pj[NT], pk[NT];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+        const short2 jk = P.rows[(size_t)(G.tile0 + t) * 128 + row];
+        pj[t] = jk.x;
+        pk[t] = jk.y;
+    }
+    // B operand items of this thread, decoded once.  Tile t's B block holds rows n < W (hi of single s0 + n) and
+    // rows W + n (lo), 32 cells each: element (row, cell k) at (row / 8) * 1024 + (k / 4) * 128 + (row % 8) * 16 +
+    // (k % 4) * 4 bytes.  An item is one single and one 4-cell piece of this group's half: it loads 16 bytes from
+    // the ring and stores the hi and the lo piece.  bsrc = map row in the slot (-1: zero), boff = byte offset of the
+    // hi piece in the B stage (the lo piece is at boff + blo_d), bquad = 4-cell piece within the half.
+    const int ptid = 32 * ((warp - 1) & 3) + lane;       // 0 .. 127 within the group
+    int bsrc[kMaxItems], boff[kMaxItems], blo_d[kMaxItems], bquad[kMaxItems];
+    int nmine = 0;
+    {
+        int total = 0;
+#pragma unroll
+        for (int t = 0; t < NT; ++t) total += 4 * G.tile_w[t];
+#pragma unroll
+        for (int m = 0; m < kMaxItems; ++m) {
+            const int it = ptid + 128 * m;
+            bsrc[m] = -1;
+            boff[m] = blo_d[m] = bquad[m] = 0;
+            if (it < total) {
+                int t = 0, loc = it;
+                while (t + 1 < NT && loc >= 4 * G.tile_w[t]) { loc -= 4 * G.tile_w[t]; ++t; }
+                const int W = G.tile_w[t];
+                const int n = loc % W, quad = loc / W;
+                const int si = G.tile_s0[t] + n;
+                if (si < P.nh) bsrc[m] = P.hsep ? P.h_row0 + si : si;
+                const int col = (4 * gp + quad) * 128 + (n & 7) * 16;
+                boff[m] = G.tile_boff[t] + (n >> 3) * 1024 + col;
+                blo_d[m] = (((W + n) >> 3) - (n >> 3)) * 1024;
+                bquad[m] = quad;
+                nmine = m + 1;
+            }
+        }
+    }
+    for (int st = 0; st < nstages; ++st) {
+        const int s = st % kRingSlots;
+        const int as = st % nA;
+        bool ok = warp_wait(&slot_full[s], (uint32_t)((st / kRingSlots) & 1), abort_flag, err);
+        if (ok && st >= nA) ok = warp_wait(&a_empty[as], (uint32_t)((st / nA - 1) & 1), abort_flag, err);
+        if (!ok) break;
+        tc_fence_after();
+        const unsigned char* slot = ring + (size_t)s * slot_bytes;
+        float4 bx[kMaxItems];
+#pragma unroll
+        for (int m = 0; m < kMaxItems; ++m)
+            if (m < nmine && bsrc[m] >= 0) bx[m] = *ring_chunk(slot, bsrc[m], 4 * gp + bquad[m]);
+        uint32_t v[NT][32];
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+            if (pj[t] >= 0) {
+                float4 x[4], y[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    x[c] = *ring_chunk(slot, pj[t], 4 * gp + c);
+                    y[c] = *ring_chunk(slot, pk[t], 4 * gp + c);
+                }
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    uint64_t h0, l0, h1, l1;
+                    split_x2(mul_x2(f2pack(x[c].x, x[c].y), f2pack(y[c].x, y[c].y)), h0, l0);
+                    split_x2(mul_x2(f2pack(x[c].z, x[c].w), f2pack(y[c].z, y[c].w)), h1, l1);
+                    v[t][4 * c + 0] = (uint32_t)h0;
+                    v[t][4 * c + 1] = (uint32_t)(h0 >> 32);
+                    v[t][4 * c + 2] = (uint32_t)h1;
+                    v[t][4 * c + 3] = (uint32_t)(h1 >> 32);
+                    v[t][16 + 4 * c + 0] = (uint32_t)l0;
+                    v[t][16 + 4 * c + 1] = (uint32_t)(l0 >> 32);
+                    v[t][16 + 4 * c + 2] = (uint32_t)l1;
+                    v[t][16 + 4 * c + 3] = (uint32_t)(l1 >> 32);
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < 32; ++c) v[t][c] = 0u;
+            }
+            tmem_st32(tmem + lane_base + (uint32_t)(a_col0 + as * 64 * NT + 64 * t + 32 * gp), v[t]);
+        }
+        unsigned char* bs = bst + (size_t)as * bstage_bytes;
+#pragma unroll
+        for (int m = 0; m < kMaxItems; ++m) {
+            if (m >= nmine) break;
+            uint64_t h01 = 0, h23 = 0, l01 = 0, l23 = 0;
+            if (bsrc[m] >= 0) {
+                split_x2(f2pack(bx[m].x, bx[m].y), h01, l01);
+                split_x2(f2pack(bx[m].z, bx[m].w), h23, l23);
+            }
+            *reinterpret_cast<uint4*>(bs + boff[m]) =
+                make_uint4((uint32_t)h01, (uint32_t)(h01 >> 32), (uint32_t)h23, (uint32_t)(h23 >> 32));
+            *reinterpret_cast<uint4*>(bs + boff[m] + blo_d[m]) =
+                make_uint4((uint32_t)l01, (uint32_t)(l01 >> 32), (uint32_t)l23, (uint32_t)(l23 >> 32));
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_fence_before();
+        mbar_arrive(&a_full[as]);
+        mbar_arrive(&slot_empty[s]);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_contract_tc(const __grid_constant__ CUtensorMap tmap_g, const __grid_constant__ CUtensorMap tmap_h,
+                  const __grid_constant__ Params P) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    const GroupDesc& G = P.grp[blockIdx.y];
+    unsigned char* ring = smem;
+    unsigned char* bst = smem + P.off_b;
+    double* acc64 = reinterpret_cast<double*>(smem + P.off_acc);                 // [unit][16][128]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + P.off_bar);
+    uint64_t* slot_full = bars;                        // [kRingSlots]  TMA -> producers
+    uint64_t* slot_empty = bars + kRingSlots;          // [kRingSlots]  producers -> TMA
+    uint64_t* a_full = bars + 2 * kRingSlots;          // [kMaxAStages] producers -> issuers
+    uint64_t* a_empty = a_full + kMaxAStages;          // [kMaxAStages] MMA commit -> producers
+    uint64_t* d_full = a_empty + kMaxAStages;          // [2][kMaxTiles] MMA commit -> epilogue (D buffer, tile)
+    uint64_t* d_empty = d_full + 2 * kMaxTiles;        // [2]            epilogue -> issuers (D buffer)
+    uint64_t* fin = d_empty + 2;                       // [kIssWarps]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + kIssWarps);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
-    const int tid = threadIdx.x;
-    const int warp = tid >> 5, lane = tid & 31;
-    const long cbeg = (long)blockIdx.x * P.cells_cta;
-    const int rg = blockIdx.y;                                  // row group: pair tiles 2 rg, 2 rg + 1
-    const int ntl = min(kTiles, P.ntiles - kTiles * rg);        // tiles of this CTA
-    const long cend = min(P.ncell, cbeg + P.cells_cta);
-    const int nchunks = cbeg < cend ? (int)((cend - cbeg + kKC - 1) / kKC) : 0;
-    const int nperiods = (nchunks + kPeriod - 1) / kPeriod;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long c0 = (long)blockIdx.x * P.cells_cta;
+    const long c1 = min(P.ncell, c0 + P.cells_cta);
+    const int nslots = c0 < c1 ? (int)((c1 - c0 + kSlotCells - 1) / kSlotCells) : 0;
+    const int nstages = nslots;                 // one A stage per ring slot
+    // plan fields used in the loops, in registers
+    const int nA = G.nA, ntiles = G.ntiles, a_col0 = G.a_col0, bstage_bytes = G.bstage_bytes;
+    const int slot_bytes = P.slot_bytes;
+    int* const err = P.err;
 
-    for (int i = tid; i < kTiles * kNCols * 128; i += blockDim.x) acc64[i] = 0.0;
+    for (int i = tid; i < G.nunits * 16 * 128; i += kThreads) acc64[i] = 0.0;
     if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) { mbar_init(&full[s], kProducers); mbar_init(&empty[s], kIssuers); }
-        for (int d = 0; d < 2; ++d) { mbar_init(&dfull[d], kIssuers); mbar_init(&dempty[d], kEpilogue); }
-        mbar_init(fin, kIssuers);
+        for (int s = 0; s < kRingSlots; ++s) {
+            mbar_init(&slot_full[s], 1);
+            mbar_init(&slot_empty[s], 32 * kProdWarps);
+        }
+        for (int s = 0; s < kMaxAStages; ++s) {
+            mbar_init(&a_full[s], 32 * kProdWarps);   // both producer groups make a stage
+            mbar_init(&a_empty[s], ntiles);        // one commit per issuing thread (tile)
+        }
+        for (int i = 0; i < 2 * kMaxTiles; ++i) mbar_init(&d_full[i], 1);
+        for (int i = 0; i < 2; ++i) mbar_init(&d_empty[i], 32 * kEpiWarps);
+        for (int i = 0; i < kIssWarps; ++i) mbar_init(&fin[i], 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == kMmaWarp) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_u32(tmem_slot)));
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = *tmem_slot;        // D buffer d, tile t at column 64 d + 32 t
-    const uint32_t A0 = tmem + 128;          // A stage s, tile t: hi at 128 + 64 s + 32 t, lo at +16
+    const uint32_t tmem = *tmem_slot;
 
-    if (warp < kProducerWarps) {
+    if (warp == 0) {
+        // ------------------------------------------------------------------ TMA producer
+        if (lane == 0 && nslots > 0) {
+            const uint32_t bytes = (uint32_t)(P.ng * 128 + (P.hsep ? P.nh * 128 : 0));
+            const bool hsep = P.hsep != 0;
+            const int hoff = P.h_row0 * 128;
+            int issued = 0;
+            for (int sl = 0; sl < nslots; ++sl) {
+                const int s = sl % kRingSlots;
+                if (sl >= kRingSlots &&
+                    !thread_wait(&slot_empty[s], (uint32_t)((sl / kRingSlots - 1) & 1), abort_flag, err))
+                    break;
+                unsigned char* dst = ring + (size_t)s * slot_bytes;
+                const int x = (int)(c0 + (long)sl * kSlotCells);
+                mbar_expect_tx(&slot_full[s], bytes);
+                tma_load_2d(dst, &tmap_g, x, 0, &slot_full[s]);
+                if (hsep) tma_load_2d(dst + hoff, &tmap_h, x, 0, &slot_full[s]);
+                ++issued;
+            }
+            // every load issued has landed before the CTA may exit
+            for (int sl = max(0, issued - kRingSlots); sl < issued; ++sl)
+                drain_wait(&slot_full[sl % kRingSlots], (uint32_t)((sl / kRingSlots) & 1), err);
+        }
+        __syncwarp();
+    } else if (warp <= kProdWarps) {
         // ------------------------------------------------------------------ producers
-        const bool hsep = P.h != P.g;
-        const int quarter = warp & 3;
-        const int row = 32 * quarter + lane;
-        const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
-        int pj[kTiles], pk[kTiles];
-#pragma unroll
-        for (int u = 0; u < kTiles; ++u) {
-            const int p = 128 * (kTiles * rg + u) + row;
-            if (u < ntl && p < P.npairs) { short2 jk = P.pairs[p]; pj[u] = jk.x; pk[u] = jk.y; }
-            else { pj[u] = -1; pk[u] = -1; }
+        switch (ntiles) {
+            case 1: producer<1>(G, P, tmem, ring, bst, slot_full, slot_empty, a_full, a_empty, abort_flag, nstages, warp, lane); break;
+            case 2: producer<2>(G, P, tmem, ring, bst, slot_full, slot_empty, a_full, a_empty, abort_flag, nstages, warp, lane); break;
+            default: producer<3>(G, P, tmem, ring, bst, slot_full, slot_empty, a_full, a_empty, abort_flag, nstages, warp, lane); break;
         }
-        auto issue = [&](int c) {
-            if (c < nchunks) {
-                float* slot = ring + (size_t)(c % kRing) * rows * kGS;
-                const long x0 = cbeg + (long)c * kKC;
-                for (int q = tid; q < rows * 4; q += kProducers) {
-                    const int r = q >> 2, quad = q & 3;
-                    const float* src = (r < P.ng) ? P.g + (long)r * P.ncell : P.h + (long)(r - P.ng) * P.ncell;
-                    const long cell = x0 + quad * 4;
-                    const long valid = min(4L, max(0L, cend - cell));
-                    cp_async16(slot + r * kGS + quad * 4, valid > 0 ? src + cell : src, (int)(valid * 4));
-                }
-            }
-            asm volatile("cp.async.commit_group;" ::: "memory");
-        };
-        issue(0);
-        issue(1);
-        issue(2);
-        bool ok = true;
-        for (int c = 0; c < nchunks; ++c) {
-            const int s = c % kStages;
-            asm volatile("cp.async.wait_group 2;" ::: "memory");
-            bool mine = true;
-            if (c >= kStages) mine = mbar_wait(&empty[s], (uint32_t)((c / kStages - 1) & 1), abort_flag, P.err, 0);
-            // uniform decision + barrier: chunk c's tile is visible to all producers and chunk c-1 is finished
-            ok = producers_all(mine);
-            if (!ok) break;
-            if (c >= kStages) tc_fence_after();
-            issue(c + 3);
-            const float* tile = ring + (size_t)(c % kRing) * rows * kGS;
-            // A operand: pair products split into TF32 hi and FP32 remainder (read as TF32 by the MMA), into TMEM
-#pragma unroll
-            for (int u = 0; u < kTiles; ++u) {
-                const int t = u;
-                if (t >= ntl) break;
-                uint32_t hi[kKC], lo[kKC];
-                if (pj[u] >= 0) {
-                    const float4* a = reinterpret_cast<const float4*>(tile + pj[u] * kGS);
-                    const float4* b = reinterpret_cast<const float4*>(tile + pk[u] * kGS);
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const float4 x = a[q], y = b[q];
-                        split2(x.x * y.x, hi[4 * q + 0], lo[4 * q + 0]);
-                        split2(x.y * y.y, hi[4 * q + 1], lo[4 * q + 1]);
-                        split2(x.z * y.z, hi[4 * q + 2], lo[4 * q + 2]);
-                        split2(x.w * y.w, hi[4 * q + 3], lo[4 * q + 3]);
-                    }
-                } else {
-#pragma unroll
-                    for (int q = 0; q < kKC; ++q) { hi[q] = 0u; lo[q] = 0u; }
-                }
-                const uint32_t col = 128u + 64u * s + 32u * t;
-                tmem_st16(tmem + lane_base + col, hi);
-                tmem_st16(tmem + lane_base + col + 16u, lo);
-            }
-            // B operand (threads 0..127): singles hi/lo in the no-swizzle K-major layout:
-            // element (row r, cell k) at (r / 8) * 512 + (k / 4) * 128 + (r % 8) * 16 + (k % 4) * 4 bytes.
-            if (tid < 128) {
-                unsigned char* bs = bbase + s * BSTAGE;
-                const int r = tid >> 2, quad = tid & 3;
-                uint4 vh = make_uint4(0, 0, 0, 0), vl = make_uint4(0, 0, 0, 0);
-                if (r < P.nh) {
-                    const int rr = hsep ? P.ng + r : r;
-                    const float4 v = *reinterpret_cast<const float4*>(tile + rr * kGS + quad * 4);
-                    split2(v.x, vh.x, vl.x);
-                    split2(v.y, vh.y, vl.y);
-                    split2(v.z, vh.z, vl.z);
-                    split2(v.w, vh.w, vl.w);
-                }
-                const int off = (r >> 3) * 512 + quad * 128 + (r & 7) * 16;
-                *reinterpret_cast<uint4*>(bs + off) = vh;
-                *reinterpret_cast<uint4*>(bs + 2048 + off) = vl;
-            }
-            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            tc_fence_before();
-            mbar_arrive(&full[s]);
-        }
-        asm volatile("cp.async.wait_all;" ::: "memory");
-        if (!ok) *abort_flag = 1;
-    } else {
-        // ------------------------------------------------------------------ epilogue (+ MMA issue in warp 8)
-        const int quarter = warp & 3;              // TMEM lane quarter this warp may access
-        const int row = 32 * quarter + lane;
-        const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
-        const int iidx = warp - kMmaWarp;
-        const bool issuer = iidx < kIssuers;
-        float acc[kTiles][kNCols];
-#pragma unroll
-        for (int u = 0; u < kTiles; ++u)
-#pragma unroll
-            for (int i = 0; i < kNCols; ++i) acc[u][i] = 0.f;
-        auto spill = [&]() {
-#pragma unroll
-            for (int u = 0; u < kTiles; ++u) {
-                const int t = u;
-                if (t >= ntl) break;
-#pragma unroll
-                for (int i = 0; i < kNCols; ++i) {
-                    acc64[(t * kNCols + i) * 128 + row] += (double)acc[u][i];
-                    acc[u][i] = 0.f;
-                }
-            }
-        };
-        // read the accumulators of period q, release the D buffer, add into the FP32 register sums
-        auto drain = [&](int q) -> bool {
-            const int d = q & 1;
-            if (!mbar_wait(&dfull[d], (uint32_t)((q >> 1) & 1), abort_flag, P.err, issuer ? 0 : 1)) return false;
-            tc_fence_after();
-#pragma unroll
-            for (int u = 0; u < kTiles; ++u) {
-                const int t = u;
-                if (t >= ntl) break;
-                uint32_t v[kNCols];
-                tmem_ld32(tmem + lane_base + 64u * d + 32u * t, v);
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-                for (int i = 0; i < kNCols; ++i) acc[u][i] += __uint_as_float(v[i]);
-            }
-            tc_fence_before();
-            mbar_arrive(&dempty[d]);
-            if ((q + 1) % kSpill == 0) spill();
-            return true;
-        };
-        // issue the MMAs of period q (lane 0 of the issuer warp)
-        bool mma_ok = true;
-        auto issue_period = [&](int q) {
-            const uint32_t idesc = idesc_tf32(128, kNCols);
-            const uint32_t bstage0 = smem_u32(bbase);
-            const int d = q & 1;
-            if (q >= 2 && !mbar_wait(&dempty[d], (uint32_t)((q / 2 - 1) & 1), abort_flag, P.err, 0)) { mma_ok = false; return; }
-            const int c1 = min(nchunks, (q + 1) * kPeriod);
-            for (int c = q * kPeriod; c < c1; ++c) {
-                const int s = c % kStages;
-                const bool first = c == q * kPeriod;
-                if (!mbar_wait(&full[s], (uint32_t)((c / kStages) & 1), abort_flag, P.err, 0)) { mma_ok = false; return; }
-                tc_fence_after();
-                const uint32_t bh = bstage0 + s * BSTAGE, bl = bh + 2048;
-                for (int t = iidx; t < ntl; t += kIssuers) {
-                    const uint32_t dcol = tmem + 64u * d + 32u * t;
-                    const uint32_t ah = A0 + 64u * s + 32u * t, al = ah + 16u;
+    } else if (warp <= kProdWarps + kIssWarps) {
+        // ------------------------------------------------------------------ MMA issue
+        // The whole warp runs the loop (converged; every lane polls the barriers), lane 0 issues and commits.
+        const int t = warp - 1 - kProdWarps;
+        if (t < ntiles) {
+            const int W = G.tile_w[t];
+            const uint32_t idesc_m = idesc_tf32(128, 2 * W), idesc_l = idesc_tf32(128, W);
+            const uint32_t dm = (uint32_t)G.dm_col[t], dl = (uint32_t)G.dl_col[t];
+            const uint32_t d_cols = (uint32_t)G.d_cols;
+            const uint32_t aoff = (uint32_t)(64 * t);
+            const uint32_t b0 = smem_u32(bst + G.tile_boff[t]);
+            for (int st = 0; st < nstages; ++st) {
+                const int as = st % nA;
+                const int per = st / kPeriod, db = per % kDBuf;
+                const bool pstart = (st % kPeriod) == 0;
+                if (pstart && per >= kDBuf &&
+                    !warp_wait(&d_empty[db], (uint32_t)((per / kDBuf - 1) & 1), abort_flag, err))
+                    break;
+                if (!warp_wait(&a_full[as], (uint32_t)((st / nA) & 1), abort_flag, err)) break;
+                if (lane == 0) {
+                    tc_fence_after();
+                    const uint32_t bb = b0 + (uint32_t)(as * bstage_bytes);
+                    const uint32_t aa = tmem + (uint32_t)(a_col0 + as * 64 * ntiles) + aoff;
+                    const uint32_t dbuf = tmem + (uint32_t)db * d_cols;
 #pragma unroll
                     for (int ks = 0; ks < kKC / 8; ++ks) {
-                        const uint64_t dbh = sdesc(bh + ks * 256, 128, 512);
-                        const uint64_t dbl = sdesc(bl + ks * 256, 128, 512);
-                        mma_tf32(dcol, ah + 8u * ks, dbh, idesc, (first && ks == 0) ? 0u : 1u);
-                        mma_tf32(dcol, ah + 8u * ks, dbl, idesc, 1u);
-                        mma_tf32(dcol, al + 8u * ks, dbh, idesc, 1u);
+                        // K step ks: cells 8 ks .. 8 ks + 7; A_hi at half (ks / 2), column 8 (ks % 2); A_lo at +16
+                        const uint64_t bd = sdesc(bb + 256u * ks, 128, 1024);
+                        const uint32_t ah = aa + 32u * (ks >> 1) + 8u * (ks & 1);
+                        const uint32_t acc = (pstart && ks == 0) ? 0u : 1u;
+                        mma_tf32(dbuf + dm, ah, bd, idesc_m, acc);          // A_hi . [B_hi | B_lo]
+                        mma_tf32(dbuf + dl, ah + 16u, bd, idesc_l, acc);    // A_lo . B_hi (independent chain)
                     }
+                    mma_commit(&a_empty[as]);
+                    if ((st % kPeriod) == kPeriod - 1 || st == nstages - 1) mma_commit(&d_full[db * kMaxTiles + t]);
                 }
-                mma_commit(&empty[s]);
-            }
-            mma_commit(&dfull[d]);
-        };
-        bool ok = true;
-        if (issuer) {
-            for (int q = 0; q < nperiods; ++q) {
-                if (lane == 0 && mma_ok) issue_period(q);
                 __syncwarp();
-                if (q >= 1 && ok) ok = drain(q - 1);
             }
-            if (nperiods >= 1 && ok) ok = drain(nperiods - 1);
             if (lane == 0) {
                 // every MMA issued by this thread has completed before TMEM is released
-                mma_commit(fin);
-                for (unsigned it = 0; it < kSpinLimit && !mbar_try(fin, 0); ++it) {
-                }
-                if (!mma_ok) *abort_flag = 1;
+                mma_commit(&fin[t]);
+                drain_wait(&fin[t], 0, err);
             }
             __syncwarp();
-        } else {
-            for (int q = 0; q < nperiods && ok; ++q) ok = drain(q);
         }
-        spill();
-        for (int u = 0; u < kTiles; ++u) {
-            const int t = u;
-            if (t >= ntl) break;
-            const int p = 128 * (kTiles * rg + t) + row;
-            if (p >= P.npairs) continue;
-            double* out = P.partial + ((size_t)blockIdx.x * P.npairs + p) * P.nh;
-            for (int i = 0; i < P.nh; ++i) out[i] = acc64[(t * kNCols + i) * 128 + row];
+    } else {
+        // ------------------------------------------------------------------ epilogue
+        const int nper = (nstages + kPeriod - 1) / kPeriod;
+        switch (G.nunits) {
+            case 1: epilogue<1>(G, P, tmem, acc64, d_full, d_empty, abort_flag, nper, warp, lane); break;
+            case 2: epilogue<2>(G, P, tmem, acc64, d_full, d_empty, abort_flag, nper, warp, lane); break;
+            default: epilogue<3>(G, P, tmem, acc64, d_full, d_empty, abort_flag, nper, warp, lane); break;
         }
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == kMmaWarp) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+}
+
+// out[o] = sum over CTAs of partial[cta][gidx[o]], in CTA order (deterministic).
+__global__ void k_reduce_gather(const double* __restrict__ partial, int ncta, long stride,
+                                const int* __restrict__ gidx, int n_out, double* __restrict__ out) {
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= n_out) return;
+    const long g = gidx[o];
+    double s = 0.0;
+    for (int c = 0; c < ncta; ++c) s += partial[(long)c * stride + g];
+    out[o] = s;
 }
 
 // Self-test of the bounded waits: one thread waits on an mbarrier phase that nothing completes; the wait gives up
@@ -441,9 +616,335 @@ __global__ void k_wait_selftest(int* err, unsigned limit) {
     }
 }
 
+// ------------------------------------------------------------------------------------------------ host planner
+
+// A pair row with the range of singles it needs and where each of its outputs goes.
+struct NeedPair {
+    int j, k;
+    int lo, hi;                                   // singles needed: [lo, hi]
+    std::vector<std::pair<int, int>> outs;        // (single, output index)
+};
+
+struct Plan {
+    int ng = 0, nh = 0, hsep = 0, n_out = 0, ncta = 0, ngroups = 0, total_units = 0;
+    long cells_cta = 0;
+    Params base{};
+    size_t smem = 0;
+    short2* d_rows = nullptr;
+    int* d_gidx = nullptr;
+    double* d_partial = nullptr;
+    ~Plan() {
+        if (d_rows) cudaFree(d_rows);
+        if (d_gidx) cudaFree(d_gidx);
+        if (d_partial) cudaFree(d_partial);
+    }
+};
+
+static int round_w(int w) { return w <= 16 ? 16 : 32; }
+
+// Tiles of <= 128 pairs, consecutive in the order of (hi, lo), cut by dynamic programming to minimise the summed
+// window width (the tensor work) plus a per-tile cost.
+static std::vector<std::pair<int, int>> cut_tiles(const std::vector<NeedPair>& P) {
+    const int n = (int)P.size();
+    std::vector<long> f(n + 1, (long)1 << 40);
+    std::vector<int> arg(n + 1, 0);
+    f[0] = 0;
+    for (int i = 1; i <= n; ++i) {
+        int lo = 1 << 30, hi = -1;
+        for (int j = i - 1; j >= 0 && j >= i - 128; --j) {
+            lo = std::min(lo, P[j].lo);
+            hi = std::max(hi, P[j].hi);
+            const int s0 = lo / 8 * 8;
+            if (hi + 1 - s0 > 32) break;
+            const long c = f[j] + round_w(hi + 1 - s0) + 8;
+            if (c < f[i]) { f[i] = c; arg[i] = j; }
+        }
+    }
+    std::vector<std::pair<int, int>> seg;
+    for (int i = n; i > 0; i = arg[i]) seg.push_back({arg[i], i});
+    std::reverse(seg.begin(), seg.end());
+    return seg;
+}
+
+// Pure host layout of a plan (no CUDA calls): tiles, row groups, TMEM / shared-memory layout, the row table and the
+// gather index of every output.  Returns nullptr or an error message.
+static const char* layout_plan(Plan& pl, long ncell, int nsm, int ng, int nh, int hsep, std::vector<NeedPair> need,
+                               int n_out, std::vector<short2>& rows, std::vector<int>& gidx) {
+    pl.ng = ng; pl.nh = nh; pl.hsep = hsep; pl.n_out = n_out;
+    std::stable_sort(need.begin(), need.end(), [](const NeedPair& a, const NeedPair& b) {
+        return std::tie(a.hi, a.lo) < std::tie(b.hi, b.lo);
+    });
+    for (const NeedPair& p : need)
+        if (p.hi + 1 - p.lo / 8 * 8 > 32) return "contract_tc: a pair needs a window of more than 32 singles";
+    auto seg = need.empty() ? std::vector<std::pair<int, int>>{} : cut_tiles(need);
+    struct TileH { int first, last, s0, W; };
+    std::vector<TileH> tiles;
+    for (auto& sg : seg) {
+        int lo = 1 << 30, hi = -1;
+        for (int i = sg.first; i < sg.second; ++i) { lo = std::min(lo, need[i].lo); hi = std::max(hi, need[i].hi); }
+        const int s0 = lo / 8 * 8;
+        // within a tile, order rows by (j, k): lanes of a warp then share j and read consecutive k (no bank conflicts)
+        std::stable_sort(need.begin() + sg.first, need.begin() + sg.second,
+                         [](const NeedPair& a, const NeedPair& b) { return std::tie(a.j, a.k) < std::tie(b.j, b.k); });
+        tiles.push_back({sg.first, sg.second, s0, round_w(hi + 1 - s0)});
+    }
+    if (tiles.empty()) tiles.push_back({0, 0, 0, 16});
+    // row groups: consecutive tiles while TMEM (two accumulator buffers + two A stages) and the 3 output units allow
+    std::vector<std::pair<int, int>> groups;
+    for (int t = 0; t < (int)tiles.size();) {
+        int e = t, dcols = 0, units = 0;
+        while (e < (int)tiles.size() && e - t < kMaxTiles) {
+            const int nd = dcols + 3 * tiles[e].W, nu = units + tiles[e].W / 16, nt = e - t + 1;
+            if (nu > kMaxUnits || kDBuf * ((nd + 31) / 32 * 32) + 2 * 2 * kKC * nt > 512) break;
+            dcols = nd; units = nu; ++e;
+        }
+        if (e == t) return "contract_tc: tile does not fit tensor memory";
+        groups.push_back({t, e});
+        t = e;
+    }
+    if ((int)groups.size() > kMaxGroups) return "contract_tc: more than 4 row groups";
+    pl.ngroups = (int)groups.size();
+
+    Params& P = pl.base;
+    P = Params{};
+    P.ng = ng; P.nh = nh; P.hsep = hsep;
+    const int grows = (ng + 7) / 8 * 8;
+    P.h_row0 = grows;
+    P.slot_bytes = (grows + (hsep ? (nh + 7) / 8 * 8 : 0)) * 128;
+    int max_b = 0, max_units = 0;
+    rows.assign(tiles.size() * 128, make_short2(-1, -1));
+    gidx.assign(std::max(n_out, 1), 0);
+    int unit_base = 0;
+    for (int gi = 0; gi < pl.ngroups; ++gi) {
+        GroupDesc& D = P.grp[gi];
+        D = GroupDesc{};
+        const int t0 = groups[gi].first, nt = groups[gi].second - t0;
+        D.tile0 = t0; D.ntiles = nt; D.unit_base = unit_base;
+        // accumulators: hi*[hi | lo] (2W) and lo*hi (W) of every tile, largest first, so each is aligned to its size
+        std::vector<std::tuple<int, int, int>> dl;   // (size, tile, which)
+        for (int t = 0; t < nt; ++t) { dl.push_back({2 * tiles[t0 + t].W, t, 0}); dl.push_back({tiles[t0 + t].W, t, 1}); }
+        std::stable_sort(dl.begin(), dl.end(), [](auto& a, auto& b) { return std::get<0>(a) > std::get<0>(b); });
+        int col = 0;
+        for (auto& x : dl) {
+            if (std::get<2>(x) == 0) D.dm_col[std::get<1>(x)] = col; else D.dl_col[std::get<1>(x)] = col;
+            col += std::get<0>(x);
+        }
+        D.d_cols = (col + 31) / 32 * 32;
+        D.a_col0 = kDBuf * D.d_cols;
+        D.nA = std::min(kMaxAStages, (512 - D.a_col0) / (2 * kKC * nt));
+        // B blocks: one per tile (its window's hi and lo rows x the 32 cells of a stage)
+        int boff = 0;
+        for (int t = 0; t < nt; ++t) {
+            const TileH& T = tiles[t0 + t];
+            D.tile_w[t] = T.W;
+            D.tile_s0[t] = T.s0;
+            D.tile_boff[t] = boff;
+            boff += 2 * T.W * 4 * kKC;
+        }
+        D.bstage_bytes = (boff + 1023) / 1024 * 1024;
+        max_b = std::max(max_b, D.nA * D.bstage_bytes);
+        // output units
+        int u = 0;
+        for (int t = 0; t < nt; ++t)
+            for (int c = 0; c < tiles[t0 + t].W; c += 16) { D.unit_tile[u] = t; D.unit_c[u] = c; ++u; }
+        D.nunits = u;
+        for (int x = u; x < kMaxUnits; ++x) { D.unit_tile[x] = kMaxTiles; D.unit_c[x] = 0; }
+        max_units = std::max(max_units, u);
+        // rows and the gather index of every output
+        for (int t = 0; t < nt; ++t) {
+            const TileH& T = tiles[t0 + t];
+            int uf = 0;
+            while (D.unit_tile[uf] != t) ++uf;
+            for (int i = T.first; i < T.last; ++i) {
+                const int r = i - T.first;
+                rows[(size_t)(t0 + t) * 128 + r] = make_short2((short)need[i].j, (short)need[i].k);
+                for (auto& so : need[i].outs) {
+                    const int cc = so.first - T.s0;
+                    const int gu = unit_base + uf + cc / 16;
+                    gidx[so.second] = (gu * 16 + cc % 16) * 128 + r;
+                }
+            }
+        }
+        unit_base += u;
+    }
+    pl.total_units = unit_base;
+    P.total_units = unit_base;
+    P.off_b = kRingSlots * P.slot_bytes;
+    P.off_acc = P.off_b + max_b;
+    P.off_bar = P.off_acc + kMaxUnits * 16 * 128 * 8;
+    // + 1024: the kernel aligns the start of its dynamic shared memory to 1024 bytes (128-byte swizzle atoms)
+    pl.smem = std::max((size_t)kMinSmem, (size_t)P.off_bar + 64 * 8 + 64) + 1024;
+    if (pl.smem > 227 * 1024) return "contract_tc: shared memory plan exceeds 227 KB";
+
+    const long nsl = (ncell + kSlotCells - 1) / kSlotCells;
+    pl.ncta = (int)std::max(1L, std::min((long)nsm, nsl));
+    pl.cells_cta = (nsl + pl.ncta - 1) / pl.ncta * kSlotCells;
+    pl.ncta = (int)((ncell + pl.cells_cta - 1) / pl.cells_cta);
+    P.ncell = ncell;
+    P.cells_cta = pl.cells_cta;
+    return nullptr;
+}
+
+static int build_plan(polybin_ctx* ctx, Plan& pl, int ng, int nh, int hsep, std::vector<NeedPair> need, int n_out) {
+    int dev = 0, nsm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return fail_cuda(ctx, e, "cudaDeviceGetAttribute", __FILE__, __LINE__);
+    std::vector<short2> rows;
+    std::vector<int> gidx;
+    const char* msg = layout_plan(pl, ctx->ncell, nsm, ng, nh, hsep, std::move(need), n_out, rows, gidx);
+    if (msg) return fail(ctx, POLYBIN_EINVAL, "%s", msg);
+    PB_CUDA_OK(cudaMalloc(&pl.d_rows, sizeof(short2) * rows.size()));
+    PB_CUDA_OK(cudaMemcpy(pl.d_rows, rows.data(), sizeof(short2) * rows.size(), cudaMemcpyHostToDevice));
+    PB_CUDA_OK(cudaMalloc(&pl.d_gidx, sizeof(int) * gidx.size()));
+    PB_CUDA_OK(cudaMemcpy(pl.d_gidx, gidx.data(), sizeof(int) * gidx.size(), cudaMemcpyHostToDevice));
+    PB_CUDA_OK(cudaMalloc(&pl.d_partial, sizeof(double) * (size_t)pl.ncta * pl.total_units * 2048));
+    pl.base.rows = pl.d_rows;
+    pl.base.partial = pl.d_partial;
+    return POLYBIN_OK;
+}
+
+struct PlanCache {
+    std::map<std::tuple<int, int, int, int>, Plan*> plans;   // (ng, nh, hsep, kind)
+    ~PlanCache() {
+        for (auto& kv : plans) delete kv.second;
+    }
+};
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, []() {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+// 2D map over `rows` maps of ncell floats (map-major): box = 32 cells x all maps, 128-byte swizzle.
+static int make_map(polybin_ctx* ctx, CUtensorMap* m, const float* base, int rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return fail(ctx, POLYBIN_ECUDA, "contract_tc: cuTensorMapEncodeTiled is not available");
+    if (reinterpret_cast<uintptr_t>(base) % 16) return fail(ctx, POLYBIN_EINVAL, "contract_tc: maps must be 16-byte aligned");
+    const cuuint64_t dims[2] = {(cuuint64_t)ctx->ncell, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ctx->ncell * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)kSlotCells, (cuuint32_t)rows};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(ctx, POLYBIN_ECUDA, "contract_tc: cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return POLYBIN_OK;
+}
+
+static int launch(polybin_ctx* ctx, Plan& pl, const float* g, const float* h, double* d_out) {
+    CUtensorMap mg, mh;
+    int rc = make_map(ctx, &mg, g, pl.ng);
+    if (rc) return rc;
+    if (pl.hsep) {
+        if ((rc = make_map(ctx, &mh, h, pl.nh))) return rc;
+    } else {
+        mh = mg;
+    }
+    if ((rc = ensure_err_flag(ctx))) return rc;
+    cudaError_t e = cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream);
+    if (e != cudaSuccess) return fail_cuda(ctx, e, "cudaMemsetAsync", __FILE__, __LINE__);
+    e = cudaFuncSetAttribute((const void*)k_contract_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
+    if (e != cudaSuccess) return fail_cuda(ctx, e, "cudaFuncSetAttribute(k_contract_tc)", __FILE__, __LINE__);
+    Params P = pl.base;
+    P.err = ctx->d_err;
+    {
+        StageTimer timer(ctx, kStageContract);
+        k_contract_tc<<<dim3(pl.ncta, pl.ngroups, 1), kThreads, pl.smem, ctx->stream>>>(mg, mh, P);
+        ctx->launches += 1;
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return fail_cuda(ctx, e, "k_contract_tc", __FILE__, __LINE__);
+        k_reduce_gather<<<(pl.n_out + 255) / 256, 256, 0, ctx->stream>>>(pl.d_partial, pl.ncta,
+                                                                          (long)pl.total_units * 2048, pl.d_gidx,
+                                                                          pl.n_out, d_out);
+        ctx->launches += 1;
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return fail_cuda(ctx, e, "k_reduce_gather", __FILE__, __LINE__);
+    }
+    if (ctx->capturing) return POLYBIN_OK;   // the caller reads the error flag after the graph has run
+    int herr = 0;
+    e = cudaMemcpyAsync(&herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return fail_cuda(ctx, e, "contract_tc error flag", __FILE__, __LINE__);
+    if (herr) return fail(ctx, POLYBIN_ETIMEOUT, "contract_tc: a pipeline wait timed out");
+    return POLYBIN_OK;
+}
+
+static PlanCache* cache_of(polybin_ctx* ctx) {
+    if (!ctx->tc) ctx->tc = new PlanCache();
+    return static_cast<PlanCache*>(ctx->tc);
+}
+
+// Plan of all pairs (j <= k) of ng maps against the nh singles [0, nh), output M[(j, k)][i] pair-major.
+static int full_plan(polybin_ctx* ctx, int ng, int nh, int hsep, Plan** out) {
+    PlanCache* pc = cache_of(ctx);
+    auto key = std::make_tuple(ng, nh, hsep, 0);
+    auto it = pc->plans.find(key);
+    if (it != pc->plans.end()) { *out = it->second; return POLYBIN_OK; }
+    std::vector<NeedPair> need;
+    int p = 0;
+    for (int j = 0; j < ng; ++j)
+        for (int k = j; k < ng; ++k, ++p) {
+            NeedPair np{j, k, 0, nh - 1, {}};
+            for (int i = 0; i < nh; ++i) np.outs.push_back({i, p * nh + i});
+            need.push_back(std::move(np));
+        }
+    Plan* pl = new Plan();
+    int rc = build_plan(ctx, *pl, ng, nh, hsep, std::move(need), p * nh);
+    if (rc) { delete pl; return rc; }
+    pc->plans[key] = pl;
+    *out = pl;
+    return POLYBIN_OK;
+}
+
+// Plan of the closed triplets of the context: triplet a <= b <= c from pair (b, c) and single a, output S in
+// triplet order.
+static int triplet_plan(polybin_ctx* ctx, Plan** out) {
+    PlanCache* pc = cache_of(ctx);
+    const int nb = ctx->nb;
+    auto key = std::make_tuple(nb, nb, 0, 1);
+    auto it = pc->plans.find(key);
+    if (it != pc->plans.end()) { *out = it->second; return POLYBIN_OK; }
+    std::map<std::pair<int, int>, NeedPair> m;
+    const int nt = (int)ctx->Nabc.size();
+    for (int t = 0; t < nt; ++t) {
+        const int a = ctx->trip[3 * t], b = ctx->trip[3 * t + 1], c = ctx->trip[3 * t + 2];
+        auto f = m.find({b, c});
+        if (f == m.end()) f = m.emplace(std::make_pair(b, c), NeedPair{b, c, a, a, {}}).first;
+        f->second.lo = std::min(f->second.lo, a);
+        f->second.hi = std::max(f->second.hi, a);
+        f->second.outs.push_back({a, t});
+    }
+    std::vector<NeedPair> need;
+    for (auto& kv : m) need.push_back(std::move(kv.second));
+    Plan* pl = new Plan();
+    int rc = build_plan(ctx, *pl, nb, nb, 0, std::move(need), nt);
+    if (rc) { delete pl; return rc; }
+    pc->plans[key] = pl;
+    *out = pl;
+    return POLYBIN_OK;
+}
+
 }  // namespace tc
 
 bool split_tc_available() { return true; }
+
+void destroy_tc(polybin_ctx* ctx) {
+    delete static_cast<tc::PlanCache*>(ctx->tc);
+    ctx->tc = nullptr;
+}
 
 int ensure_err_flag(polybin_ctx* ctx) {
     if (ctx->d_err) return POLYBIN_OK;
@@ -454,65 +955,36 @@ int ensure_err_flag(polybin_ctx* ctx) {
     return POLYBIN_OK;
 }
 
-static size_t tc_smem_bytes(int rows) {
-    return (size_t)tc::kTiles * tc::kNCols * 128 * sizeof(double) + tc::kStages * 2 * tc::kNCols * tc::kKC * 4 +
-           (size_t)tc::kRing * rows * tc::kGS * sizeof(float) + 256;
+// Shapes the tensor-core kernel takes: <= 512 pairs, <= 32 singles, cells a multiple of 4, 16-byte aligned maps.
+bool tc_shape_ok(polybin_ctx* ctx, const float* g, int ng, const float* h, int nh) {
+    if (ng < 1 || ng * (ng + 1) / 2 > 512 || nh < 1 || nh > 32) return false;
+    if (ctx->ncell % 4 || ctx->ncell > 0x7fffffffL) return false;
+    if (reinterpret_cast<uintptr_t>(g) % 16 || (h && reinterpret_cast<uintptr_t>(h) % 16)) return false;
+    return true;
 }
 
-// Geometry of the tensor-core contraction: one CTA per SM over a contiguous cell range.
-ContractGeom contract_geom_tc(int ng, int nh, long ncell) {
-    ContractGeom G;
-    G.nb = ng; G.nh = nh; G.npairs = ng * (ng + 1) / 2;
-    G.rt = G.ct = 0; G.rows_cta = 128; G.nhp = tc::kNCols;
-    G.ngroups = (G.npairs + 127) / 128;                 // pair tiles; a CTA takes kTiles of them
-    const int nrg = (G.ngroups + tc::kTiles - 1) / tc::kTiles;
-    const long nchunk = (ncell + tc::kKC - 1) / tc::kKC;
-    const long ncta = std::max(1L, std::min(304L / nrg, nchunk));   // two CTAs per SM over all row groups
-    G.cells_cta = ((ncell + ncta - 1) / ncta + tc::kKC - 1) / tc::kKC * tc::kKC;
-    G.ncb = (int)((ncell + G.cells_cta - 1) / G.cells_cta);
-    return G;
+// M[(j <= k)][i] (pair-major, device) of ng maps g against nh singles h (h == nullptr: h = g).
+int run_contract_tc(polybin_ctx* ctx, const float* g, int ng, const float* h, int nh, double*, size_t, double* d_out) {
+    const int hsep = (h && h != g) ? 1 : 0;
+    if (!hsep) nh = ng;
+    tc::Plan* pl = nullptr;
+    int rc = tc::full_plan(ctx, ng, nh, hsep, &pl);
+    if (rc) return rc;
+    return tc::launch(ctx, *pl, g, hsep ? h : g, d_out);
 }
 
-int run_contract_tc(polybin_ctx* ctx, const float* g, int ng, const float* h, int nh, double* d_partial,
-                    size_t partial_cap, double* d_out) {
-    if (!h) { h = g; nh = ng; }
-    ContractGeom G = contract_geom_tc(ng, nh, ctx->ncell);
-    if ((size_t)G.ncb * G.npairs * G.nh > partial_cap) return fail(ctx, POLYBIN_EINVAL, "contract_tc: partial buffer too small");
-    if (ctx->ncell % 4) return fail(ctx, POLYBIN_EINVAL, "contract_tc: the number of cells must be a multiple of 4");
-    int rc0 = ensure_err_flag(ctx);
-    if (rc0) return rc0;
-    cudaError_t e = cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream);
-    if (e != cudaSuccess) return fail_cuda(ctx, e, "cudaMemsetAsync", __FILE__, __LINE__);
-    const int rows = ng + (h != g ? nh : 0);
-    const size_t sm = tc_smem_bytes(rows);
-    e = cudaFuncSetAttribute((const void*)tc::k_contract_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return fail_cuda(ctx, e, "cudaFuncSetAttribute(k_contract_tc)", __FILE__, __LINE__);
-    tc::Params P;
-    P.g = g; P.h = h; P.ncell = ctx->ncell; P.cells_cta = G.cells_cta;
-    P.ng = ng; P.nh = nh; P.npairs = G.npairs; P.ntiles = G.ngroups;
-    P.pairs = ctx->d_pairs + pairs_offset(ng);
-    P.partial = d_partial;
-    P.err = ctx->d_err;
-    {
-        StageTimer timer(ctx, kStageContract);
-        const int nrg = (G.ngroups + tc::kTiles - 1) / tc::kTiles;
-        tc::k_contract_tc<<<dim3(G.ncb, nrg, 1), tc::kThreads, sm, ctx->stream>>>(P);
-        ctx->launches += 1;
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return fail_cuda(ctx, e, "k_contract_tc", __FILE__, __LINE__);
-        const long nout = (long)G.npairs * G.nh;
-        k_reduce_partials<<<(unsigned)((nout + 255) / 256), 256, 0, ctx->stream>>>(d_partial, G.ncb, nout, d_out);
-        ctx->launches += 1;
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return fail_cuda(ctx, e, "k_reduce_partials", __FILE__, __LINE__);
-    }
-    if (ctx->capturing) return POLYBIN_OK;   // the caller reads the error flag after the graph has run
-    int herr = 0;
-    e = cudaMemcpyAsync(&herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-    if (e != cudaSuccess) return fail_cuda(ctx, e, "contract_tc error flag", __FILE__, __LINE__);
-    if (herr) return fail(ctx, POLYBIN_ETIMEOUT, "contract_tc: a pipeline wait timed out");
-    return POLYBIN_OK;
+// Builds the closed-triplet plan ahead of time (before any stream capture).
+int prepare_triplet_tc(polybin_ctx* ctx) {
+    tc::Plan* pl = nullptr;
+    return tc::triplet_plan(ctx, &pl);
+}
+
+// S_abc of every closed triplet (device, triplet order) from the shell maps g.
+int run_triplet_sums_tc(polybin_ctx* ctx, const float* g, double* d_S) {
+    tc::Plan* pl = nullptr;
+    int rc = tc::triplet_plan(ctx, &pl);
+    if (rc) return rc;
+    return tc::launch(ctx, *pl, g, g, d_S);
 }
 
 }  // namespace pb

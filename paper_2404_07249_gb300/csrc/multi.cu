@@ -5,6 +5,8 @@
 // The graph is cached in the first context, keyed by the context ids and field pointers of the call.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include <cstring>
 #include <vector>
 
@@ -36,13 +38,14 @@ template <typename T>
 static int capture_field(polybin_ctx* c, const float* field, double* host_dst) {
     int rc;
     Work& w = c->w;
-    const int nb = c->nb, np = nb * (nb + 1) / 2;
+    const size_t nt = c->Nabc.size();
+    if (nt == 0) return POLYBIN_OK;
     if ((rc = run_forward<T, float, float>(c, field, (const float*)nullptr, (const float*)nullptr, (C<T>*)w.t1, (C<T>*)w.t2,
                                            (C<T>*)w.box)))
         return rc;
     if ((rc = run_shells<T>(c, (const C<T>*)w.box, (C<T>*)w.u1, (C<T>*)w.u2, (T*)w.g, 0))) return rc;
-    if ((rc = run_contract_any<T>(c, (const T*)w.g, nb, nullptr, nb, w.partial, w.partial_cap, w.mout))) return rc;
-    cudaError_t e = cudaMemcpyAsync(host_dst, w.mout, sizeof(double) * (size_t)np * nb, cudaMemcpyDeviceToHost, c->stream);
+    if ((rc = run_triplet_sums<T>(c, (const T*)w.g, c->d_S))) return rc;
+    cudaError_t e = cudaMemcpyAsync(host_dst, c->d_S, sizeof(double) * nt, cudaMemcpyDeviceToHost, c->stream);
     if (e != cudaSuccess) return fail_cuda(c, e, "capture copy", __FILE__, __LINE__);
     return POLYBIN_OK;
 }
@@ -85,7 +88,7 @@ extern "C" int polybin_bk_ideal_multi(polybin_ctx* const* ctxs, const float* con
         size_t total = 0;
         for (int i = 0; i < n_fields; ++i) {
             m->off.push_back(total);
-            total += (size_t)ctxs[i]->nb * (ctxs[i]->nb + 1) / 2 * ctxs[i]->nb;
+            total += std::max(ctxs[i]->Nabc.size(), (size_t)1);
         }
         {
             polybin_ctx* ctx = c0;
@@ -140,14 +143,10 @@ extern "C" int polybin_bk_ideal_multi(polybin_ctx* const* ctxs, const float* con
             PB_CUDA_OK(cudaMemcpy(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
         }
         if (herr) return fail(c0, POLYBIN_ETIMEOUT, "polybin_bk_ideal_multi: a pipeline wait timed out (field %d)", i);
-        const int nb = c->nb;
-        const double* M = m->host + m->off[i];
+        const double* S = m->host + m->off[i];
         const double pref = c->vol * c->vol / ((double)c->ncell * (double)c->ncell * (double)c->ncell);
         const size_t nt = c->Nabc.size();
-        for (size_t t = 0; t < nt; ++t) {
-            const int a = c->trip[3 * t], b = c->trip[3 * t + 1], cc = c->trip[3 * t + 2];
-            bk_out[i][t] = pref * M[(size_t)pair_index(nb, a, b) * nb + cc] / c->Tabc[t];
-        }
+        for (size_t t = 0; t < nt; ++t) bk_out[i][t] = pref * S[t] / c->Tabc[t];
     }
     return POLYBIN_OK;
 }

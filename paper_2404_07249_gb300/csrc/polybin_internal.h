@@ -78,8 +78,13 @@ void free_work(Work&);
 int resolve_input(polybin_ctx*, const float*, size_t, const float**);
 int ensure_triplets(polybin_ctx*);
 bool split_tc_available();
-ContractGeom contract_geom_tc(int ng, int nh, long ncell);
+bool tc_shape_ok(polybin_ctx*, const float* g, int ng, const float* h, int nh);
 int run_contract_tc(polybin_ctx*, const float*, int, const float*, int, double*, size_t, double*);
+int prepare_triplet_tc(polybin_ctx*);
+int run_triplet_sums_tc(polybin_ctx*, const float* g, double* d_S);
+void destroy_tc(polybin_ctx*);
+// S_abc of every closed triplet (device, triplet order) from the nb shell maps g of the context.
+template <typename T> int run_triplet_sums(polybin_ctx*, const T* g, double* d_S);
 void destroy_extras(polybin_ctx*);
 void destroy_unwindowed(polybin_ctx*);
 void destroy_multi(polybin_ctx*);
@@ -125,10 +130,15 @@ struct polybin_ctx {
     std::vector<double> counts;
     std::vector<double> fish_disc;   // [nb][nell][nell]
 
-    // closed triplets (lexicographic), T_abc and N_abc
+    // closed triplets (lexicographic), T_abc and N_abc; on the device: S_abc of the last field and the index of
+    // each triplet's entry in the pair-major contraction M[(a <= b)][c]
     bool trip_ready = false;
     std::vector<int> trip;
     std::vector<double> Tabc, Nabc;
+    double* d_S = nullptr;
+    int* d_trip_m = nullptr;
+    // tensor-core contraction plans
+    void* tc = nullptr;
 
     // instrumentation: kernel launches issued, and (when enabled) per-stage device time from CUDA events.
     // Stage brackets are recorded without blocking into tev (start, stop pairs) and read back lazily: when the

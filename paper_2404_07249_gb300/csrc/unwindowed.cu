@@ -753,10 +753,12 @@ static int bk_unwindowed_t(polybin_ctx* ctx, const float* d, const float* w, con
     // u = w d -> g[u] (kept in W.g)
     if ((rc = run_forward<T, float, float>(ctx, d, w, (const float*)nullptr, (C<T>*)W.t1, (C<T>*)W.t2, (C<T>*)W.box))) return rc;
     if ((rc = run_shells<T>(ctx, (const C<T>*)W.box, (C<T>*)W.u1, (C<T>*)W.u2, (T*)W.g, 0))) return rc;
-    std::vector<double> S((size_t)np * nb), lin(nt, 0.0), Mv((size_t)np * nb);
-    if ((rc = run_contract_any<T>(ctx, (const T*)W.g, nb, nullptr, nb, W.partial, W.partial_cap, W.mout))) return rc;
-    PB_CUDA_OK(cudaMemcpyAsync(S.data(), W.mout, sizeof(double) * S.size(), cudaMemcpyDeviceToHost, ctx->stream));
-    PB_CUDA_OK(cudaStreamSynchronize(ctx->stream));
+    std::vector<double> S(std::max(nt, 1), 0.0), lin(nt, 0.0), Mv((size_t)np * nb);
+    if (nt > 0) {
+        if ((rc = run_triplet_sums<T>(ctx, (const T*)W.g, ctx->d_S))) return rc;
+        PB_CUDA_OK(cudaMemcpyAsync(S.data(), ctx->d_S, sizeof(double) * nt, cudaMemcpyDeviceToHost, ctx->stream));
+        PB_CUDA_OK(cudaStreamSynchronize(ctx->stream));
+    }
     for (int i = 0; i < n_mocks; ++i) {
         const float* mock = mocks + (size_t)i * N;
         if ((rc = run_forward<T, float, float>(ctx, mock, w, (const float*)nullptr, (C<T>*)W.t1, (C<T>*)W.t2, (C<T>*)W.box))) return rc;
@@ -776,7 +778,7 @@ static int bk_unwindowed_t(polybin_ctx* ctx, const float* d, const float* w, con
         const int a = ctx->trip[3 * t], b = ctx->trip[3 * t + 1], c = ctx->trip[3 * t + 2];
         const double dl = (a == b && b == c) ? 6.0 : ((a == b || b == c) ? 2.0 : 1.0);
         if (n_mocks > 0) lin[t] /= n_mocks;
-        bnum[t] = (S[(size_t)pair_index(nb, a, b) * nb + c] - lin[t]) / dl;
+        bnum[t] = (S[t] - lin[t]) / dl;
     }
     if (bnum_out) std::memcpy(bnum_out, bnum.data(), sizeof(double) * nt);
     if (lin_out) std::memcpy(lin_out, lin.data(), sizeof(double) * nt);
