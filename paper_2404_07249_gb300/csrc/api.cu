@@ -205,12 +205,19 @@ int run_shells(polybin_ctx* ctx, const C<T>* box, C<T>* u1, C<T>* u2, T* g, int 
             b.it[i].kin = bb.rz.cnt;
         }
         const long nlines = (long)N0 * N1;
-        dim3 grid((unsigned)((nlines + 2 * LP - 1) / (2 * LP)), nb, 1);
-        PB_WITH_NT(N2, NT, {
-            if ((rc = set_smem<T>(ctx, (const void*)k_inv_z<T, NT>, sm))) return rc;
-            k_inv_z<T, NT><<<grid, 256, sm, ctx->stream>>>(b, nlines, T(1), (const T*)nullptr, ctx->plan[2],
-                                                          twiddles<T>(ctx, 2), LP);
-        })
+        if (N2 == 512) {
+            // register-resident 512-point transform, 16 line pairs per CTA
+            const int lpc = 16;
+            dim3 grid512((unsigned)(((nlines + 1) / 2 + lpc - 1) / lpc), nb, 1);
+            k_inv_z512<T><<<grid512, 256, 0, ctx->stream>>>(b, nlines, T(1), (const T*)nullptr, twiddles<T>(ctx, 2), lpc);
+        } else {
+            dim3 grid((unsigned)((nlines + 2 * LP - 1) / (2 * LP)), nb, 1);
+            PB_WITH_NT(N2, NT, {
+                if ((rc = set_smem<T>(ctx, (const void*)k_inv_z<T, NT>, sm))) return rc;
+                k_inv_z<T, NT><<<grid, 256, sm, ctx->stream>>>(b, nlines, T(1), (const T*)nullptr, ctx->plan[2],
+                                                              twiddles<T>(ctx, 2), LP);
+            })
+        }
         if ((rc = launch_check(ctx, "k_inv_z"))) return rc;
     }
     return POLYBIN_OK;

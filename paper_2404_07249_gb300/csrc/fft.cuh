@@ -331,6 +331,115 @@ __global__ void __launch_bounds__(256) k_inv_z(ZInvBatch batch, long nlines, T s
     }
 }
 
+// z-pass, inverse (C2R), length 512, register-resident: the same result as k_inv_z (including the packing of
+// line pairs and the treatment of the kz = 0 and n/2 coefficients) computed as 512 = 8 x 8 x 8.  A group of 64
+// threads transforms one packed line pair: thread t holds the eight points Z[t + 64 j]; stage 1 takes the 8-point
+// DFT over j and multiplies by w512^(t k1); stage 2 (after an exchange through shared memory) the DFT over
+// t2 = t / 8 and multiplies by w64^(t1 m1); stage 3 the DFT over t1 = t % 8, which leaves X[k1 + 8 m1 + 64 m2] in
+// the thread; a last exchange through shared memory makes the 2 x 512 real outputs coalesced.  Twiddles are
+// read once per thread from the table tw[m] = e^{-2 pi i m / 512}.  Four groups per CTA, each synchronised by its
+// own named barrier; a CTA takes `lpc` line pairs of one item (blockIdx.y).
+__device__ __forceinline__ void group_sync(int gid) {
+    asm volatile("bar.sync %0, 64;" ::"r"(gid + 1) : "memory");
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_inv_z512(ZInvBatch batch, long nlines, T scale, const T* __restrict__ mulout,
+                                                 const C<T>* __restrict__ twg, int lpc) {
+    constexpr int N = 512, PAD = 9;                     // exchange rows of 8 complex values padded to 9
+    __shared__ C<T> sbuf[4][64 * PAD];
+    const ZInvItem item = batch.it[blockIdx.y];
+    const C<T>* __restrict__ in = static_cast<const C<T>*>(item.in);
+    T* __restrict__ out = static_cast<T*>(item.out);
+    const int kin = item.kin;
+    const int gid = threadIdx.x >> 6, t = threadIdx.x & 63;
+    C<T>* buf = sbuf[gid];
+    // per-thread twiddles (inverse transform: conjugates of the table)
+    C<T> w1[8], w2[8];
+    const int t1 = t & 7, k1s2 = t >> 3;                // stage-2 / stage-3 roles of this thread
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const C<T> a = twg[(t * r) & (N - 1)];
+        const C<T> b = twg[(8 * t1 * r) & (N - 1)];
+        w1[r] = mk<T>(a.x, -a.y);
+        w2[r] = mk<T>(b.x, -b.y);
+    }
+    const long npairs = (nlines + 1) / 2;
+    for (int q = gid; q < lpc; q += 4) {
+        const long p = (long)blockIdx.x * lpc + q;
+        if (p >= npairs) break;                          // uniform within the group
+        const long l1 = 2 * p, l2 = 2 * p + 1;
+        const C<T>* in1 = in + l1 * kin;
+        const C<T>* in2 = in + l2 * kin;
+        const bool has2 = l2 < nlines;
+        // stage 1: load Z[t + 64 j] (packed Hermitian pair), DFT over j, twiddle w512^(t k1)
+        C<T> v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int k = t + 64 * j;
+            C<T> z = mk<T>(T(0), T(0));
+            if (k == 0 || 2 * k == N) {
+                if (k < kin) z = mk<T>(in1[k].x, has2 ? in2[k].x : T(0));
+            } else if (k < kin) {
+                const C<T> a = in1[k];
+                const C<T> b = has2 ? in2[k] : mk<T>(T(0), T(0));
+                z = mk<T>(a.x - b.y, a.y + b.x);
+            } else if (N - k < kin) {
+                const C<T> a = in1[N - k];
+                const C<T> b = has2 ? in2[N - k] : mk<T>(T(0), T(0));
+                z = mk<T>(a.x + b.y, b.x - a.y);
+            }
+            v[j] = z;
+        }
+        dft<T, +1>(v, 8);
+#pragma unroll
+        for (int r = 1; r < 8; ++r) v[r] = mul<T>(v[r], w1[r]);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) buf[t * PAD + r] = v[r];
+        group_sync(gid);
+        // stage 2: thread (t1, k1) = (t % 8, t / 8) takes Y[t1 + 8 t2][k1], DFT over t2, twiddle w64^(t1 m1)
+#pragma unroll
+        for (int r = 0; r < 8; ++r) v[r] = buf[(t1 + 8 * r) * PAD + k1s2];
+        dft<T, +1>(v, 8);
+#pragma unroll
+        for (int r = 1; r < 8; ++r) v[r] = mul<T>(v[r], w2[r]);
+        group_sync(gid);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) buf[(k1s2 * 8 + r) * PAD + t1] = v[r];   // row (k1, m1), column t1
+        group_sync(gid);
+        // stage 3: thread w = (k1, m1) = (t / 8, t % 8) takes W[t1] for t1 = 0..7, DFT over t1 -> X[k1 + 8 m1 + 64 m2]
+#pragma unroll
+        for (int r = 0; r < 8; ++r) v[r] = buf[t * PAD + r];
+        dft<T, +1>(v, 8);
+        group_sync(gid);
+        // outputs: real parts -> line l1, imaginary parts -> line l2, via shared memory for coalesced stores
+        T* re = reinterpret_cast<T*>(buf);
+        T* im = re + N + 8;
+        const int k1 = t >> 3, m1 = t & 7;
+#pragma unroll
+        for (int m2 = 0; m2 < 8; ++m2) {
+            const int x = k1 + 8 * m1 + 64 * m2;
+            re[x] = v[m2].x * scale;
+            im[x] = v[m2].y * scale;
+        }
+        group_sync(gid);
+        T* o1 = out + l1 * N;
+        T* o2 = out + l2 * N;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int x = t + 64 * e;
+            T a = re[x], b = im[x];
+            if (mulout) {
+                a *= mulout[l1 * N + x];
+                if (has2) b *= mulout[l2 * N + x];
+            }
+            o1[x] = a;
+            if (has2) o2[x] = b;
+        }
+        group_sync(gid);
+    }
+}
+
 // ------------------------------------------------------------------------------------------------
 // Strided column pass (y or x axis).  Each CTA transforms TK consecutive columns of one outer slab.
 //   forward (DIR = -1): input positions 0..n-1 at in[o*in_os + i*in_es + c]; keeps wave numbers

@@ -378,12 +378,18 @@ static int run_inverse_box(polybin_ctx* ctx, const C<T>* box, C<T>* v1, C<T>* v2
         ZInvBatch b;
         b.it[0].in = v2; b.it[0].out = out; b.it[0].kin = Bz;
         const long nlines = (long)N0 * N1;
-        PB_WITH_NT(N2, NT, {
-            e = cudaFuncSetAttribute((const void*)k_inv_z<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            if (e != cudaSuccess) return fail_cuda(ctx, e, "attr", __FILE__, __LINE__);
-            k_inv_z<T, NT><<<dim3((unsigned)((nlines + 2 * lp - 1) / (2 * lp)), 1, 1), 256, sm, ctx->stream>>>(
-                b, nlines, T(1.0 / (double)ctx->ncell), mulout, ctx->plan[2], tw2, lp);
-        })
+        if (N2 == 512) {
+            const int lpc = 16;
+            k_inv_z512<T><<<dim3((unsigned)(((nlines + 1) / 2 + lpc - 1) / lpc), 1, 1), 256, 0, ctx->stream>>>(
+                b, nlines, T(1.0 / (double)ctx->ncell), mulout, tw2, lpc);
+        } else {
+            PB_WITH_NT(N2, NT, {
+                e = cudaFuncSetAttribute((const void*)k_inv_z<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+                if (e != cudaSuccess) return fail_cuda(ctx, e, "attr", __FILE__, __LINE__);
+                k_inv_z<T, NT><<<dim3((unsigned)((nlines + 2 * lp - 1) / (2 * lp)), 1, 1), 256, sm, ctx->stream>>>(
+                    b, nlines, T(1.0 / (double)ctx->ncell), mulout, ctx->plan[2], tw2, lp);
+            })
+        }
         ctx->launches++;
     }
     e = cudaGetLastError();

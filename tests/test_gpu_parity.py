@@ -43,6 +43,8 @@ CASES = [
     ((40, 40, 40), 700.0, 1.0 + 1.5 * np.arange(8), "lognormal"),      # radix 5
     ((32, 48, 40), 800.0, 1.0 + 2.0 * np.arange(6), "lognormal"),      # non-cubic grid, cubic box
     ((16, 16, 16), 500.0, np.array([0.5, 3.0, 6.0, 9.5, 14.0]), "lognormal"),  # bins beyond Nyquist (full axes)
+    ((16, 8, 512), 2000.0, 1.0 + 6.0 * np.arange(8), "lognormal"),    # 512-point z lines, few z modes
+    ((8, 4, 512), 2000.0, 1.0 + 40.0 * np.arange(8), "lognormal"),    # 512-point z lines up to the z Nyquist
 ]
 
 
