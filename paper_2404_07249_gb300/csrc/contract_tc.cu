@@ -214,6 +214,19 @@ __device__ __forceinline__ void tmem_wait_ld16(uint32_t* v) {
                  : "memory");
 }
 
+// tcgen05.wait::ld tied to three 16-register loads (48 operands).
+__device__ __forceinline__ void tmem_wait_ld48(uint32_t* a, uint32_t* b, uint32_t* c) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]), "+r"(a[6]), "+r"(a[7]),
+                   "+r"(a[8]), "+r"(a[9]), "+r"(a[10]), "+r"(a[11]), "+r"(a[12]), "+r"(a[13]), "+r"(a[14]), "+r"(a[15]),
+                   "+r"(b[0]), "+r"(b[1]), "+r"(b[2]), "+r"(b[3]), "+r"(b[4]), "+r"(b[5]), "+r"(b[6]), "+r"(b[7]),
+                   "+r"(b[8]), "+r"(b[9]), "+r"(b[10]), "+r"(b[11]), "+r"(b[12]), "+r"(b[13]), "+r"(b[14]), "+r"(b[15]),
+                   "+r"(c[0]), "+r"(c[1]), "+r"(c[2]), "+r"(c[3]), "+r"(c[4]), "+r"(c[5]), "+r"(c[6]), "+r"(c[7]),
+                   "+r"(c[8]), "+r"(c[9]), "+r"(c[10]), "+r"(c[11]), "+r"(c[12]), "+r"(c[13]), "+r"(c[14]), "+r"(c[15])
+                 :
+                 : "memory");
+}
+
 // Shared-memory matrix descriptor, no swizzle (canonical K-major layout): core matrices of 8 rows x 16 bytes;
 // LBO = byte distance between core matrices adjacent in K, SBO = between 8-row groups.
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
@@ -296,13 +309,16 @@ __device__ __forceinline__ void epilogue(const GroupDesc& G, const Params& P, ui
         const uint32_t dbase = tmem + lane_base + (uint32_t)db * d_cols;
 #pragma unroll
         for (int u = 0; u < NU; ++u)
+            {
+                // the three pieces in flight together, one wait
+                uint32_t v0[16], v1[16], v2[16];
+                tmem_ld16(dbase + cols[u][0], v0);
+                tmem_ld16(dbase + cols[u][1], v1);
+                tmem_ld16(dbase + cols[u][2], v2);
+                tmem_wait_ld48(v0, v1, v2);
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                uint32_t v[16];
-                tmem_ld16(dbase + cols[u][k], v);
-                tmem_wait_ld16(v);
-#pragma unroll
-                for (int j = 0; j < 16; ++j) acc[u][j] += __uint_as_float(v[j]);
+                for (int j = 0; j < 16; ++j)
+                    acc[u][j] += (__uint_as_float(v0[j]) + __uint_as_float(v1[j])) + __uint_as_float(v2[j]);
             }
         tc_fence_before();
         mbar_arrive(&d_empty[db]);
