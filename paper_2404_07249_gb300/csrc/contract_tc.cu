@@ -65,6 +65,7 @@ constexpr int kWarps = 1 + kProdWarps + kIssWarps + kEpiWarps;
 constexpr int kThreads = 32 * kWarps;
 constexpr int kMinSmem = 120 * 1024;   // one CTA per SM (the CTA allocates all 512 TMEM columns)
 constexpr unsigned kSpinLimit = 1u << 22;
+constexpr int kBloItems = 2;       // B_lo chunks per producer thread: <= 64 singles rows x 8 chunks / 256 threads
 
 struct GroupDesc {
     int tile0;                 // first tile (row table index / 128)
@@ -72,12 +73,11 @@ struct GroupDesc {
     int unit_base;             // first unit of this group in the partial layout
     int d_cols;                // TMEM columns of one accumulator buffer (kDBuf buffers at 0, d_cols, ...)
     int a_col0;                // first TMEM column of the A ring
-    int bstage_bytes;          // B operand bytes per A stage (all windows)
+    int bstage_bytes;          // B_lo bytes per A stage (the singles region of a slot)
     int tile_w[kMaxTiles];
     int dm_col[kMaxTiles];     // TMEM column of tile t's hi*[hi | lo] accumulator (2W columns)
     int dl_col[kMaxTiles];     // TMEM column of tile t's lo*hi accumulator (W columns)
     int tile_s0[kMaxTiles];    // first single of tile t's window
-    int tile_boff[kMaxTiles];  // byte offset of tile t's B block within a B stage (2W rows x 32 cells)
     int unit_tile[kMaxUnits], unit_c[kMaxUnits];
 };
 
@@ -85,6 +85,7 @@ struct Params {
     long ncell, cells_cta;
     int ng, nh, hsep, h_row0;  // maps in the slot; singles; singles from the h part; first h row in a slot
     int slot_bytes, off_b, off_acc, off_bar;
+    int s_off, s_chunks;       // singles region of a slot: byte offset and 16-byte chunks (B_lo is made for all)
     int total_units;
     const short2* rows;        // [tiles][128] pairs (j, k); (-1, -1) pads
     double* partial;           // [gridDim.x][total_units][16][128]
@@ -238,22 +239,42 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t
     return d;                 // base offset 0, layout type 0 (no swizzle)
 }
 
+// Shared-memory matrix descriptor for the 128-byte swizzle, K-major: 8-row x 128-byte atoms (1024-byte aligned,
+// chunk c of row r at r * 128 + ((c ^ (r % 8)) << 4), the layout TMA writes), SBO = 1024 between 8-row groups; the
+// K offset within the atom is added to the start address (32 bytes per K = 8 step of TF32).
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1 << 16;                    // LBO: unused for a swizzled K-major operand
+    d |= (uint64_t)(1024 >> 4) << 32;          // SBO
+    d |= (uint64_t)1 << 46;                    // descriptor version for tcgen05
+    d |= (uint64_t)2 << 61;                    // 128-byte swizzle
+    return d;
+}
+
 // Instruction descriptor: kind::tf32, D = F32, A = B = TF32, both K-major.
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// The MMA and its commit are executed by a whole converged warp and issued by the one lane that elect.sync picks
+// (the same lane every time with all 32 active, so the commit tracks the MMAs of the issuing thread).  Keeping the
+// issuing code warp-uniform, rather than inside a one-lane branch, lets the compiler hold the operands in uniform
+// registers: measured on this part, one thread then issues an M = 128, N = 32 MMA every ~16 cycles (the tensor
+// pipe's rate) instead of one every ~200 cycles from a divergent branch.
 __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
                                          uint32_t accum) {
     asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "{\n\t.reg .pred p, q;\n\telect.sync _|q, 0xffffffff;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "@q tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
         "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accum)
         : "memory");
 }
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
+    asm volatile(
+        "{\n\t.reg .pred q;\n\telect.sync _|q, 0xffffffff;\n\t"
+        "@q tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}" ::"r"(smem_u32(bar))
+        : "memory");
 }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
@@ -344,9 +365,7 @@ __device__ __forceinline__ void epilogue(const GroupDesc& G, const Params& P, ui
 // compile-time count: every tile's products live in their own registers, so the next tile's arithmetic does not
 // wait for the previous tile's TMEM store to read its registers).  A thread owns TMEM lane 32 (warp % 4) + lane,
 // i.e. row `row` of every tile.  The 64 columns of a tile's stage block are [hi 16 | lo 16] of half 0, then of half
-// 1; a thread writes its half with one 32-column TMEM store per tile.
-constexpr int kMaxItems = 2;   // B items per producer thread: 4 W items a tile per group, W summed <= 48 -> <= 192 / 128
-
+// 1; a thread writes its half with one 32-column TMEM store per tile.  (The B operand is made by warp 0.)
 template <int NT>
 __device__ __forceinline__ void producer(const GroupDesc& G, const Params& P, uint32_t tmem, const unsigned char* ring,
                                          unsigned char* bst, uint64_t* slot_full, uint64_t* slot_empty,
@@ -357,6 +376,8 @@ __device__ __forceinline__ void producer(const GroupDesc& G, const Params& P, ui
     const int row = 32 * q + lane;
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
     const int nA = G.nA, a_col0 = G.a_col0, slot_bytes = P.slot_bytes, bstage_bytes = G.bstage_bytes;
+    const int s_off = P.s_off, s_chunks = P.s_chunks;
+    const int ptid = 32 * (warp - 1) + lane;   // 0 .. 255 over both groups
     int* const err = P.err;
     int pj[NT], pk[NT];
 #pragma unroll
@@ -364,38 +385,6 @@ __device__ __forceinline__ void producer(const GroupDesc& G, const Params& P, ui
         const short2 jk = P.rows[(size_t)(G.tile0 + t) * 128 + row];
         pj[t] = jk.x;
         pk[t] = jk.y;
-    }
-    // B operand items of this thread, decoded once.  Tile t's B block holds rows n < W (hi of single s0 + n) and
-    // rows W + n (lo), 32 cells each: element (row, cell k) at (row / 8) * 1024 + (k / 4) * 128 + (row % 8) * 16 +
-    // (k % 4) * 4 bytes.  An item is one single and one 4-cell piece of this group's half: it loads 16 bytes from
-    // the ring and stores the hi and the lo piece.  bsrc = map row in the slot (-1: zero), boff = byte offset of the
-    // hi piece in the B stage (the lo piece is at boff + blo_d), bquad = 4-cell piece within the half.
-    const int ptid = 32 * ((warp - 1) & 3) + lane;       // 0 .. 127 within the group
-    int bsrc[kMaxItems], boff[kMaxItems], blo_d[kMaxItems], bquad[kMaxItems];
-    int nmine = 0;
-    {
-        int total = 0;
-#pragma unroll
-        for (int t = 0; t < NT; ++t) total += 4 * G.tile_w[t];
-#pragma unroll
-        for (int m = 0; m < kMaxItems; ++m) {
-            const int it = ptid + 128 * m;
-            bsrc[m] = -1;
-            boff[m] = blo_d[m] = bquad[m] = 0;
-            if (it < total) {
-                int t = 0, loc = it;
-                while (t + 1 < NT && loc >= 4 * G.tile_w[t]) { loc -= 4 * G.tile_w[t]; ++t; }
-                const int W = G.tile_w[t];
-                const int n = loc % W, quad = loc / W;
-                const int si = G.tile_s0[t] + n;
-                if (si < P.nh) bsrc[m] = P.hsep ? P.h_row0 + si : si;
-                const int col = (4 * gp + quad) * 128 + (n & 7) * 16;
-                boff[m] = G.tile_boff[t] + (n >> 3) * 1024 + col;
-                blo_d[m] = (((W + n) >> 3) - (n >> 3)) * 1024;
-                bquad[m] = quad;
-                nmine = m + 1;
-            }
-        }
     }
     for (int st = 0; st < nstages; ++st) {
         const int s = st % kRingSlots;
@@ -405,10 +394,12 @@ __device__ __forceinline__ void producer(const GroupDesc& G, const Params& P, ui
         if (!ok) break;
         tc_fence_after();
         const unsigned char* slot = ring + (size_t)s * slot_bytes;
-        float4 bx[kMaxItems];
+        // B_lo chunks of this thread: loaded first, so that their latency hides behind the pair products
+        uint4 bl[kBloItems];
 #pragma unroll
-        for (int m = 0; m < kMaxItems; ++m)
-            if (m < nmine && bsrc[m] >= 0) bx[m] = *ring_chunk(slot, bsrc[m], 4 * gp + bquad[m]);
+        for (int m = 0; m < kBloItems; ++m)
+            if (ptid + 256 * m < s_chunks)
+                bl[m] = *reinterpret_cast<const uint4*>(slot + s_off + 16 * (ptid + 256 * m));
         uint32_t v[NT][32];
 #pragma unroll
         for (int t = 0; t < NT; ++t) {
@@ -439,22 +430,22 @@ __device__ __forceinline__ void producer(const GroupDesc& G, const Params& P, ui
             }
             tmem_st32(tmem + lane_base + (uint32_t)(a_col0 + as * 64 * NT + 64 * t + 32 * gp), v[t]);
         }
+        // B_lo = (g - trunc(g)) rounded to TF32 (nearest, ties away), at the same byte offset as g (same swizzle)
         unsigned char* bs = bst + (size_t)as * bstage_bytes;
 #pragma unroll
-        for (int m = 0; m < kMaxItems; ++m) {
-            if (m >= nmine) break;
-            uint64_t h01 = 0, h23 = 0, l01 = 0, l23 = 0;
-            if (bsrc[m] >= 0) {
-                split_x2(f2pack(bx[m].x, bx[m].y), h01, l01);
-                split_x2(f2pack(bx[m].z, bx[m].w), h23, l23);
+        for (int m = 0; m < kBloItems; ++m)
+            if (ptid + 256 * m < s_chunks) {
+                uint32_t* w = reinterpret_cast<uint32_t*>(&bl[m]);
+                const uint64_t g01 = (uint64_t)w[0] | ((uint64_t)w[1] << 32);
+                const uint64_t g23 = (uint64_t)w[2] | ((uint64_t)w[3] << 32);
+                const uint64_t t01 = g01 & 0xFFFFE000FFFFE000ull, t23 = g23 & 0xFFFFE000FFFFE000ull;
+                const uint64_t l01 = sub_x2(g01, t01), l23 = sub_x2(g23, t23);
+                *reinterpret_cast<uint4*>(bs + 16 * (ptid + 256 * m)) =
+                    make_uint4(((uint32_t)l01 + 0x1000u) & 0xFFFFE000u, ((uint32_t)(l01 >> 32) + 0x1000u) & 0xFFFFE000u,
+                               ((uint32_t)l23 + 0x1000u) & 0xFFFFE000u, ((uint32_t)(l23 >> 32) + 0x1000u) & 0xFFFFE000u);
             }
-            *reinterpret_cast<uint4*>(bs + boff[m]) =
-                make_uint4((uint32_t)h01, (uint32_t)(h01 >> 32), (uint32_t)h23, (uint32_t)(h23 >> 32));
-            *reinterpret_cast<uint4*>(bs + boff[m] + blo_d[m]) =
-                make_uint4((uint32_t)l01, (uint32_t)(l01 >> 32), (uint32_t)l23, (uint32_t)(l23 >> 32));
-        }
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // B_lo stores -> tensor core
         tc_fence_before();
         mbar_arrive(&a_full[as]);
         mbar_arrive(&slot_empty[s]);
@@ -495,10 +486,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (tid == 0) {
         for (int s = 0; s < kRingSlots; ++s) {
             mbar_init(&slot_full[s], 1);
-            mbar_init(&slot_empty[s], 32 * kProdWarps);
+            mbar_init(&slot_empty[s], 32 * kProdWarps + ntiles);   // producers read a slot, the MMAs read B_hi
         }
         for (int s = 0; s < kMaxAStages; ++s) {
-            mbar_init(&a_full[s], 32 * kProdWarps);   // both producer groups make a stage
+            mbar_init(&a_full[s], 32 * kProdWarps);   // both producer groups make a stage (A and B_lo)
             mbar_init(&a_empty[s], ntiles);        // one commit per issuing thread (tile)
         }
         for (int i = 0; i < 2 * kMaxTiles; ++i) mbar_init(&d_full[i], 1);
@@ -549,47 +540,52 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else if (warp <= kProdWarps + kIssWarps) {
         // ------------------------------------------------------------------ MMA issue
-        // The whole warp runs the loop (converged; every lane polls the barriers), lane 0 issues and commits.
+        // The whole warp runs the loop (converged; every lane polls the barriers); the elected lane issues and
+        // commits inside mma_tf32 / mma_commit.
         const int t = warp - 1 - kProdWarps;
         if (t < ntiles) {
             const int W = G.tile_w[t];
-            const uint32_t idesc_m = idesc_tf32(128, 2 * W), idesc_l = idesc_tf32(128, W);
+            const uint32_t idesc_w = idesc_tf32(128, W);
             const uint32_t dm = (uint32_t)G.dm_col[t], dl = (uint32_t)G.dl_col[t];
             const uint32_t d_cols = (uint32_t)G.d_cols;
             const uint32_t aoff = (uint32_t)(64 * t);
-            const uint32_t b0 = smem_u32(bst + G.tile_boff[t]);
+            // tile t's window of singles: rows s0 .. s0 + W - 1 of a slot's singles region (B_hi: the slot itself,
+            // read as TF32, i.e. truncated) and of the B_lo stage (same layout)
+            const uint32_t bh0 = smem_u32(ring + P.s_off + 128 * G.tile_s0[t]);
+            const uint32_t bl0 = smem_u32(bst + 128 * G.tile_s0[t]);
             for (int st = 0; st < nstages; ++st) {
+                const int s = st % kRingSlots;
                 const int as = st % nA;
                 const int per = st / kPeriod, db = per % kDBuf;
                 const bool pstart = (st % kPeriod) == 0;
                 if (pstart && per >= kDBuf &&
                     !warp_wait(&d_empty[db], (uint32_t)((per / kDBuf - 1) & 1), abort_flag, err))
                     break;
+                if (!warp_wait(&slot_full[s], (uint32_t)((st / kRingSlots) & 1), abort_flag, err)) break;
                 if (!warp_wait(&a_full[as], (uint32_t)((st / nA) & 1), abort_flag, err)) break;
-                if (lane == 0) {
-                    tc_fence_after();
-                    const uint32_t bb = b0 + (uint32_t)(as * bstage_bytes);
-                    const uint32_t aa = tmem + (uint32_t)(a_col0 + as * 64 * ntiles) + aoff;
-                    const uint32_t dbuf = tmem + (uint32_t)db * d_cols;
+                tc_fence_after();
+                const uint32_t aa = tmem + (uint32_t)(a_col0 + as * 64 * ntiles) + aoff;
+                const uint32_t dbuf = tmem + (uint32_t)db * d_cols;
+                const uint64_t bh = sdesc_sw128(bh0 + (uint32_t)(s * slot_bytes));
+                const uint64_t bl = sdesc_sw128(bl0 + (uint32_t)(as * bstage_bytes));
 #pragma unroll
-                    for (int ks = 0; ks < kKC / 8; ++ks) {
-                        // K step ks: cells 8 ks .. 8 ks + 7; A_hi at half (ks / 2), column 8 (ks % 2); A_lo at +16
-                        const uint64_t bd = sdesc(bb + 256u * ks, 128, 1024);
-                        const uint32_t ah = aa + 32u * (ks >> 1) + 8u * (ks & 1);
-                        const uint32_t acc = (pstart && ks == 0) ? 0u : 1u;
-                        mma_tf32(dbuf + dm, ah, bd, idesc_m, acc);          // A_hi . [B_hi | B_lo]
-                        mma_tf32(dbuf + dl, ah + 16u, bd, idesc_l, acc);    // A_lo . B_hi (independent chain)
-                    }
-                    mma_commit(&a_empty[as]);
-                    if ((st % kPeriod) == kPeriod - 1 || st == nstages - 1) mma_commit(&d_full[db * kMaxTiles + t]);
+                for (int ks = 0; ks < kKC / 8; ++ks) {
+                    // K step ks: cells 8 ks .. 8 ks + 7; A_hi at half (ks / 2), column 8 (ks % 2); A_lo at +16.  B
+                    // advances 32 bytes a step within the swizzle atom (2 in the descriptor's address field, which
+                    // cannot carry out: the shared-memory window is 2^18 bytes)
+                    const uint32_t ah = aa + 32u * (ks >> 1) + 8u * (ks & 1);
+                    const uint32_t acc = (pstart && ks == 0) ? 0u : 1u;
+                    mma_tf32(dbuf + dm, ah, bh + (uint64_t)(2 * ks), idesc_w, acc);                 // A_hi . B_hi
+                    mma_tf32(dbuf + dm + (uint32_t)W, ah, bl + (uint64_t)(2 * ks), idesc_w, acc);   // A_hi . B_lo
+                    mma_tf32(dbuf + dl, ah + 16u, bh + (uint64_t)(2 * ks), idesc_w, acc);           // A_lo . B_hi
                 }
-                __syncwarp();
+                mma_commit(&a_empty[as]);
+                mma_commit(&slot_empty[s]);
+                if ((st % kPeriod) == kPeriod - 1 || st == nstages - 1) mma_commit(&d_full[db * kMaxTiles + t]);
             }
-            if (lane == 0) {
-                // every MMA issued by this thread has completed before TMEM is released
-                mma_commit(&fin[t]);
-                drain_wait(&fin[t], 0, err);
-            }
+            // every MMA issued by the elected thread has completed before TMEM is released
+            mma_commit(&fin[t]);
+            drain_wait(&fin[t], 0, err);
             __syncwarp();
         }
     } else {
@@ -727,6 +723,10 @@ static const char* layout_plan(Plan& pl, long ncell, int nsm, int ng, int nh, in
     const int grows = (ng + 7) / 8 * 8;
     P.h_row0 = grows;
     P.slot_bytes = (grows + (hsep ? (nh + 7) / 8 * 8 : 0)) * 128;
+    const int srows = hsep ? (nh + 7) / 8 * 8 : grows;     // rows of the singles region of a slot
+    P.s_off = hsep ? grows * 128 : 0;
+    P.s_chunks = srows * 8;
+    if (P.s_chunks > 256 * kBloItems) return "contract_tc: more than 64 rows of singles";
     int max_b = 0, max_units = 0;
     rows.assign(tiles.size() * 128, make_short2(-1, -1));
     gidx.assign(std::max(n_out, 1), 0);
@@ -748,16 +748,13 @@ static const char* layout_plan(Plan& pl, long ncell, int nsm, int ng, int nh, in
         D.d_cols = (col + 31) / 32 * 32;
         D.a_col0 = kDBuf * D.d_cols;
         D.nA = std::min(kMaxAStages, (512 - D.a_col0) / (2 * kKC * nt));
-        // B blocks: one per tile (its window's hi and lo rows x the 32 cells of a stage)
-        int boff = 0;
+        // windows of singles; B_lo stages hold a slot's whole singles region
         for (int t = 0; t < nt; ++t) {
             const TileH& T = tiles[t0 + t];
             D.tile_w[t] = T.W;
             D.tile_s0[t] = T.s0;
-            D.tile_boff[t] = boff;
-            boff += 2 * T.W * 4 * kKC;
         }
-        D.bstage_bytes = (boff + 1023) / 1024 * 1024;
+        D.bstage_bytes = srows * 128;
         max_b = std::max(max_b, D.nA * D.bstage_bytes);
         // output units
         int u = 0;
