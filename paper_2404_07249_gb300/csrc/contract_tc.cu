@@ -59,9 +59,16 @@ constexpr int kMaxUnits = 3;       // 16-column output units per CTA (16 FP32 su
 constexpr int kMaxGroups = 4;      // row groups (grid.y)
 constexpr int kProdGroups = 2;     // producer warp groups; group g makes half g (16 cells) of every stage
 constexpr int kProdWarps = 4 * kProdGroups;
-constexpr int kIssWarps = kMaxTiles;   // lane 0 of warp t issues the MMAs of tile t
 constexpr int kEpiWarps = 4;
-constexpr int kWarps = 1 + kProdWarps + kIssWarps + kEpiWarps;
+// Warpgroup 0: TMA (warp 0), MMA issue (warp 1), two idle warps; warpgroups 1-2: producers; warpgroup 3: epilogue.
+constexpr int kProdWarp0 = 4;
+constexpr int kWarps = 16;
+// Register split (setmaxnreg, per warpgroup): the CTA is launched with 128 registers a thread (65536 in all);
+// warpgroup 0 gives registers back, the producers take them, the epilogue keeps 128:
+// 48 * 128 + 168 * 256 + 128 * 128 = 65536.
+constexpr int kRegsLaunch = 128, kRegsCtl = 48, kRegsProd = 168;
+static_assert(kRegsCtl * 128 + kRegsProd * 256 + kRegsLaunch * 128 <= kRegsLaunch * 32 * kWarps,
+              "register split exceeds the launch allocation");
 constexpr int kThreads = 32 * kWarps;
 constexpr int kMinSmem = 120 * 1024;   // one CTA per SM (the CTA allocates all 512 TMEM columns)
 constexpr unsigned kSpinLimit = 1u << 22;
@@ -75,8 +82,7 @@ struct GroupDesc {
     int a_col0;                // first TMEM column of the A ring
     int bstage_bytes;          // B_lo bytes per A stage (the singles region of a slot)
     int tile_w[kMaxTiles];
-    int dm_col[kMaxTiles];     // TMEM column of tile t's hi*[hi | lo] accumulator (2W columns)
-    int dl_col[kMaxTiles];     // TMEM column of tile t's lo*hi accumulator (W columns)
+    int dm_col[kMaxTiles];     // TMEM column of tile t's accumulator: [hi*hi | hi*lo + lo*hi] (2W columns)
     int tile_s0[kMaxTiles];    // first single of tile t's window
     int unit_tile[kMaxUnits], unit_c[kMaxUnits];
 };
@@ -215,15 +221,13 @@ __device__ __forceinline__ void tmem_wait_ld16(uint32_t* v) {
                  : "memory");
 }
 
-// tcgen05.wait::ld tied to three 16-register loads (48 operands).
-__device__ __forceinline__ void tmem_wait_ld48(uint32_t* a, uint32_t* b, uint32_t* c) {
+// tcgen05.wait::ld tied to two 16-register loads (32 operands).
+__device__ __forceinline__ void tmem_wait_ld32(uint32_t* a, uint32_t* b) {
     asm volatile("tcgen05.wait::ld.sync.aligned;"
                  : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]), "+r"(a[6]), "+r"(a[7]),
                    "+r"(a[8]), "+r"(a[9]), "+r"(a[10]), "+r"(a[11]), "+r"(a[12]), "+r"(a[13]), "+r"(a[14]), "+r"(a[15]),
                    "+r"(b[0]), "+r"(b[1]), "+r"(b[2]), "+r"(b[3]), "+r"(b[4]), "+r"(b[5]), "+r"(b[6]), "+r"(b[7]),
-                   "+r"(b[8]), "+r"(b[9]), "+r"(b[10]), "+r"(b[11]), "+r"(b[12]), "+r"(b[13]), "+r"(b[14]), "+r"(b[15]),
-                   "+r"(c[0]), "+r"(c[1]), "+r"(c[2]), "+r"(c[3]), "+r"(c[4]), "+r"(c[5]), "+r"(c[6]), "+r"(c[7]),
-                   "+r"(c[8]), "+r"(c[9]), "+r"(c[10]), "+r"(c[11]), "+r"(c[12]), "+r"(c[13]), "+r"(c[14]), "+r"(c[15])
+                   "+r"(b[8]), "+r"(b[9]), "+r"(b[10]), "+r"(b[11]), "+r"(b[12]), "+r"(b[13]), "+r"(b[14]), "+r"(b[15])
                  :
                  : "memory");
 }
@@ -303,13 +307,12 @@ __device__ __forceinline__ void epilogue(const GroupDesc& G, const Params& P, ui
     const int row = 32 * q + lane;
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
     const int ntiles = G.ntiles;
-    uint32_t cols[NU][3];     // hi*hi, hi*lo and lo*hi of unit u
+    uint32_t cols[NU][2];     // hi*hi and the corrections (hi*lo + lo*hi) of unit u
 #pragma unroll
     for (int u = 0; u < NU; ++u) {
         const int t = G.unit_tile[u], cu = G.unit_c[u];
         cols[u][0] = (uint32_t)(G.dm_col[t] + cu);
         cols[u][1] = (uint32_t)(G.dm_col[t] + G.tile_w[t] + cu);
-        cols[u][2] = (uint32_t)(G.dl_col[t] + cu);
     }
     const uint32_t d_cols = (uint32_t)G.d_cols;
     int* const err = P.err;
@@ -331,15 +334,13 @@ __device__ __forceinline__ void epilogue(const GroupDesc& G, const Params& P, ui
 #pragma unroll
         for (int u = 0; u < NU; ++u)
             {
-                // the three pieces in flight together, one wait
-                uint32_t v0[16], v1[16], v2[16];
+                // both pieces in flight together, one wait
+                uint32_t v0[16], v1[16];
                 tmem_ld16(dbase + cols[u][0], v0);
                 tmem_ld16(dbase + cols[u][1], v1);
-                tmem_ld16(dbase + cols[u][2], v2);
-                tmem_wait_ld48(v0, v1, v2);
+                tmem_wait_ld32(v0, v1);
 #pragma unroll
-                for (int j = 0; j < 16; ++j)
-                    acc[u][j] += (__uint_as_float(v0[j]) + __uint_as_float(v1[j])) + __uint_as_float(v2[j]);
+                for (int j = 0; j < 16; ++j) acc[u][j] += __uint_as_float(v0[j]) + __uint_as_float(v1[j]);
             }
         tc_fence_before();
         mbar_arrive(&d_empty[db]);
@@ -371,13 +372,13 @@ __device__ __forceinline__ void producer(const GroupDesc& G, const Params& P, ui
                                          unsigned char* bst, uint64_t* slot_full, uint64_t* slot_empty,
                                          uint64_t* a_full, uint64_t* a_empty, volatile int* abort_flag, int nstages,
                                          int warp, int lane) {
-    const int gp = (warp - 1) >> 2;
+    const int gp = (warp - kProdWarp0) >> 2;
     const int q = warp & 3;
     const int row = 32 * q + lane;
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
     const int nA = G.nA, a_col0 = G.a_col0, slot_bytes = P.slot_bytes, bstage_bytes = G.bstage_bytes;
     const int s_off = P.s_off, s_chunks = P.s_chunks;
-    const int ptid = 32 * (warp - 1) + lane;   // 0 .. 255 over both groups
+    const int ptid = 32 * (warp - kProdWarp0) + lane;   // 0 .. 255 over both groups
     int* const err = P.err;
     int pj[NT], pk[NT];
 #pragma unroll
@@ -386,54 +387,80 @@ __device__ __forceinline__ void producer(const GroupDesc& G, const Params& P, ui
         pj[t] = jk.x;
         pk[t] = jk.y;
     }
+    // Rolling prefetch: the operands of the next tile (the next stage's first tile after the last one) are loaded
+    // before the current tile's products are formed, so shared-memory latency overlaps the arithmetic.  Padding rows
+    // (j < 0) read row 0 and store zeros.
+    float4 xc[4], yc[4], xn[4], yn[4];
+    uint4 bl[kBloItems];
+    auto load_tile = [&](const unsigned char* slot, int t, float4 (&x)[4], float4 (&y)[4]) {
+        const int j = max(pj[t], 0), k = max(pk[t], 0);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            x[c] = *ring_chunk(slot, j, 4 * gp + c);
+            y[c] = *ring_chunk(slot, k, 4 * gp + c);
+        }
+    };
+    auto load_blo = [&](const unsigned char* slot, uint4 (&b)[kBloItems]) {
+#pragma unroll
+        for (int m = 0; m < kBloItems; ++m)
+            if (ptid + 256 * m < s_chunks) b[m] = *reinterpret_cast<const uint4*>(slot + s_off + 16 * (ptid + 256 * m));
+    };
+    if (nstages <= 0) return;
+    if (!warp_wait(&slot_full[0], 0u, abort_flag, err)) return;
+    load_tile(ring, 0, xc, yc);
+    load_blo(ring, bl);
     for (int st = 0; st < nstages; ++st) {
         const int s = st % kRingSlots;
         const int as = st % nA;
-        bool ok = warp_wait(&slot_full[s], (uint32_t)((st / kRingSlots) & 1), abort_flag, err);
-        if (ok && st >= nA) ok = warp_wait(&a_empty[as], (uint32_t)((st / nA - 1) & 1), abort_flag, err);
-        if (!ok) break;
-        tc_fence_after();
         const unsigned char* slot = ring + (size_t)s * slot_bytes;
-        // B_lo chunks of this thread: loaded first, so that their latency hides behind the pair products
-        uint4 bl[kBloItems];
-#pragma unroll
-        for (int m = 0; m < kBloItems; ++m)
-            if (ptid + 256 * m < s_chunks)
-                bl[m] = *reinterpret_cast<const uint4*>(slot + s_off + 16 * (ptid + 256 * m));
-        uint32_t v[NT][32];
+        bool ok = true;
 #pragma unroll
         for (int t = 0; t < NT; ++t) {
-            if (pj[t] >= 0) {
-                float4 x[4], y[4];
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    x[c] = *ring_chunk(slot, pj[t], 4 * gp + c);
-                    y[c] = *ring_chunk(slot, pk[t], 4 * gp + c);
-                }
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    uint64_t h0, l0, h1, l1;
-                    split_x2(mul_x2(f2pack(x[c].x, x[c].y), f2pack(y[c].x, y[c].y)), h0, l0);
-                    split_x2(mul_x2(f2pack(x[c].z, x[c].w), f2pack(y[c].z, y[c].w)), h1, l1);
-                    v[t][4 * c + 0] = (uint32_t)h0;
-                    v[t][4 * c + 1] = (uint32_t)(h0 >> 32);
-                    v[t][4 * c + 2] = (uint32_t)h1;
-                    v[t][4 * c + 3] = (uint32_t)(h1 >> 32);
-                    v[t][16 + 4 * c + 0] = (uint32_t)l0;
-                    v[t][16 + 4 * c + 1] = (uint32_t)(l0 >> 32);
-                    v[t][16 + 4 * c + 2] = (uint32_t)l1;
-                    v[t][16 + 4 * c + 3] = (uint32_t)(l1 >> 32);
-                }
-            } else {
-#pragma unroll
-                for (int c = 0; c < 32; ++c) v[t][c] = 0u;
+            // (no break inside this unrolled loop: a failed wait clears ok, the rest of the stage is skipped)
+            if (t + 1 < NT) {
+                load_tile(slot, t + 1, xn, yn);
+            } else if (st + 1 < nstages) {
+                const int s1 = (st + 1) % kRingSlots;
+                ok = ok && warp_wait(&slot_full[s1], (uint32_t)(((st + 1) / kRingSlots) & 1), abort_flag, err);
+                if (ok) load_tile(ring + (size_t)s1 * slot_bytes, 0, xn, yn);
             }
-            tmem_st32(tmem + lane_base + (uint32_t)(a_col0 + as * 64 * NT + 64 * t + 32 * gp), v[t]);
+            if (t == 0) {
+                // tensor memory A stage and B_lo stage `as` are free once the MMAs of stage st - nA completed
+                if (st >= nA) ok = ok && warp_wait(&a_empty[as], (uint32_t)((st / nA - 1) & 1), abort_flag, err);
+                tc_fence_after();
+            }
+            if (!ok) continue;
+            uint32_t v[32];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                uint64_t h0, l0, h1, l1;
+                split_x2(mul_x2(f2pack(xc[c].x, xc[c].y), f2pack(yc[c].x, yc[c].y)), h0, l0);
+                split_x2(mul_x2(f2pack(xc[c].z, xc[c].w), f2pack(yc[c].z, yc[c].w)), h1, l1);
+                v[4 * c + 0] = (uint32_t)h0;
+                v[4 * c + 1] = (uint32_t)(h0 >> 32);
+                v[4 * c + 2] = (uint32_t)h1;
+                v[4 * c + 3] = (uint32_t)(h1 >> 32);
+                v[16 + 4 * c + 0] = (uint32_t)l0;
+                v[16 + 4 * c + 1] = (uint32_t)(l0 >> 32);
+                v[16 + 4 * c + 2] = (uint32_t)l1;
+                v[16 + 4 * c + 3] = (uint32_t)(l1 >> 32);
+            }
+            if (pj[t] < 0) {
+#pragma unroll
+                for (int c = 0; c < 32; ++c) v[c] = 0u;
+            }
+            tmem_st32(tmem + lane_base + (uint32_t)(a_col0 + as * 64 * NT + 64 * t + 32 * gp), v);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                xc[c] = xn[c];
+                yc[c] = yn[c];
+            }
         }
+        if (!ok) break;
         // B_lo = (g - trunc(g)) rounded to TF32 (nearest, ties away), at the same byte offset as g (same swizzle)
         unsigned char* bs = bst + (size_t)as * bstage_bytes;
 #pragma unroll
-        for (int m = 0; m < kBloItems; ++m)
+        for (int m = 0; m < kBloItems; ++m) {
             if (ptid + 256 * m < s_chunks) {
                 uint32_t* w = reinterpret_cast<uint32_t*>(&bl[m]);
                 const uint64_t g01 = (uint64_t)w[0] | ((uint64_t)w[1] << 32);
@@ -444,6 +471,9 @@ __device__ __forceinline__ void producer(const GroupDesc& G, const Params& P, ui
                     make_uint4(((uint32_t)l01 + 0x1000u) & 0xFFFFE000u, ((uint32_t)(l01 >> 32) + 0x1000u) & 0xFFFFE000u,
                                ((uint32_t)l23 + 0x1000u) & 0xFFFFE000u, ((uint32_t)(l23 >> 32) + 0x1000u) & 0xFFFFE000u);
             }
+        }
+        // the next stage's B_lo chunks (its slot is already full: waited for the first tile's prefetch)
+        if (st + 1 < nstages) load_blo(ring + (size_t)((st + 1) % kRingSlots) * slot_bytes, bl);
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // B_lo stores -> tensor core
         tc_fence_before();
@@ -468,8 +498,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t* a_empty = a_full + kMaxAStages;          // [kMaxAStages] MMA commit -> producers
     uint64_t* d_full = a_empty + kMaxAStages;          // [2][kMaxTiles] MMA commit -> epilogue (D buffer, tile)
     uint64_t* d_empty = d_full + 2 * kMaxTiles;        // [2]            epilogue -> issuers (D buffer)
-    uint64_t* fin = d_empty + 2;                       // [kIssWarps]
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + kIssWarps);
+    uint64_t* fin = d_empty + 2;                       // [kMaxTiles]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + kMaxTiles);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -494,7 +524,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         for (int i = 0; i < 2 * kMaxTiles; ++i) mbar_init(&d_full[i], 1);
         for (int i = 0; i < 2; ++i) mbar_init(&d_empty[i], 32 * kEpiWarps);
-        for (int i = 0; i < kIssWarps; ++i) mbar_init(&fin[i], 1);
+        for (int i = 0; i < kMaxTiles; ++i) mbar_init(&fin[i], 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -507,52 +537,45 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    if (warp == 0) {
-        // ------------------------------------------------------------------ TMA producer
-        if (lane == 0 && nslots > 0) {
-            const uint32_t bytes = (uint32_t)(P.ng * 128 + (P.hsep ? P.nh * 128 : 0));
-            const bool hsep = P.hsep != 0;
-            const int hoff = P.h_row0 * 128;
-            int issued = 0;
-            for (int sl = 0; sl < nslots; ++sl) {
-                const int s = sl % kRingSlots;
-                if (sl >= kRingSlots &&
-                    !thread_wait(&slot_empty[s], (uint32_t)((sl / kRingSlots - 1) & 1), abort_flag, err))
-                    break;
-                unsigned char* dst = ring + (size_t)s * slot_bytes;
-                const int x = (int)(c0 + (long)sl * kSlotCells);
-                mbar_expect_tx(&slot_full[s], bytes);
-                tma_load_2d(dst, &tmap_g, x, 0, &slot_full[s]);
-                if (hsep) tma_load_2d(dst + hoff, &tmap_h, x, 0, &slot_full[s]);
-                ++issued;
+    if (warp < kProdWarp0) {
+        // warpgroup 0 hands registers to the producers (all four warps, one instruction)
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegsCtl));
+        if (warp == 0) {
+            // ------------------------------------------------------------------ TMA producer
+            if (lane == 0 && nslots > 0) {
+                const uint32_t bytes = (uint32_t)(P.ng * 128 + (P.hsep ? P.nh * 128 : 0));
+                const bool hsep = P.hsep != 0;
+                const int hoff = P.h_row0 * 128;
+                int issued = 0;
+                for (int sl = 0; sl < nslots; ++sl) {
+                    const int s = sl % kRingSlots;
+                    if (sl >= kRingSlots &&
+                        !thread_wait(&slot_empty[s], (uint32_t)((sl / kRingSlots - 1) & 1), abort_flag, err))
+                        break;
+                    unsigned char* dst = ring + (size_t)s * slot_bytes;
+                    const int x = (int)(c0 + (long)sl * kSlotCells);
+                    mbar_expect_tx(&slot_full[s], bytes);
+                    tma_load_2d(dst, &tmap_g, x, 0, &slot_full[s]);
+                    if (hsep) tma_load_2d(dst + hoff, &tmap_h, x, 0, &slot_full[s]);
+                    ++issued;
+                }
+                // every load issued has landed before the CTA may exit
+                for (int sl = max(0, issued - kRingSlots); sl < issued; ++sl)
+                    drain_wait(&slot_full[sl % kRingSlots], (uint32_t)((sl / kRingSlots) & 1), err);
             }
-            // every load issued has landed before the CTA may exit
-            for (int sl = max(0, issued - kRingSlots); sl < issued; ++sl)
-                drain_wait(&slot_full[sl % kRingSlots], (uint32_t)((sl / kRingSlots) & 1), err);
-        }
-        __syncwarp();
-    } else if (warp <= kProdWarps) {
-        // ------------------------------------------------------------------ producers
-        switch (ntiles) {
-            case 1: producer<1>(G, P, tmem, ring, bst, slot_full, slot_empty, a_full, a_empty, abort_flag, nstages, warp, lane); break;
-            case 2: producer<2>(G, P, tmem, ring, bst, slot_full, slot_empty, a_full, a_empty, abort_flag, nstages, warp, lane); break;
-            default: producer<3>(G, P, tmem, ring, bst, slot_full, slot_empty, a_full, a_empty, abort_flag, nstages, warp, lane); break;
-        }
-    } else if (warp <= kProdWarps + kIssWarps) {
-        // ------------------------------------------------------------------ MMA issue
-        // The whole warp runs the loop (converged; every lane polls the barriers); the elected lane issues and
-        // commits inside mma_tf32 / mma_commit.
-        const int t = warp - 1 - kProdWarps;
-        if (t < ntiles) {
+            __syncwarp();
+        } else if (warp - 1 < ntiles) {
+            // ------------------------------------------------------------------ MMA issue (warp 1 + t: tile t)
+            // The whole warp runs the loop (converged; every lane polls the barriers); the elected lane issues and
+            // commits inside mma_tf32 / mma_commit.
+            // tile t's window of singles: rows s0 .. s0 + W - 1 of a slot's singles region (B_hi: the slot itself, read
+            // as TF32, i.e. truncated) and of the B_lo stage (same layout)
+            const uint32_t ring_s = smem_u32(ring) + (uint32_t)P.s_off, bst_s = smem_u32(bst);
+            const uint32_t d_cols = (uint32_t)G.d_cols;
+            const int t = warp - 1;
             const int W = G.tile_w[t];
             const uint32_t idesc_w = idesc_tf32(128, W);
-            const uint32_t dm = (uint32_t)G.dm_col[t], dl = (uint32_t)G.dl_col[t];
-            const uint32_t d_cols = (uint32_t)G.d_cols;
-            const uint32_t aoff = (uint32_t)(64 * t);
-            // tile t's window of singles: rows s0 .. s0 + W - 1 of a slot's singles region (B_hi: the slot itself,
-            // read as TF32, i.e. truncated) and of the B_lo stage (same layout)
-            const uint32_t bh0 = smem_u32(ring + P.s_off + 128 * G.tile_s0[t]);
-            const uint32_t bl0 = smem_u32(bst + 128 * G.tile_s0[t]);
+            const uint32_t bh0 = ring_s + (uint32_t)(128 * G.tile_s0[t]), bl0 = bst_s + (uint32_t)(128 * G.tile_s0[t]);
             for (int st = 0; st < nstages; ++st) {
                 const int s = st % kRingSlots;
                 const int as = st % nA;
@@ -564,8 +587,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (!warp_wait(&slot_full[s], (uint32_t)((st / kRingSlots) & 1), abort_flag, err)) break;
                 if (!warp_wait(&a_full[as], (uint32_t)((st / nA) & 1), abort_flag, err)) break;
                 tc_fence_after();
-                const uint32_t aa = tmem + (uint32_t)(a_col0 + as * 64 * ntiles) + aoff;
-                const uint32_t dbuf = tmem + (uint32_t)db * d_cols;
+                const uint32_t dm = tmem + (uint32_t)db * d_cols + (uint32_t)G.dm_col[t], dc = dm + (uint32_t)W;
+                const uint32_t aa = tmem + (uint32_t)(a_col0 + as * 64 * ntiles + 64 * t);
                 const uint64_t bh = sdesc_sw128(bh0 + (uint32_t)(s * slot_bytes));
                 const uint64_t bl = sdesc_sw128(bl0 + (uint32_t)(as * bstage_bytes));
 #pragma unroll
@@ -575,9 +598,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                     // cannot carry out: the shared-memory window is 2^18 bytes)
                     const uint32_t ah = aa + 32u * (ks >> 1) + 8u * (ks & 1);
                     const uint32_t acc = (pstart && ks == 0) ? 0u : 1u;
-                    mma_tf32(dbuf + dm, ah, bh + (uint64_t)(2 * ks), idesc_w, acc);                 // A_hi . B_hi
-                    mma_tf32(dbuf + dm + (uint32_t)W, ah, bl + (uint64_t)(2 * ks), idesc_w, acc);   // A_hi . B_lo
-                    mma_tf32(dbuf + dl, ah + 16u, bh + (uint64_t)(2 * ks), idesc_w, acc);           // A_lo . B_hi
+                    mma_tf32(dm, ah, bh + (uint64_t)(2 * ks), idesc_w, acc);          // A_hi . B_hi
+                    mma_tf32(dc, ah, bl + (uint64_t)(2 * ks), idesc_w, acc);          // A_hi . B_lo
+                    mma_tf32(dc, ah + 16u, bh + (uint64_t)(2 * ks), idesc_w, 1u);     // + A_lo . B_hi
                 }
                 mma_commit(&a_empty[as]);
                 mma_commit(&slot_empty[s]);
@@ -587,6 +610,14 @@ __global__ void __launch_bounds__(kThreads, 1)
             mma_commit(&fin[t]);
             drain_wait(&fin[t], 0, err);
             __syncwarp();
+        }
+    } else if (warp < kProdWarp0 + kProdWarps) {
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kRegsProd));
+        // ------------------------------------------------------------------ producers
+        switch (ntiles) {
+            case 1: producer<1>(G, P, tmem, ring, bst, slot_full, slot_empty, a_full, a_empty, abort_flag, nstages, warp, lane); break;
+            case 2: producer<2>(G, P, tmem, ring, bst, slot_full, slot_empty, a_full, a_empty, abort_flag, nstages, warp, lane); break;
+            default: producer<3>(G, P, tmem, ring, bst, slot_full, slot_empty, a_full, a_empty, abort_flag, nstages, warp, lane); break;
         }
     } else {
         // ------------------------------------------------------------------ epilogue
@@ -706,7 +737,7 @@ static const char* layout_plan(Plan& pl, long ncell, int nsm, int ng, int nh, in
     for (int t = 0; t < (int)tiles.size();) {
         int e = t, dcols = 0, units = 0;
         while (e < (int)tiles.size() && e - t < kMaxTiles) {
-            const int nd = dcols + 3 * tiles[e].W, nu = units + tiles[e].W / 16, nt = e - t + 1;
+            const int nd = dcols + 2 * tiles[e].W, nu = units + tiles[e].W / 16, nt = e - t + 1;
             if (nu > kMaxUnits || kDBuf * ((nd + 31) / 32 * 32) + 2 * 2 * kKC * nt > 512) break;
             dcols = nd; units = nu; ++e;
         }
@@ -736,14 +767,14 @@ static const char* layout_plan(Plan& pl, long ncell, int nsm, int ng, int nh, in
         D = GroupDesc{};
         const int t0 = groups[gi].first, nt = groups[gi].second - t0;
         D.tile0 = t0; D.ntiles = nt; D.unit_base = unit_base;
-        // accumulators: hi*[hi | lo] (2W) and lo*hi (W) of every tile, largest first, so each is aligned to its size
-        std::vector<std::tuple<int, int, int>> dl;   // (size, tile, which)
-        for (int t = 0; t < nt; ++t) { dl.push_back({2 * tiles[t0 + t].W, t, 0}); dl.push_back({tiles[t0 + t].W, t, 1}); }
-        std::stable_sort(dl.begin(), dl.end(), [](auto& a, auto& b) { return std::get<0>(a) > std::get<0>(b); });
+        // accumulators: [hi*hi | corrections] (2W) of every tile, largest first, so each is aligned to its size
+        std::vector<std::pair<int, int>> dl;   // (size, tile)
+        for (int t = 0; t < nt; ++t) dl.push_back({2 * tiles[t0 + t].W, t});
+        std::stable_sort(dl.begin(), dl.end(), [](auto& a, auto& b) { return a.first > b.first; });
         int col = 0;
         for (auto& x : dl) {
-            if (std::get<2>(x) == 0) D.dm_col[std::get<1>(x)] = col; else D.dl_col[std::get<1>(x)] = col;
-            col += std::get<0>(x);
+            D.dm_col[x.second] = col;
+            col += x.first;
         }
         D.d_cols = (col + 31) / 32 * 32;
         D.a_col0 = kDBuf * D.d_cols;
@@ -871,6 +902,16 @@ static int launch(polybin_ctx* ctx, Plan& pl, const float* g, const float* h, do
     if (e != cudaSuccess) return fail_cuda(ctx, e, "cudaMemsetAsync", __FILE__, __LINE__);
     e = cudaFuncSetAttribute((const void*)k_contract_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
     if (e != cudaSuccess) return fail_cuda(ctx, e, "cudaFuncSetAttribute(k_contract_tc)", __FILE__, __LINE__);
+    {
+        // the setmaxnreg split assumes exactly kRegsLaunch registers a thread at launch (a smaller allocation would
+        // leave the producers' increase waiting for registers that do not exist)
+        cudaFuncAttributes fa{};
+        e = cudaFuncGetAttributes(&fa, (const void*)k_contract_tc);
+        if (e != cudaSuccess) return fail_cuda(ctx, e, "cudaFuncGetAttributes(k_contract_tc)", __FILE__, __LINE__);
+        if (fa.numRegs != kRegsLaunch)
+            return fail(ctx, POLYBIN_ECUDA, "contract_tc: kernel built with %d registers a thread, %d expected", fa.numRegs,
+                        kRegsLaunch);
+    }
     Params P = pl.base;
     P.err = ctx->d_err;
     {
