@@ -7,30 +7,34 @@
 // the triplet a <= b <= c is read from pair (b, c) and single a, which prunes the 465 pairs x 30 singles of a
 // 30-bin binning to 255 pairs in two tiles with windows of 16 and 32 singles.
 //
-// Arithmetic: every value v is split as v = hi + lo, hi = v rounded to TF32 (nearest, ties away from zero),
-// lo = v - hi in FP32 (read by the MMA as TF32).  Per tile and K = 8 cells two MMAs run, on independent
-// accumulators:  D_m[:, 0:2W] += A_hi . [B_hi | B_lo]^T  (N = 2W: hi*hi in columns < W, hi*lo in columns >= W) and
-// D_l[:, 0:W] += A_lo . B_hi^T  (N = W); the lo*lo term (~2^-22 relative) is dropped.  A = pair products (g_j g_k in
-// FP32, then split), B = singles.  The tensor core's internal accumulation is not round-to-nearest, so D restarts
-// every 64 cells (8 MMAs per accumulator column); the epilogue adds D into FP32 registers (round-to-nearest) and
-// those into FP64 shared memory every 2048 cells.  Cross-CTA sums are FP64 in a fixed order (deterministic).
+// Arithmetic: A = pair products g_j g_k (FP32), split as A = A_hi + A_lo with A_hi = A rounded to TF32 (nearest,
+// ties away from zero) and A_lo = A - A_hi in FP32 (read by the MMA as TF32).  B = singles: the tensor core reads an
+// FP32 operand as TF32 by truncation (measured: the 13 low bits are dropped toward zero), so the raw maps in the TMA
+// ring serve as B_hi = trunc(g) directly, and B_lo = g - trunc(g), rounded to TF32, is made per stage.  Per tile
+// and K = 8 cells three MMAs of N = W run:  D[:, 0:W] += A_hi . B_hi^T  and  D[:, W:2W] += A_hi . B_lo^T +
+// A_lo . B_hi^T  (both corrections in one accumulator); the lo*lo term (~2^-21 relative, unbiased) is dropped.  The
+// tensor core's internal accumulation is not round-to-nearest, so D restarts every 64 cells (8 MMAs per hi*hi
+// column); the epilogue adds D into FP32 registers (round-to-nearest) and those into FP64 shared memory every 2048
+// cells.  Cross-CTA sums are FP64 in a fixed order (deterministic).
 //
-// Measured on this part (and shaping the design): one thread issues a tcgen05.mma per ~50-120 cycles whatever its
-// size; consecutive MMAs into the same accumulator columns complete ~150 cycles apart, so independent accumulators
-// and wide N per instruction matter more than the tensor core's peak rate; tensor memory (512 columns) is shared by
-// the accumulators (one buffer, D_m + D_l = 3W columns a tile) and the ring of A stages (64 columns a tile a stage).
+// Measured on this part (and shaping the design): an MMA issued from warp-uniform code with its operands in uniform
+// registers costs ~16-20 cycles at N = 32 (the tensor pipe's rate), but ~200 cycles from a one-lane branch, so the
+// issuing loops are warp-uniform (elect.sync inside the asm) and divide-free; MMAs into one accumulator back to back
+// run at full rate; tensor memory stores reach ~650 B/clk an SM; the producers' shared-memory gathers (~500
+// wavefronts a stage) and their latency set the stage time.  Tensor memory (512 columns) holds the accumulator
+// (2W columns a tile) and a ring of A stages (64 columns a tile a stage).
 //
-// One CTA per SM over a contiguous range of cells, in stages of 32 cells (one TMA ring slot); warp roles:
+// One CTA per SM over a contiguous range of cells, in stages of 32 cells (one TMA ring slot).  Warp roles, by
+// warpgroup (setmaxnreg moves registers from warpgroup 0 to the producers):
 //   warp 0       TMEM allocation; lane 0 streams the maps with TMA (cp.async.bulk.tensor, 32 cells x all maps per
 //                load, 128-byte swizzle) into an 8-slot shared-memory ring.
-//   warps 1-8    producers, two groups of four warps; group g makes cells 16g..16g+15 of every stage, so the two
-//                groups overlap each other's load and store latencies.  A thread owns one TMEM lane, i.e. one row
-//                of every tile: it forms the pair products, splits them (packed FP32 pairs) and writes hi / lo
-//                straight into tensor memory (tcgen05.st: the A operand never touches shared memory), and converts
-//                its share of every tile's window of singles into the hi / lo B operand (canonical no-swizzle
-//                K-major layout) in shared memory.
-//   warps 9-11   MMA issue: warp 9 + t waits for the stage (all lanes, converged) and its lane 0 issues tile t's
-//                MMAs and commits them to the stage's release barrier.
+//   warps 1-3    MMA issue: warp 1 + t waits for the stage (converged) and issues tile t's MMAs, commits them to the
+//                stage's release barriers (A stage, ring slot) and, at a period's end, to the accumulator barrier.
+//   warps 4-11   producers, two groups of four warps; group g makes cells 16g..16g+15 of every stage.  A thread owns
+//                one TMEM lane, i.e. one row of every tile: it forms the pair products, splits them (packed FP32
+//                pairs) and writes hi / lo straight into tensor memory (tcgen05.st: the A operand never touches
+//                shared memory), loading the next tile's operands before forming the current tile's products; each
+//                thread also makes one 16-byte chunk of the stage's B_lo.
 //   warps 12-15  epilogue: after every period read D with tcgen05.ld (each warp its TMEM lane quarter), release
 //                it to the issuers, accumulate.
 #include <cuda.h>
@@ -54,6 +58,7 @@ constexpr int kMaxAStages = 6;
 constexpr int kPeriod = 2;         // A stages per TMEM accumulation period (64 cells)
 constexpr int kSpill = 32;         // periods per FP32 register sum (2048 cells)
 constexpr int kDBuf = 1;           // accumulator buffers (1: the issuers wait for the epilogue between periods)
+static_assert(kDBuf == 1, "the MMA issue loop assumes one accumulator buffer");
 constexpr int kMaxTiles = 3;       // tiles per CTA
 constexpr int kMaxUnits = 3;       // 16-column output units per CTA (16 FP32 sums each, in registers)
 constexpr int kMaxGroups = 4;      // row groups (grid.y)
@@ -343,7 +348,8 @@ __device__ __forceinline__ void epilogue(const GroupDesc& G, const Params& P, ui
                 for (int j = 0; j < 16; ++j) acc[u][j] += __uint_as_float(v0[j]) + __uint_as_float(v1[j]);
             }
         tc_fence_before();
-        mbar_arrive(&d_empty[db]);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&d_empty[db]);   // one arrival a warp (the warp's loads are done)
         if ((per + 1) % kSpill == 0) {
 #pragma unroll
             for (int u = 0; u < NU; ++u)
@@ -477,8 +483,13 @@ __device__ __forceinline__ void producer(const GroupDesc& G, const Params& P, ui
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // B_lo stores -> tensor core
         tc_fence_before();
-        mbar_arrive(&a_full[as]);
-        mbar_arrive(&slot_empty[s]);
+        // one arrival a warp on each barrier: __syncwarp orders the other lanes' stores and reads before lane 0's
+        // release (256 single-thread arrivals were 512 shared-memory atomics on two words every stage)
+        __syncwarp();
+        if (lane == 0) {
+            mbar_arrive(&a_full[as]);
+            mbar_arrive(&slot_empty[s]);
+        }
     }
 }
 
@@ -516,14 +527,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (tid == 0) {
         for (int s = 0; s < kRingSlots; ++s) {
             mbar_init(&slot_full[s], 1);
-            mbar_init(&slot_empty[s], 32 * kProdWarps + ntiles);   // producers read a slot, the MMAs read B_hi
+            mbar_init(&slot_empty[s], kProdWarps + ntiles);   // producer warps read a slot, the MMAs read B_hi
         }
         for (int s = 0; s < kMaxAStages; ++s) {
-            mbar_init(&a_full[s], 32 * kProdWarps);   // both producer groups make a stage (A and B_lo)
+            mbar_init(&a_full[s], kProdWarps);   // both producer groups make a stage (A and B_lo), one arrival a warp
             mbar_init(&a_empty[s], ntiles);        // one commit per issuing thread (tile)
         }
         for (int i = 0; i < 2 * kMaxTiles; ++i) mbar_init(&d_full[i], 1);
-        for (int i = 0; i < 2; ++i) mbar_init(&d_empty[i], 32 * kEpiWarps);
+        for (int i = 0; i < 2; ++i) mbar_init(&d_empty[i], kEpiWarps);
         for (int i = 0; i < kMaxTiles; ++i) mbar_init(&fin[i], 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -571,31 +582,38 @@ __global__ void __launch_bounds__(kThreads, 1)
             // tile t's window of singles: rows s0 .. s0 + W - 1 of a slot's singles region (B_hi: the slot itself, read
             // as TF32, i.e. truncated) and of the B_lo stage (same layout)
             const uint32_t ring_s = smem_u32(ring) + (uint32_t)P.s_off, bst_s = smem_u32(bst);
-            const uint32_t d_cols = (uint32_t)G.d_cols;
             const int t = warp - 1;
             const int W = G.tile_w[t];
             const uint32_t idesc_w = idesc_tf32(128, W);
-            const uint32_t bh0 = ring_s + (uint32_t)(128 * G.tile_s0[t]), bl0 = bst_s + (uint32_t)(128 * G.tile_s0[t]);
-            for (int st = 0; st < nstages; ++st) {
-                const int s = st % kRingSlots;
-                const int as = st % nA;
-                const int per = st / kPeriod, db = per % kDBuf;
-                const bool pstart = (st % kPeriod) == 0;
-                if (pstart && per >= kDBuf &&
-                    !warp_wait(&d_empty[db], (uint32_t)((per / kDBuf - 1) & 1), abort_flag, err))
-                    break;
-                if (!warp_wait(&slot_full[s], (uint32_t)((st / kRingSlots) & 1), abort_flag, err)) break;
-                if (!warp_wait(&a_full[as], (uint32_t)((st / nA) & 1), abort_flag, err)) break;
+            // Every operand below is built from warp-uniform values (parameters, constants, loop-carried counters;
+            // no division) so that the compiler keeps it in uniform registers: the tensor memory base is the
+            // constant 0, which is what a CTA allocating all 512 columns receives (lane 0, column 0).
+            const bool tmem_ok = tmem == 0u;
+            if (!tmem_ok && lane == 0) {
+                *abort_flag = 1;
+                atomicExch(err, 1);
+            }
+            const uint32_t dm = (uint32_t)G.dm_col[t], dc = dm + (uint32_t)W;
+            const uint32_t a_first = (uint32_t)(a_col0 + 64 * t), a_step = (uint32_t)(64 * ntiles);
+            const uint64_t bh_first = sdesc_sw128(ring_s + (uint32_t)(128 * G.tile_s0[t]));
+            const uint64_t bl_first = sdesc_sw128(bst_s + (uint32_t)(128 * G.tile_s0[t]));
+            // descriptor address steps (16-byte units; no carry out of the 14-bit field: shared memory < 2^18 bytes)
+            const uint64_t bh_step = (uint64_t)(slot_bytes >> 4), bl_step = (uint64_t)(bstage_bytes >> 4);
+            int s = 0, as = 0, pos = 0, per = 0;
+            uint32_t sph = 0, aph = 0;
+            uint32_t aa = a_first;
+            uint64_t bh = bh_first, bl = bl_first;
+            for (int st = 0; st < nstages && tmem_ok; ++st) {
+                const bool pstart = pos == 0;
+                // one accumulator buffer: a period's first MMAs wait until the epilogue has read the previous one
+                if (pstart && per >= 1 && !warp_wait(&d_empty[0], (uint32_t)((per - 1) & 1), abort_flag, err)) break;
+                if (!warp_wait(&slot_full[s], sph, abort_flag, err)) break;
+                if (!warp_wait(&a_full[as], aph, abort_flag, err)) break;
                 tc_fence_after();
-                const uint32_t dm = tmem + (uint32_t)db * d_cols + (uint32_t)G.dm_col[t], dc = dm + (uint32_t)W;
-                const uint32_t aa = tmem + (uint32_t)(a_col0 + as * 64 * ntiles + 64 * t);
-                const uint64_t bh = sdesc_sw128(bh0 + (uint32_t)(s * slot_bytes));
-                const uint64_t bl = sdesc_sw128(bl0 + (uint32_t)(as * bstage_bytes));
 #pragma unroll
                 for (int ks = 0; ks < kKC / 8; ++ks) {
                     // K step ks: cells 8 ks .. 8 ks + 7; A_hi at half (ks / 2), column 8 (ks % 2); A_lo at +16.  B
-                    // advances 32 bytes a step within the swizzle atom (2 in the descriptor's address field, which
-                    // cannot carry out: the shared-memory window is 2^18 bytes)
+                    // advances 32 bytes a step within the swizzle atom (2 in the descriptor's address field)
                     const uint32_t ah = aa + 32u * (ks >> 1) + 8u * (ks & 1);
                     const uint32_t acc = (pstart && ks == 0) ? 0u : 1u;
                     mma_tf32(dm, ah, bh + (uint64_t)(2 * ks), idesc_w, acc);          // A_hi . B_hi
@@ -604,7 +622,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 mma_commit(&a_empty[as]);
                 mma_commit(&slot_empty[s]);
-                if ((st % kPeriod) == kPeriod - 1 || st == nstages - 1) mma_commit(&d_full[db * kMaxTiles + t]);
+                if (pos == kPeriod - 1 || st == nstages - 1) mma_commit(&d_full[t]);
+                if (++s == kRingSlots) { s = 0; sph ^= 1u; bh = bh_first; } else { bh += bh_step; }
+                if (++as == nA) { as = 0; aph ^= 1u; aa = a_first; bl = bl_first; } else { aa += a_step; bl += bl_step; }
+                if (++pos == kPeriod) { pos = 0; ++per; }
             }
             // every MMA issued by the elected thread has completed before TMEM is released
             mma_commit(&fin[t]);
