@@ -7,6 +7,8 @@
 // A line of length n lives in shared memory as element (l, e) at l + e * ES, so that consecutive
 // threads touch consecutive lines (conflict-free) in every radix pass.
 #pragma once
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace pb {
@@ -336,44 +338,49 @@ __global__ void __launch_bounds__(256) k_inv_z(ZInvBatch batch, long nlines, T s
 // threads transforms one packed line pair: thread t holds the eight points Z[t + 64 j]; stage 1 takes the 8-point
 // DFT over j and multiplies by w512^(t k1); stage 2 (after an exchange through shared memory) the DFT over
 // t2 = t / 8 and multiplies by w64^(t1 m1); stage 3 the DFT over t1 = t % 8, which leaves X[k1 + 8 m1 + 64 m2] in
-// the thread; a last exchange through shared memory makes the 2 x 512 real outputs coalesced.  Twiddles are
-// read once per thread from the table tw[m] = e^{-2 pi i m / 512}.  Four groups per CTA, each synchronised by its
-// own named barrier; a CTA takes `lpc` line pairs of one item (blockIdx.y).
+// the thread; a last exchange through shared memory makes the 2 x 512 real outputs coalesced (16-byte stores).
+// Twiddles are read once per thread from the table tw[m] = e^{-2 pi i m / 512} and kept in registers (measured:
+// a shared-memory table costs more in bank conflicts than the registers it frees; prefetching the next pair's
+// input costs more in occupancy than it hides).  Four groups per CTA, each synchronised by its own named barrier;
+// a CTA takes `lpc` line pairs of one item (blockIdx.y).
+// (immediate barrier ids, so that the kernel reserves 5 hardware barriers rather than all 16, which would cap the
+// CTAs an SM can hold)
 __device__ __forceinline__ void group_sync(int gid) {
-    asm volatile("bar.sync %0, 64;" ::"r"(gid + 1) : "memory");
+    switch (gid) {
+        case 0: asm volatile("bar.sync 1, 64;" ::: "memory"); break;
+        case 1: asm volatile("bar.sync 2, 64;" ::: "memory"); break;
+        case 2: asm volatile("bar.sync 3, 64;" ::: "memory"); break;
+        default: asm volatile("bar.sync 4, 64;" ::: "memory"); break;
+    }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_inv_z512(ZInvBatch batch, long nlines, T scale, const T* __restrict__ mulout,
                                                  const C<T>* __restrict__ twg, int lpc) {
     constexpr int N = 512, PAD = 9;                     // exchange rows of 8 complex values padded to 9
-    __shared__ C<T> sbuf[4][64 * PAD];
+    constexpr int V = 16 / (int)sizeof(T);              // outputs per 16-byte vector store
+    using VT = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+    __shared__ __align__(16) C<T> sbuf[4][64 * PAD];
     const ZInvItem item = batch.it[blockIdx.y];
     const C<T>* __restrict__ in = static_cast<const C<T>*>(item.in);
     T* __restrict__ out = static_cast<T*>(item.out);
     const int kin = item.kin;
     const int gid = threadIdx.x >> 6, t = threadIdx.x & 63;
     C<T>* buf = sbuf[gid];
-    // per-thread twiddles (inverse transform: conjugates of the table)
-    C<T> w1[8], w2[8];
     const int t1 = t & 7, k1s2 = t >> 3;                // stage-2 / stage-3 roles of this thread
+    C<T> w1[8], w2[8];
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
-        const C<T> a = twg[(t * r) & (N - 1)];
-        const C<T> b = twg[(8 * t1 * r) & (N - 1)];
-        w1[r] = mk<T>(a.x, -a.y);
-        w2[r] = mk<T>(b.x, -b.y);
+        w1[r] = twg[(t * r) & (N - 1)];
+        w2[r] = twg[(8 * t1 * r) & (N - 1)];
     }
     const long npairs = (nlines + 1) / 2;
-    for (int q = gid; q < lpc; q += 4) {
-        const long p = (long)blockIdx.x * lpc + q;
-        if (p >= npairs) break;                          // uniform within the group
+    // stage-1 input of line pair p: Z[t + 64 j] of the packed Hermitian pair (zero beyond the kept wave numbers)
+    auto load_pair = [&](long p, C<T> (&v)[8]) {
         const long l1 = 2 * p, l2 = 2 * p + 1;
         const C<T>* in1 = in + l1 * kin;
         const C<T>* in2 = in + l2 * kin;
         const bool has2 = l2 < nlines;
-        // stage 1: load Z[t + 64 j] (packed Hermitian pair), DFT over j, twiddle w512^(t k1)
-        C<T> v[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int k = t + 64 * j;
@@ -391,9 +398,19 @@ __global__ void __launch_bounds__(256) k_inv_z512(ZInvBatch batch, long nlines, 
             }
             v[j] = z;
         }
+    };
+    // the next pair's input is loaded before the current pair is transformed (global latency under the FFT)
+    for (int q = gid; q < lpc; q += 4) {
+        const long p = (long)blockIdx.x * lpc + q;
+        if (p >= npairs) break;                          // uniform within the group
+        const long l1 = 2 * p, l2 = 2 * p + 1;
+        const bool has2 = l2 < nlines;
+        C<T> v[8];
+        load_pair(p, v);
+        // stage 1: DFT over j, twiddle w512^(t k1) (inverse: conjugated table)
         dft<T, +1>(v, 8);
 #pragma unroll
-        for (int r = 1; r < 8; ++r) v[r] = mul<T>(v[r], w1[r]);
+        for (int r = 1; r < 8; ++r) v[r] = mulc<T>(v[r], w1[r]);
 #pragma unroll
         for (int r = 0; r < 8; ++r) buf[t * PAD + r] = v[r];
         group_sync(gid);
@@ -402,7 +419,7 @@ __global__ void __launch_bounds__(256) k_inv_z512(ZInvBatch batch, long nlines, 
         for (int r = 0; r < 8; ++r) v[r] = buf[(t1 + 8 * r) * PAD + k1s2];
         dft<T, +1>(v, 8);
 #pragma unroll
-        for (int r = 1; r < 8; ++r) v[r] = mul<T>(v[r], w2[r]);
+        for (int r = 1; r < 8; ++r) v[r] = mulc<T>(v[r], w2[r]);
         group_sync(gid);
 #pragma unroll
         for (int r = 0; r < 8; ++r) buf[(k1s2 * 8 + r) * PAD + t1] = v[r];   // row (k1, m1), column t1
@@ -412,7 +429,7 @@ __global__ void __launch_bounds__(256) k_inv_z512(ZInvBatch batch, long nlines, 
         for (int r = 0; r < 8; ++r) v[r] = buf[t * PAD + r];
         dft<T, +1>(v, 8);
         group_sync(gid);
-        // outputs: real parts -> line l1, imaginary parts -> line l2, via shared memory for coalesced stores
+        // outputs: real parts -> line l1, imaginary parts -> line l2, via shared memory for coalesced 16-byte stores
         T* re = reinterpret_cast<T*>(buf);
         T* im = re + N + 8;
         const int k1 = t >> 3, m1 = t & 7;
@@ -426,15 +443,21 @@ __global__ void __launch_bounds__(256) k_inv_z512(ZInvBatch batch, long nlines, 
         T* o1 = out + l1 * N;
         T* o2 = out + l2 * N;
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const int x = t + 64 * e;
-            T a = re[x], b = im[x];
+        for (int e = 0; e < N / (64 * V); ++e) {
+            const int x = V * (t + 64 * e);
+            VT a = *reinterpret_cast<const VT*>(re + x);
+            VT b = *reinterpret_cast<const VT*>(im + x);
             if (mulout) {
-                a *= mulout[l1 * N + x];
-                if (has2) b *= mulout[l2 * N + x];
+                T* pa = reinterpret_cast<T*>(&a);
+                T* pb = reinterpret_cast<T*>(&b);
+#pragma unroll
+                for (int i = 0; i < V; ++i) {
+                    pa[i] *= mulout[l1 * N + x + i];
+                    if (has2) pb[i] *= mulout[l2 * N + x + i];
+                }
             }
-            o1[x] = a;
-            if (has2) o2[x] = b;
+            *reinterpret_cast<VT*>(o1 + x) = a;
+            if (has2) *reinterpret_cast<VT*>(o2 + x) = b;
         }
         group_sync(gid);
     }
