@@ -411,13 +411,17 @@ __device__ __forceinline__ void producer(const GroupDesc& G, const Params& P, ui
         for (int m = 0; m < kBloItems; ++m)
             if (ptid + 256 * m < s_chunks) b[m] = *reinterpret_cast<const uint4*>(slot + s_off + 16 * (ptid + 256 * m));
     };
-    if (nstages <= 0) return;
+    // tensor-memory addresses from warp-uniform, divide-free values (the base is 0: the CTA holds all 512
+    // columns; the issuing warps check it), so that the compiler keeps the store addresses in uniform registers
+    if (nstages <= 0 || tmem != 0u) return;
     if (!warp_wait(&slot_full[0], 0u, abort_flag, err)) return;
     load_tile(ring, 0, xc, yc);
     load_blo(ring, bl);
+    int s = 0, as = 0, s1 = 1 % kRingSlots;
+    uint32_t aph = 1u, s1ph = 0u;                        // a_empty parity of round st / nA - 1; slot_full of st + 1
+    uint32_t a_stage = (uint32_t)a_col0;
+    const uint32_t a_step = 64u * NT;
     for (int st = 0; st < nstages; ++st) {
-        const int s = st % kRingSlots;
-        const int as = st % nA;
         const unsigned char* slot = ring + (size_t)s * slot_bytes;
         bool ok = true;
 #pragma unroll
@@ -426,13 +430,12 @@ __device__ __forceinline__ void producer(const GroupDesc& G, const Params& P, ui
             if (t + 1 < NT) {
                 load_tile(slot, t + 1, xn, yn);
             } else if (st + 1 < nstages) {
-                const int s1 = (st + 1) % kRingSlots;
-                ok = ok && warp_wait(&slot_full[s1], (uint32_t)(((st + 1) / kRingSlots) & 1), abort_flag, err);
+                ok = ok && warp_wait(&slot_full[s1], s1ph, abort_flag, err);
                 if (ok) load_tile(ring + (size_t)s1 * slot_bytes, 0, xn, yn);
             }
             if (t == 0) {
                 // tensor memory A stage and B_lo stage `as` are free once the MMAs of stage st - nA completed
-                if (st >= nA) ok = ok && warp_wait(&a_empty[as], (uint32_t)((st / nA - 1) & 1), abort_flag, err);
+                if (st >= nA) ok = ok && warp_wait(&a_empty[as], aph, abort_flag, err);
                 tc_fence_after();
             }
             if (!ok) continue;
@@ -455,7 +458,7 @@ __device__ __forceinline__ void producer(const GroupDesc& G, const Params& P, ui
 #pragma unroll
                 for (int c = 0; c < 32; ++c) v[c] = 0u;
             }
-            tmem_st32(tmem + lane_base + (uint32_t)(a_col0 + as * 64 * NT + 64 * t + 32 * gp), v);
+            tmem_st32(lane_base + a_stage + (uint32_t)(64 * t + 32 * gp), v);
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 xc[c] = xn[c];
@@ -479,7 +482,7 @@ __device__ __forceinline__ void producer(const GroupDesc& G, const Params& P, ui
             }
         }
         // the next stage's B_lo chunks (its slot is already full: waited for the first tile's prefetch)
-        if (st + 1 < nstages) load_blo(ring + (size_t)((st + 1) % kRingSlots) * slot_bytes, bl);
+        if (st + 1 < nstages) load_blo(ring + (size_t)s1 * slot_bytes, bl);
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // B_lo stores -> tensor core
         tc_fence_before();
@@ -490,6 +493,9 @@ __device__ __forceinline__ void producer(const GroupDesc& G, const Params& P, ui
             mbar_arrive(&a_full[as]);
             mbar_arrive(&slot_empty[s]);
         }
+        s = s1;
+        if (++s1 == kRingSlots) { s1 = 0; s1ph ^= 1u; }
+        if (++as == nA) { as = 0; aph ^= 1u; a_stage = (uint32_t)a_col0; } else { a_stage += a_step; }
     }
 }
 
