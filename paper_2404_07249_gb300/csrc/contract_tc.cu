@@ -519,7 +519,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + kMaxTiles);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // warp index through a shuffle from lane 0: the compiler then knows it is warp-uniform, so role branches and
+    // the tensor-memory addresses derived from it stay in uniform registers
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int warp = __shfl_sync(0xffffffffu, tid >> 5, 0);
     const long c0 = (long)blockIdx.x * P.cells_cta;
     const long c1 = min(P.ncell, c0 + P.cells_cta);
     const int nslots = c0 < c1 ? (int)((c1 - c0 + kSlotCells - 1) / kSlotCells) : 0;
