@@ -398,6 +398,8 @@ __device__ __forceinline__ void producer(const GroupDesc& G, const Params& P, ui
     // (j < 0) read row 0 and store zeros.
     float4 xc[4], yc[4], xn[4], yn[4];
     uint4 bl[kBloItems];
+    // with one or two tiles warp 3 (idle otherwise) makes B_lo; with three it issues tile 2's MMAs
+    constexpr bool kBloByProducers = NT > 2;
     auto load_tile = [&](const unsigned char* slot, int t, float4 (&x)[4], float4 (&y)[4]) {
         const int j = max(pj[t], 0), k = max(pk[t], 0);
 #pragma unroll
@@ -416,7 +418,7 @@ __device__ __forceinline__ void producer(const GroupDesc& G, const Params& P, ui
     if (nstages <= 0 || tmem != 0u) return;
     if (!warp_wait(&slot_full[0], 0u, abort_flag, err)) return;
     load_tile(ring, 0, xc, yc);
-    load_blo(ring, bl);
+    if (kBloByProducers) load_blo(ring, bl);
     int s = 0, as = 0, s1 = 1 % kRingSlots;
     uint32_t aph = 1u, s1ph = 0u;                        // a_empty parity of round st / nA - 1; slot_full of st + 1
     uint32_t a_stage = (uint32_t)a_col0;
@@ -470,7 +472,7 @@ __device__ __forceinline__ void producer(const GroupDesc& G, const Params& P, ui
         unsigned char* bs = bst + (size_t)as * bstage_bytes;
 #pragma unroll
         for (int m = 0; m < kBloItems; ++m) {
-            if (ptid + 256 * m < s_chunks) {
+            if (kBloByProducers && ptid + 256 * m < s_chunks) {
                 uint32_t* w = reinterpret_cast<uint32_t*>(&bl[m]);
                 const uint64_t g01 = (uint64_t)w[0] | ((uint64_t)w[1] << 32);
                 const uint64_t g23 = (uint64_t)w[2] | ((uint64_t)w[3] << 32);
@@ -482,7 +484,7 @@ __device__ __forceinline__ void producer(const GroupDesc& G, const Params& P, ui
             }
         }
         // the next stage's B_lo chunks (its slot is already full: waited for the first tile's prefetch)
-        if (st + 1 < nstages) load_blo(ring + (size_t)s1 * slot_bytes, bl);
+        if (kBloByProducers && st + 1 < nstages) load_blo(ring + (size_t)s1 * slot_bytes, bl);
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // B_lo stores -> tensor core
         tc_fence_before();
@@ -536,10 +538,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (tid == 0) {
         for (int s = 0; s < kRingSlots; ++s) {
             mbar_init(&slot_full[s], 1);
-            mbar_init(&slot_empty[s], kProdWarps + ntiles);   // producer warps read a slot, the MMAs read B_hi
+            // producer warps read a slot, the MMAs read B_hi, warp 3 (one or two tiles) reads it for B_lo
+            mbar_init(&slot_empty[s], kProdWarps + ntiles + (ntiles <= 2 ? 1 : 0));
         }
         for (int s = 0; s < kMaxAStages; ++s) {
-            mbar_init(&a_full[s], kProdWarps);   // both producer groups make a stage (A and B_lo), one arrival a warp
+            // both producer groups make a stage's A (and B_lo with three tiles; warp 3 makes it otherwise)
+            mbar_init(&a_full[s], kProdWarps + (ntiles <= 2 ? 1 : 0));
             mbar_init(&a_empty[s], ntiles);        // one commit per issuing thread (tile)
         }
         for (int i = 0; i < 2 * kMaxTiles; ++i) mbar_init(&d_full[i], 1);
@@ -584,6 +588,48 @@ __global__ void __launch_bounds__(kThreads, 1)
                     drain_wait(&slot_full[sl % kRingSlots], (uint32_t)((sl / kRingSlots) & 1), err);
             }
             __syncwarp();
+        } else if (warp == 3 && ntiles <= 2) {
+            // ------------------------------------------------------------------ B_lo (one or two tiles)
+            // every 16-byte chunk of a slot's singles region -> (g - trunc(g)) rounded to TF32, same offset in the
+            // B_lo stage; released to the issuers with one arrival on the stage barrier
+            const int s_off = P.s_off, s_chunks = P.s_chunks;
+            int s = 0, as = 0;
+            uint32_t sph = 0u, aph = 1u;
+            for (int st = 0; st < nstages; ++st) {
+                if (!warp_wait(&slot_full[s], sph, abort_flag, err)) break;
+                if (st >= nA && !warp_wait(&a_empty[as], aph, abort_flag, err)) break;
+                const unsigned char* src = ring + (size_t)s * slot_bytes + s_off;
+                unsigned char* dst = bst + (size_t)as * bstage_bytes;
+                for (int i0 = 0; i0 < s_chunks; i0 += 128) {
+                    uint4 g[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int i = i0 + 32 * u + lane;
+                        if (i < s_chunks) g[u] = *reinterpret_cast<const uint4*>(src + 16 * i);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int i = i0 + 32 * u + lane;
+                        if (i < s_chunks) {
+                            const uint64_t g01 = (uint64_t)g[u].x | ((uint64_t)g[u].y << 32);
+                            const uint64_t g23 = (uint64_t)g[u].z | ((uint64_t)g[u].w << 32);
+                            const uint64_t l01 = sub_x2(g01, g01 & 0xFFFFE000FFFFE000ull);
+                            const uint64_t l23 = sub_x2(g23, g23 & 0xFFFFE000FFFFE000ull);
+                            *reinterpret_cast<uint4*>(dst + 16 * i) = make_uint4(
+                                ((uint32_t)l01 + 0x1000u) & 0xFFFFE000u, ((uint32_t)(l01 >> 32) + 0x1000u) & 0xFFFFE000u,
+                                ((uint32_t)l23 + 0x1000u) & 0xFFFFE000u, ((uint32_t)(l23 >> 32) + 0x1000u) & 0xFFFFE000u);
+                        }
+                    }
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // B_lo stores -> tensor core
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(&a_full[as]);
+                    mbar_arrive(&slot_empty[s]);
+                }
+                if (++s == kRingSlots) { s = 0; sph ^= 1u; }
+                if (++as == nA) { as = 0; aph ^= 1u; }
+            }
         } else if (warp - 1 < ntiles) {
             // ------------------------------------------------------------------ MMA issue (warp 1 + t: tile t)
             // The whole warp runs the loop (converged; every lane polls the barriers); the elected lane issues and
