@@ -217,15 +217,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* v) {
         : "r"(taddr)
         : "memory");
 }
-// tcgen05.wait::ld with the loaded registers as operands, so that no use of them is scheduled before the wait.
-__device__ __forceinline__ void tmem_wait_ld16(uint32_t* v) {
-    asm volatile("tcgen05.wait::ld.sync.aligned;"
-                 : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]),
-                   "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15])
-                 :
-                 : "memory");
-}
-
 // tcgen05.wait::ld tied to two 16-register loads (32 operands).
 __device__ __forceinline__ void tmem_wait_ld32(uint32_t* a, uint32_t* b) {
     asm volatile("tcgen05.wait::ld.sync.aligned;"
@@ -235,17 +226,6 @@ __device__ __forceinline__ void tmem_wait_ld32(uint32_t* a, uint32_t* b) {
                    "+r"(b[8]), "+r"(b[9]), "+r"(b[10]), "+r"(b[11]), "+r"(b[12]), "+r"(b[13]), "+r"(b[14]), "+r"(b[15])
                  :
                  : "memory");
-}
-
-// Shared-memory matrix descriptor, no swizzle (canonical K-major layout): core matrices of 8 rows x 16 bytes;
-// LBO = byte distance between core matrices adjacent in K, SBO = between 8-row groups.
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-    d |= (uint64_t)1 << 46;   // descriptor version for tcgen05
-    return d;                 // base offset 0, layout type 0 (no swizzle)
 }
 
 // Shared-memory matrix descriptor for the 128-byte swizzle, K-major: 8-row x 128-byte atoms (1024-byte aligned,
