@@ -378,8 +378,9 @@ __device__ __forceinline__ void producer(const GroupDesc& G, const Params& P, ui
     // (j < 0) read row 0 and store zeros.
     float4 xc[4], yc[4], xn[4], yn[4];
     uint4 bl[kBloItems];
-    // with one or two tiles warp 3 (idle otherwise) makes B_lo; with three it issues tile 2's MMAs
-    constexpr bool kBloByProducers = NT > 2;
+    // with two tiles warp 3 (idle otherwise) makes B_lo; with one tile the producers have the time for it (one warp
+    // would be the slower path: measured), with three warp 3 issues tile 2's MMAs
+    constexpr bool kBloByProducers = NT != 2;
     auto load_tile = [&](const unsigned char* slot, int t, float4 (&x)[4], float4 (&y)[4]) {
         const int j = max(pj[t], 0), k = max(pk[t], 0);
 #pragma unroll
@@ -518,12 +519,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (tid == 0) {
         for (int s = 0; s < kRingSlots; ++s) {
             mbar_init(&slot_full[s], 1);
-            // producer warps read a slot, the MMAs read B_hi, warp 3 (one or two tiles) reads it for B_lo
-            mbar_init(&slot_empty[s], kProdWarps + ntiles + (ntiles <= 2 ? 1 : 0));
+            // producer warps read a slot, the MMAs read B_hi, warp 3 (two tiles) reads it for B_lo
+            mbar_init(&slot_empty[s], kProdWarps + ntiles + (ntiles == 2 ? 1 : 0));
         }
         for (int s = 0; s < kMaxAStages; ++s) {
-            // both producer groups make a stage's A (and B_lo with three tiles; warp 3 makes it otherwise)
-            mbar_init(&a_full[s], kProdWarps + (ntiles <= 2 ? 1 : 0));
+            // both producer groups make a stage's A (and B_lo, except with two tiles: then warp 3 makes it)
+            mbar_init(&a_full[s], kProdWarps + (ntiles == 2 ? 1 : 0));
             mbar_init(&a_empty[s], ntiles);        // one commit per issuing thread (tile)
         }
         for (int i = 0; i < 2 * kMaxTiles; ++i) mbar_init(&d_full[i], 1);
@@ -568,8 +569,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     drain_wait(&slot_full[sl % kRingSlots], (uint32_t)((sl / kRingSlots) & 1), err);
             }
             __syncwarp();
-        } else if (warp == 3 && ntiles <= 2) {
-            // ------------------------------------------------------------------ B_lo (one or two tiles)
+        } else if (warp == 3 && ntiles == 2) {
+            // ------------------------------------------------------------------ B_lo (two tiles)
             // every 16-byte chunk of a slot's singles region -> (g - trunc(g)) rounded to TF32, same offset in the
             // B_lo stage; released to the issuers with one arrival on the stage barrier
             const int s_off = P.s_off, s_chunks = P.s_chunks;
