@@ -3,7 +3,8 @@
 Tolerances (float32 path): FFT outputs and shell maps within 2e-6 of the L2 norm (relative L2 error; FP32
 rounding of ~log2 N radix passes); contraction outputs within 1e-6 of sum_x |g_j g_k h_i| (the
 cancellation-aware error); bispectrum and P_ell within 1e-6 relative wherever the estimate is not dominated
-by cancellation (kappa = sum|ggg| / |sum ggg| below 1e3); N_abc bit-exact.  FP64 path:
+by cancellation (kappa = sum|ggg| / |sum ggg| below 1e3: an FP32 relative error eps in the maps moves the
+estimate by up to ~3 kappa eps relative, so larger kappa is judged by the absolute metric); N_abc bit-exact.  FP64 path:
 1e-12 in the same metrics.
 """
 import numpy as np
