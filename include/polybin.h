@@ -180,6 +180,22 @@ int polybin_get_stage_times(polybin_ctx* ctx, double* ms, long long* calls, int 
 /* Number of kernels this context has launched so far. */
 int polybin_launch_count(const polybin_ctx* ctx, long long* n);
 
+/* The contraction kernel that ran last on this context: POLYBIN_SPLIT_TF32X3 contexts use the tensor-core kernel
+ * whenever the shape allows it (<= 512 pairs, <= 32 singles a call, 16-byte aligned maps) and the FP32 SIMT kernel
+ * otherwise; this call tells which one produced the last result.  *path = -1 before the first contraction. */
+enum { POLYBIN_PATH_SIMT_FP64 = 0, POLYBIN_PATH_SIMT_FP32 = 1, POLYBIN_PATH_TENSOR_SPLIT_TF32X3 = 2 };
+int polybin_last_path(const polybin_ctx* ctx, int* path);
+
+/* Lengths of the grid the bispectrum's triplet sums are evaluated on (host int[3]).  Every shell map has wave
+ * numbers |n_i| <= m on each axis (m: the largest component of a binned mode), so the product of three maps has
+ * |n_i| <= 3m and its sum over the cells of any grid with more than 3m points per axis is the same up to the factor
+ * (cells of the data grid) / (cells of that grid).  The library evaluates the maps g_b = IFT[Theta_b D] (with the
+ * data grid's 1/N) and the triplet sums on the smallest such grid whose lengths have no prime factor other than 2,
+ * 3, 5 (the data grid's length on an axis where 3m + 1 would not be shorter), and rescales: the outputs are those
+ * of the data grid (Sec. 4.3.1, eq. beta-def, and Sec. 4.4.1 on the data grid).  Outputs of polybin_shell_maps and
+ * polybin_contract stay on the data grid. */
+int polybin_contraction_grid(const polybin_ctx* ctx, int dims[3]);
+
 /* Failure-detection self-test: a kernel waits on an mbarrier phase that nothing completes, using the same bounded
  * poll as the tensor-core pipeline; the wait gives up after 2^14 polls and sets the device error flag, the kernel
  * returns and the context stays usable.  *timed_out = 1 when the bounded wait gave up (the expected outcome). */
@@ -211,17 +227,18 @@ int polybin_contract(polybin_ctx* ctx, const void* g, int n_g, const void* h, in
  * running inside a caller-managed memory pool or arena, plugins whose host application owns every allocation,
  * threads that must not call cudaMalloc/cudaFree because those can synchronise the device).
  * It computes the same M[p][i] = sum_x g_{j_p}(x) g_{k_p}(x) h_i(x) as polybin_contract (FP32 SIMT kernel) without a
- * context and without allocating: its scratch (FP64 per-block partial sums and the pair table) is a fixed
- * file-scope device array of 2^21 doubles (16 MiB) plus 8 KiB, held by every GPU that loads the library until the
- * process exits.
+ * context and without allocating: its scratch (FP64 per-block partial sums and the pair tables of every n <= 64) is
+ * a fixed file-scope device array of 2^21 doubles (16 MiB) plus 179 KiB, held by every GPU that loads the library
+ * until the process exits.
  *   g: device float32 [n_g][ncell]; h: device float32 [n_h][ncell] or NULL (h = g); 1 <= n_g, n_h <= 64 and
- *   n_g (n_g + 1) / 2 * n_h <= 2^21 (larger requests return POLYBIN_EINVAL).  m_out_dev: device float64
- *   [n_g (n_g + 1) / 2][n_h], written on cuda_stream (a cudaStream_t; NULL = legacy default stream).
+ *   n_g (n_g + 1) / 2 * n_h <= 2^21 (larger requests return POLYBIN_EINVAL, as do pointers that are not device
+ *   memory).  m_out_dev: device float64 [n_g (n_g + 1) / 2][n_h], written on cuda_stream (a cudaStream_t; NULL =
+ *   legacy default stream).
  * Asynchronous: the call returns after enqueueing; synchronise the stream before reading m_out_dev.  The first call
- * on a device looks up the scratch address (cudaGetSymbolAddress) and fills the pair table with a kernel: make
- * that first call before any stream capture.  Every call on a device shares the scratch, which keeps the last
- * call's contents (each call overwrites all it reads, so nothing needs clearing): calls that overlap on the GPU
- * (other streams, or other host threads) race and must be serialised by the caller.
+ * on a device looks up the scratch address (cudaGetSymbolAddress), fills the pair tables with a kernel and waits for
+ * it: make that first call before any stream capture.  Every call on a device shares the scratch, which keeps the
+ * last call's contents (each call overwrites all it reads, so nothing needs clearing): calls that overlap on the
+ * GPU (other streams, or other host threads) race and must be serialised by the caller.
  * Errors: polybin_contract_noalloc_error() describes the last failure on the calling host thread. */
 int polybin_contract_noalloc(const float* g, int n_g, const float* h, int n_h, long long ncell, double* m_out_dev,
                              void* cuda_stream);

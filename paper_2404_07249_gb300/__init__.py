@@ -59,9 +59,12 @@ _SIGS = {
     "polybin_selftest_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
     "polybin_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
                                      ctypes.c_void_p]),
+    "polybin_last_path": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
+    "polybin_contraction_grid": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
 }
 
 FISHER_PK, FISHER_BK = 0, 1
+PATH_SIMT_FP64, PATH_SIMT_FP32, PATH_TENSOR_SPLIT_TF32X3 = 0, 1, 2
 
 STAGES = ("forward", "shells", "contract", "pk_bin")
 
@@ -201,6 +204,18 @@ class PolyBin:
         t = ctypes.c_int(0)
         self._check(self.lib.polybin_selftest_wait(self.ctx, ctypes.byref(t)), "polybin_selftest_wait")
         return t.value == 1
+
+    def last_path(self) -> int:
+        """Which contraction kernel produced the last result (PATH_* constants; -1 before the first)."""
+        p = ctypes.c_int()
+        self._check(self.lib.polybin_last_path(self.ctx, ctypes.byref(p)), "polybin_last_path")
+        return p.value
+
+    def contraction_grid(self):
+        """Lengths of the alias-free grid the triplet sums are evaluated on."""
+        d = np.zeros(3, dtype=np.int32)
+        self._check(self.lib.polybin_contraction_grid(self.ctx, _ptr(d)), "polybin_contraction_grid")
+        return tuple(int(v) for v in d)
 
     def launch_count(self) -> int:
         n = ctypes.c_longlong()

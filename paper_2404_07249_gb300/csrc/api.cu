@@ -144,12 +144,15 @@ int run_forward(polybin_ctx* ctx, const TIN* in, const TM* m1, const TM* m2, C<T
     return POLYBIN_OK;
 }
 
-// a2: shell maps g_b = IFT[Theta_b L_ell D] for all bins (box == nullptr: unit spectrum, giving t_b).
+// a2: shell maps g_b = IFT[Theta_b L_ell D] for all bins on grid ig (box == nullptr: unit spectrum, giving t_b).
+// The inverse DFT is normalised by the data grid's 1/N on either grid, so a map on the contraction grid holds the
+// same band-limited function as on the data grid, sampled at fewer points.
 template <typename T>
-int run_shells(polybin_ctx* ctx, const C<T>* box, C<T>* u1, C<T>* u2, T* g, int ell) {
-    const int N0 = ctx->N[0], N1 = ctx->N[1], N2 = ctx->N[2];
+int run_shells(polybin_ctx* ctx, const C<T>* box, C<T>* u1, C<T>* u2, T* g, int ell, const InvGrid& ig) {
+    const int N0 = ig.N[0], N1 = ig.N[1], N2 = ig.N[2];
     const int nb = ctx->nb;
     int rc = POLYBIN_OK;
+    auto tw = [&](int a) { return (const C<T>*)(sizeof(T) == 4 ? ig.tw_f[a] : ig.tw_d[a]); };
     StageTimer timer(ctx, kStageShells);
     {
         const int TK = cols_per_cta<T>(N0);
@@ -157,7 +160,7 @@ int run_shells(polybin_ctx* ctx, const C<T>* box, C<T>* u1, C<T>* u2, T* g, int 
         XInvBatch b;
         int maxcols = 0;
         for (int i = 0; i < nb; ++i) {
-            const BinBox& bb = ctx->bbox[i];
+            const BinBox& bb = ig.bbox[i];
             b.it[i].out = u1 + bb.u1_off;
             b.it[i].rx = bb.rx; b.it[i].ry = bb.ry; b.it[i].rz = bb.rz;
             b.it[i].bin = i;
@@ -165,11 +168,10 @@ int run_shells(polybin_ctx* ctx, const C<T>* box, C<T>* u1, C<T>* u2, T* g, int 
             maxcols = std::max(maxcols, bb.ry.cnt * bb.rz.cnt);
         }
         dim3 grid((maxcols + TK - 1) / TK, nb, 1);
-        PB_WITH_NT(N0, NT, {
+        PB_WITH_NT_INV(N0, NT, {
             if ((rc = set_smem<T>(ctx, (const void*)k_inv_x_filter<T, NT>, sm))) return rc;
             k_inv_x_filter<T, NT><<<grid, 256, sm, ctx->stream>>>(b, box, ctx->gx, ctx->gy, ctx->gz, ctx->d_lut, ctx->smax,
-                                                                  T(1.0 / (double)ctx->ncell), ctx->plan[0],
-                                                                  twiddles<T>(ctx, 0), TK);
+                                                                  T(1.0 / (double)ctx->ncell), ig.plan[0], tw(0), TK);
         })
         if ((rc = launch_check(ctx, "k_inv_x_filter"))) return rc;
     }
@@ -179,7 +181,7 @@ int run_shells(polybin_ctx* ctx, const C<T>* box, C<T>* u1, C<T>* u2, T* g, int 
         ColBatch b;
         int maxc = 0;
         for (int i = 0; i < nb; ++i) {
-            const BinBox& bb = ctx->bbox[i];
+            const BinBox& bb = ig.bbox[i];
             ColItem& it = b.it[i];
             it.in = u1 + bb.u1_off; it.out = u2 + bb.u2_off;
             it.in_os = (long)bb.ry.cnt * bb.rz.cnt; it.in_es = bb.rz.cnt;
@@ -188,9 +190,9 @@ int run_shells(polybin_ctx* ctx, const C<T>* box, C<T>* u1, C<T>* u2, T* g, int 
             maxc = std::max(maxc, bb.rz.cnt);
         }
         dim3 grid((maxc + TK - 1) / TK, N0, nb);
-        PB_WITH_NT(N1, NT, {
+        PB_WITH_NT_INV(N1, NT, {
             if ((rc = set_smem<T>(ctx, (const void*)k_col<T, +1, NT>, sm))) return rc;
-            k_col<T, +1, NT><<<grid, 256, sm, ctx->stream>>>(b, ctx->plan[1], twiddles<T>(ctx, 1), TK);
+            k_col<T, +1, NT><<<grid, 256, sm, ctx->stream>>>(b, ig.plan[1], tw(1), TK);
         })
         if ((rc = launch_check(ctx, "k_col inv y"))) return rc;
     }
@@ -199,9 +201,9 @@ int run_shells(polybin_ctx* ctx, const C<T>* box, C<T>* u1, C<T>* u2, T* g, int 
         const size_t sm = (2 * (size_t)N2 * (LP + 1) + N2) * sizeof(C<T>);
         ZInvBatch b;
         for (int i = 0; i < nb; ++i) {
-            const BinBox& bb = ctx->bbox[i];
+            const BinBox& bb = ig.bbox[i];
             b.it[i].in = u2 + bb.u2_off;
-            b.it[i].out = g + (size_t)i * ctx->ncell;
+            b.it[i].out = g + (size_t)i * ig.ncell;
             b.it[i].kin = bb.rz.cnt;
         }
         const long nlines = (long)N0 * N1;
@@ -209,13 +211,12 @@ int run_shells(polybin_ctx* ctx, const C<T>* box, C<T>* u1, C<T>* u2, T* g, int 
             // register-resident 512-point transform, 16 line pairs per CTA
             const int lpc = 16;
             dim3 grid512((unsigned)(((nlines + 1) / 2 + lpc - 1) / lpc), nb, 1);
-            k_inv_z512<T><<<grid512, 256, 0, ctx->stream>>>(b, nlines, T(1), (const T*)nullptr, twiddles<T>(ctx, 2), lpc);
+            k_inv_z512<T><<<grid512, 256, 0, ctx->stream>>>(b, nlines, T(1), (const T*)nullptr, tw(2), lpc);
         } else {
             dim3 grid((unsigned)((nlines + 2 * LP - 1) / (2 * LP)), nb, 1);
-            PB_WITH_NT(N2, NT, {
+            PB_WITH_NT_INV(N2, NT, {
                 if ((rc = set_smem<T>(ctx, (const void*)k_inv_z<T, NT>, sm))) return rc;
-                k_inv_z<T, NT><<<grid, 256, sm, ctx->stream>>>(b, nlines, T(1), (const T*)nullptr, ctx->plan[2],
-                                                              twiddles<T>(ctx, 2), LP);
+                k_inv_z<T, NT><<<grid, 256, sm, ctx->stream>>>(b, nlines, T(1), (const T*)nullptr, ig.plan[2], tw(2), LP);
             })
         }
         if ((rc = launch_check(ctx, "k_inv_z"))) return rc;
@@ -242,33 +243,37 @@ ContractGeom contract_geom(int nb, int nh, long ncell) {
 // a3: contraction; result (device, [npairs][nh] doubles) in d_out.
 template <typename T>
 int run_contract(polybin_ctx* ctx, const T* g, int ng, const T* h, int nh, double* d_partial, size_t partial_cap,
-                 double* d_out) {
+                 double* d_out, long ncell) {
     int rc;
     StageTimer timer(ctx, kStageContract);
-    ContractGeom G = contract_geom(ng, nh, ctx->ncell);
+    ContractGeom G = contract_geom(ng, nh, ncell);
     if ((size_t)G.ncb * G.npairs * G.nh > partial_cap) return fail(ctx, POLYBIN_EINVAL, "contract: partial buffer too small");
     const size_t sm = ((size_t)kCH * G.rows_cta + (size_t)kCH * G.nhp + (size_t)ng * (kCH + 1)) * sizeof(T) + 16;
     if ((rc = set_smem<T>(ctx, (const void*)k_contract<T>, sm))) return rc;
     dim3 grid(G.ngroups, G.ncb, 1);
-    k_contract<T><<<grid, 256, sm, ctx->stream>>>(g, h, ctx->ncell, ctx->d_pairs + pairs_offset(ng), G, d_partial);
+    k_contract<T><<<grid, 256, sm, ctx->stream>>>(g, h, ncell, ctx->d_pairs + pairs_offset(ng), G, d_partial);
     if ((rc = launch_check(ctx, "k_contract"))) return rc;
     const long nout = (long)G.npairs * G.nh;
     k_reduce_partials<<<(unsigned)((nout + 255) / 256), 256, 0, ctx->stream>>>(d_partial, G.ncb, nout, d_out);
     return launch_check(ctx, "k_reduce_partials");
 }
 
-// a4: P_ell numerators num[ell][b] (host) from the box spectrum.
+// a4: P_ell binning partials [nb][nseg][nell] (device, ctx->d_pkpart) from the box spectrum.
+template <typename T>
+int run_pkbin_dev(polybin_ctx* ctx, const C<T>* box) {
+    StageTimer timer(ctx, kStagePk);
+    k_pk_bin<T><<<dim3(ctx->nb, ctx->pk_nseg, 1), 256, 0, ctx->stream>>>(box, ctx->d_offs, ctx->d_coef, ctx->nmodes,
+                                                                         ctx->d_bin_start, ctx->nell, ctx->pk_seg_len,
+                                                                         ctx->d_pkpart);
+    return launch_check(ctx, "k_pk_bin");
+}
+
+// a4: P_ell numerators num[ell][b] (host) from the box spectrum (segments summed in order on the host).
 template <typename T>
 int run_pkbin(polybin_ctx* ctx, const C<T>* box, std::vector<double>& num) {
     int rc;
     const int nb = ctx->nb, nell = ctx->nell;
-    dim3 grid(nb, ctx->pk_nseg, 1);
-    {
-    StageTimer timer(ctx, kStagePk);
-    k_pk_bin<T><<<grid, 256, 0, ctx->stream>>>(box, ctx->d_offs, ctx->d_coef, ctx->nmodes, ctx->d_bin_start, nell,
-                                                ctx->pk_seg_len, ctx->d_pkpart);
-    if ((rc = launch_check(ctx, "k_pk_bin"))) return rc;
-    }
+    if ((rc = run_pkbin_dev<T>(ctx, box))) return rc;
     std::vector<double> part((size_t)nb * ctx->pk_nseg * nell);
     PB_CUDA_OK(cudaMemcpyAsync(part.data(), ctx->d_pkpart, part.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     PB_CUDA_OK(cudaStreamSynchronize(ctx->stream));
@@ -285,18 +290,51 @@ template int run_forward<double, double, double>(polybin_ctx*, const double*, co
 template int run_forward<double, double, float>(polybin_ctx*, const double*, const float*, const float*, double2*, double2*, double2*);
 template int run_pkbin<float>(polybin_ctx*, const float2*, std::vector<double>&);
 template int run_pkbin<double>(polybin_ctx*, const double2*, std::vector<double>&);
-template int run_shells<float>(polybin_ctx*, const float2*, float2*, float2*, float*, int);
-template int run_shells<double>(polybin_ctx*, const double2*, double2*, double2*, double*, int);
-template int run_contract<float>(polybin_ctx*, const float*, int, const float*, int, double*, size_t, double*);
-template int run_contract<double>(polybin_ctx*, const double*, int, const double*, int, double*, size_t, double*);
+template int run_pkbin_dev<float>(polybin_ctx*, const float2*);
+template int run_pkbin_dev<double>(polybin_ctx*, const double2*);
+template int run_shells<float>(polybin_ctx*, const float2*, float2*, float2*, float*, int, const InvGrid&);
+template int run_shells<double>(polybin_ctx*, const double2*, double2*, double2*, double*, int, const InvGrid&);
+template int run_contract<float>(polybin_ctx*, const float*, int, const float*, int, double*, size_t, double*, long);
+template int run_contract<double>(polybin_ctx*, const double*, int, const double*, int, double*, size_t, double*, long);
 
 template <>
 int run_contract_any<double>(polybin_ctx* ctx, const double* g, int ng, const double* h, int nh, double* part,
-                             size_t cap, double* out) {
-    return run_contract<double>(ctx, g, ng, h, nh, part, cap, out);
+                             size_t cap, double* out, long ncell) {
+    return run_contract<double>(ctx, g, ng, h, nh, part, cap, out, ncell);
 }
 
 // ----------------------------------------------------------------------------------------------- planner
+
+// Smallest even length >= need that make_plan accepts (factors 2, 3, 5; <= 1024), or 0 if there is none.
+static int fft_len_at_least(int need) {
+    for (int n = std::max(need, 2); n <= 1024; ++n) {
+        FftPlan p;
+        if (n % 2 == 0 && make_plan(n, p)) return n;
+    }
+    return 0;
+}
+
+// Bin boxes and intermediate offsets of the inverse transforms on grid ig (lengths set by the caller).
+static void plan_inv_grid(polybin_ctx* ctx, InvGrid& ig) {
+    const int nb = ctx->nb;
+    ig.ncell = (long)ig.N[0] * ig.N[1] * ig.N[2];
+    for (int a = 0; a < 3; ++a) make_plan(ig.N[a], ig.plan[a]);
+    ig.bbox.resize(nb);
+    long u1 = 0, u2 = 0;
+    for (int b = 0; b < nb; ++b) {
+        BinBox& bb = ig.bbox[b];
+        const int mb = max_component(ctx->kf, ctx->edges[b + 1]);
+        bb.rx = axis_box(mb, ig.N[0]);
+        bb.ry = axis_box(mb, ig.N[1]);
+        bb.rz = z_box(mb, ig.N[2]);
+        bb.u1_off = u1;
+        bb.u2_off = u2;
+        u1 += (long)ig.N[0] * bb.ry.cnt * bb.rz.cnt;
+        u2 += (long)ig.N[0] * ig.N[1] * bb.rz.cnt;
+    }
+    ig.u1_total = u1;
+    ig.u2_total = u2;
+}
 
 static int plan_bins(polybin_ctx* ctx) {
     const int nb = ctx->nb;
@@ -318,21 +356,22 @@ static int plan_bins(polybin_ctx* ctx) {
     ctx->gx = axis_box(m, ctx->N[0]);
     ctx->gy = axis_box(m, ctx->N[1]);
     ctx->gz = z_box(m, ctx->N[2]);
-    ctx->bbox.resize(nb);
-    long u1 = 0, u2 = 0;
-    for (int b = 0; b < nb; ++b) {
-        BinBox& bb = ctx->bbox[b];
-        const int mb = max_component(kf, ctx->edges[b + 1]);
-        bb.rx = axis_box(mb, ctx->N[0]);
-        bb.ry = axis_box(mb, ctx->N[1]);
-        bb.rz = z_box(mb, ctx->N[2]);
-        bb.u1_off = u1;
-        bb.u2_off = u2;
-        u1 += (long)ctx->N[0] * bb.ry.cnt * bb.rz.cnt;
-        u2 += (long)ctx->N[0] * ctx->N[1] * bb.rz.cnt;
+    // Data grid.
+    for (int a = 0; a < 3; ++a) ctx->fg.N[a] = ctx->N[a];
+    plan_inv_grid(ctx, ctx->fg);
+    // Contraction grid.  Every shell map has wave numbers |n_i| <= m on each axis, so a product of three has
+    // |n_i| <= 3m, and the sum over the cells of a grid of length L_i per axis picks up exactly the zero mode of that
+    // product when L_i > 3m (no nonzero multiple of L_i lies within the product's band).  The data grid sum
+    // (when itself alias-free, N_i > 3m) therefore equals (N / N') times the same sum over any grid N' with
+    // N'_i > 3m: the triplet sums are evaluated on the smallest such 2-3-5 grid.  Where N_i <= 3m (triangles that
+    // wrap around the data grid are part of the sum) the axis keeps its data length.
+    for (int a = 0; a < 3; ++a) {
+        const int need = 3 * std::min(m, ctx->N[a] / 2) + 1;
+        const int L = fft_len_at_least(need);
+        ctx->cg.N[a] = (need < ctx->N[a] && L > 0 && L < ctx->N[a]) ? L : ctx->N[a];
     }
-    ctx->u1_total = u1;
-    ctx->u2_total = u2;
+    plan_inv_grid(ctx, ctx->cg);
+    ctx->cg_ratio = (double)ctx->ncell / (double)ctx->cg.ncell;
     return POLYBIN_OK;
 }
 
@@ -388,28 +427,46 @@ static int plan_pk(polybin_ctx* ctx) {
     PB_CUDA_OK_C(cudaMalloc(&c->d_coef, sizeof(double) * all_coef.size()));
     PB_CUDA_OK_C(cudaMalloc(&c->d_bin_start, sizeof(int) * (nb + 1)));
     PB_CUDA_OK_C(cudaMalloc(&c->d_pkpart, sizeof(double) * (size_t)nb * c->pk_nseg * nell));
+    PB_CUDA_OK_C(cudaMalloc(&c->d_pkout, sizeof(double) * (size_t)nb * nell));
+    PB_CUDA_OK_C(cudaMalloc(&c->d_counts, sizeof(double) * nb));
+    PB_CUDA_OK_C(cudaMemcpy(c->d_counts, c->counts.data(), sizeof(double) * nb, cudaMemcpyHostToDevice));
     if (M) PB_CUDA_OK_C(cudaMemcpy(c->d_offs, all_offs.data(), sizeof(int) * M, cudaMemcpyHostToDevice));
     PB_CUDA_OK_C(cudaMemcpy(c->d_coef, all_coef.data(), sizeof(double) * all_coef.size(), cudaMemcpyHostToDevice));
     PB_CUDA_OK_C(cudaMemcpy(c->d_bin_start, start.data(), sizeof(int) * (nb + 1), cudaMemcpyHostToDevice));
     return POLYBIN_OK;
 }
 
+// e^{-2 pi i m / n}, m = 0 .. n-1, in float and double (device arrays owned by the caller).
+static int make_twiddles(polybin_ctx* ctx, int n, void** f, void** d) {
+    std::vector<float2> tf(n);
+    std::vector<double2> td(n);
+    for (int m = 0; m < n; ++m) {
+        const double ang = 2.0 * M_PI * (double)m / (double)n;
+        const double cr = std::cos(ang), si = -std::sin(ang);
+        td[m] = make_double2(cr, si);
+        tf[m] = make_float2((float)cr, (float)si);
+    }
+    PB_CUDA_OK_C(cudaMalloc(f, sizeof(float2) * n));
+    PB_CUDA_OK_C(cudaMalloc(d, sizeof(double2) * n));
+    PB_CUDA_OK_C(cudaMemcpy(*f, tf.data(), sizeof(float2) * n, cudaMemcpyHostToDevice));
+    PB_CUDA_OK_C(cudaMemcpy(*d, td.data(), sizeof(double2) * n, cudaMemcpyHostToDevice));
+    return POLYBIN_OK;
+}
+
 static int upload_twiddles(polybin_ctx* ctx) {
+    int rc;
     for (int a = 0; a < 3; ++a) {
-        const int n = ctx->N[a];
-        std::vector<float2> tf(n);
-        std::vector<double2> td(n);
-        for (int m = 0; m < n; ++m) {
-            // e^{-2 pi i m / n}, evaluated in float64 with the argument reduced to [0, pi/4] by symmetry
-            const double ang = 2.0 * M_PI * (double)m / (double)n;
-            const double cr = std::cos(ang), si = -std::sin(ang);
-            td[m] = make_double2(cr, si);
-            tf[m] = make_float2((float)cr, (float)si);
+        if ((rc = make_twiddles(ctx, ctx->N[a], &ctx->d_tw_f[a], &ctx->d_tw_d[a]))) return rc;
+        ctx->fg.tw_f[a] = ctx->d_tw_f[a];
+        ctx->fg.tw_d[a] = ctx->d_tw_d[a];
+        if (ctx->cg.N[a] == ctx->N[a]) {
+            ctx->cg.tw_f[a] = ctx->d_tw_f[a];
+            ctx->cg.tw_d[a] = ctx->d_tw_d[a];
+        } else {
+            if ((rc = make_twiddles(ctx, ctx->cg.N[a], &ctx->d_ctw[2 * a], &ctx->d_ctw[2 * a + 1]))) return rc;
+            ctx->cg.tw_f[a] = ctx->d_ctw[2 * a];
+            ctx->cg.tw_d[a] = ctx->d_ctw[2 * a + 1];
         }
-        PB_CUDA_OK_C(cudaMalloc(&ctx->d_tw_f[a], sizeof(float2) * n));
-        PB_CUDA_OK_C(cudaMalloc(&ctx->d_tw_d[a], sizeof(double2) * n));
-        PB_CUDA_OK_C(cudaMemcpy(ctx->d_tw_f[a], tf.data(), sizeof(float2) * n, cudaMemcpyHostToDevice));
-        PB_CUDA_OK_C(cudaMemcpy(ctx->d_tw_d[a], td.data(), sizeof(double2) * n, cudaMemcpyHostToDevice));
     }
     return POLYBIN_OK;
 }
@@ -423,8 +480,8 @@ int alloc_work(polybin_ctx* ctx, Work& w) {
     PB_CUDA_OK_C(cudaMalloc(&w.t1, sizeof(C<T>) * N0 * N1 * Bz));
     PB_CUDA_OK_C(cudaMalloc(&w.t2, sizeof(C<T>) * N0 * By * Bz));
     PB_CUDA_OK_C(cudaMalloc(&w.box, sizeof(C<T>) * Bx * By * Bz));
-    PB_CUDA_OK_C(cudaMalloc(&w.u1, sizeof(C<T>) * ctx->u1_total));
-    PB_CUDA_OK_C(cudaMalloc(&w.u2, sizeof(C<T>) * ctx->u2_total));
+    PB_CUDA_OK_C(cudaMalloc(&w.u1, sizeof(C<T>) * std::max(ctx->fg.u1_total, ctx->cg.u1_total)));
+    PB_CUDA_OK_C(cudaMalloc(&w.u2, sizeof(C<T>) * std::max(ctx->fg.u2_total, ctx->cg.u2_total)));
     PB_CUDA_OK_C(cudaMalloc(&w.g, sizeof(T) * (size_t)ctx->nb * ctx->ncell));
     const int np = 64 * 65 / 2;
     ContractGeom G = contract_geom(std::max(ctx->nb, 1), std::max(ctx->nb, 1), ctx->ncell);
@@ -465,7 +522,7 @@ int resolve_input(polybin_ctx* ctx, const float* p, size_t count, const float** 
     return POLYBIN_OK;
 }
 
-// N_abc via the FP64 pipeline on unit fields (cached).
+// N_abc via the FP64 pipeline on unit fields (cached), evaluated on the contraction grid: T_abc = cg_ratio T'_abc.
 int ensure_triplets(polybin_ctx* ctx) {
     if (ctx->trip_ready) return POLYBIN_OK;
     int rc;
@@ -476,8 +533,9 @@ int ensure_triplets(polybin_ctx* ctx) {
         if ((rc = alloc_work_shells_double(ctx, tmp))) { free_work(tmp); return rc; }
         w = &tmp;
     }
-    rc = run_shells<double>(ctx, nullptr, (double2*)w->u1, (double2*)w->u2, (double*)w->g, 0);
-    if (!rc) rc = run_contract<double>(ctx, (const double*)w->g, ctx->nb, nullptr, ctx->nb, w->partial, w->partial_cap, w->mout);
+    const long cn = ctx->cg.ncell;
+    rc = run_shells<double>(ctx, nullptr, (double2*)w->u1, (double2*)w->u2, (double*)w->g, 0, ctx->cg);
+    if (!rc) rc = run_contract<double>(ctx, (const double*)w->g, ctx->nb, nullptr, ctx->nb, w->partial, w->partial_cap, w->mout, cn);
     const int nb = ctx->nb, np = nb * (nb + 1) / 2;
     std::vector<double> T((size_t)np * nb);
     if (!rc) {
@@ -494,7 +552,7 @@ int ensure_triplets(polybin_ctx* ctx) {
     for (int a = 0; a < nb; ++a)
         for (int b = a; b < nb; ++b)
             for (int c = b; c < nb; ++c) {
-                const double t = T[(size_t)pair_index(nb, a, b) * nb + c];
+                const double t = ctx->cg_ratio * T[(size_t)pair_index(nb, a, b) * nb + c];
                 const double cnt = std::nearbyint(n2 * t);
                 if (cnt > 0) {
                     ctx->trip.push_back(a); ctx->trip.push_back(b); ctx->trip.push_back(c);
@@ -506,24 +564,30 @@ int ensure_triplets(polybin_ctx* ctx) {
     std::vector<int> m(std::max(nt, (size_t)1), 0);
     for (size_t t = 0; t < nt; ++t)
         m[t] = pair_index(nb, ctx->trip[3 * t], ctx->trip[3 * t + 1]) * nb + ctx->trip[3 * t + 2];
+    std::vector<double> Tv(std::max(nt, (size_t)1), 1.0);
+    for (size_t t = 0; t < nt; ++t) Tv[t] = ctx->Tabc[t];
     polybin_ctx* c = ctx;
     PB_CUDA_OK_C(cudaMalloc(&c->d_S, sizeof(double) * m.size()));
+    PB_CUDA_OK_C(cudaMalloc(&c->d_B, sizeof(double) * m.size()));
+    PB_CUDA_OK_C(cudaMalloc(&c->d_T, sizeof(double) * m.size()));
     PB_CUDA_OK_C(cudaMalloc(&c->d_trip_m, sizeof(int) * m.size()));
     PB_CUDA_OK_C(cudaMemcpy(c->d_trip_m, m.data(), sizeof(int) * m.size(), cudaMemcpyHostToDevice));
+    PB_CUDA_OK_C(cudaMemcpy(c->d_T, Tv.data(), sizeof(double) * Tv.size(), cudaMemcpyHostToDevice));
     ctx->trip_ready = true;
     // the tensor-core plan is built now, outside any later stream capture
-    if (ctx->prec == POLYBIN_SPLIT_TF32X3 && nt > 0 && tc_shape_ok(ctx, (const float*)ctx->w.g, nb, nullptr, nb))
+    if (ctx->prec == POLYBIN_SPLIT_TF32X3 && nt > 0 && tc_shape_ok(ctx->cg.ncell, (const float*)ctx->w.g, nb, nullptr, nb))
         return prepare_triplet_tc(ctx);
     return POLYBIN_OK;
 }
 
+// FP64 workspace of the N_abc pipeline (unit-field shell maps on the contraction grid and their contraction).
 int alloc_work_shells_double(polybin_ctx* ctx, Work& w) {
     polybin_ctx* c = ctx;
     w.elem = sizeof(double);
-    PB_CUDA_OK_C(cudaMalloc(&w.u1, sizeof(double2) * ctx->u1_total));
-    PB_CUDA_OK_C(cudaMalloc(&w.u2, sizeof(double2) * ctx->u2_total));
-    PB_CUDA_OK_C(cudaMalloc(&w.g, sizeof(double) * (size_t)ctx->nb * ctx->ncell));
-    ContractGeom G = contract_geom(ctx->nb, ctx->nb, ctx->ncell);
+    PB_CUDA_OK_C(cudaMalloc(&w.u1, sizeof(double2) * ctx->cg.u1_total));
+    PB_CUDA_OK_C(cudaMalloc(&w.u2, sizeof(double2) * ctx->cg.u2_total));
+    PB_CUDA_OK_C(cudaMalloc(&w.g, sizeof(double) * (size_t)ctx->nb * ctx->cg.ncell));
+    ContractGeom G = contract_geom(ctx->nb, ctx->nb, ctx->cg.ncell);
     w.partial_cap = (size_t)G.ncb * G.npairs * G.nh;
     PB_CUDA_OK_C(cudaMalloc(&w.partial, sizeof(double) * w.partial_cap));
     PB_CUDA_OK_C(cudaMalloc(&w.mout, sizeof(double) * (size_t)G.npairs * G.nh));
@@ -606,7 +670,9 @@ extern "C" void polybin_destroy(polybin_ctx* ctx) {
     if (!ctx) return;
     free_work(ctx->w);
     void* ptrs[] = {ctx->d_lut, ctx->d_pairs, ctx->d_offs, ctx->d_coef, ctx->d_bin_start, ctx->d_pkpart, ctx->d_in,
-                    ctx->d_tw_f[0], ctx->d_tw_f[1], ctx->d_tw_f[2], ctx->d_tw_d[0], ctx->d_tw_d[1], ctx->d_tw_d[2]};
+                    ctx->d_pkout, ctx->d_counts,
+                    ctx->d_tw_f[0], ctx->d_tw_f[1], ctx->d_tw_f[2], ctx->d_tw_d[0], ctx->d_tw_d[1], ctx->d_tw_d[2],
+                    ctx->d_ctw[0], ctx->d_ctw[1], ctx->d_ctw[2], ctx->d_ctw[3], ctx->d_ctw[4], ctx->d_ctw[5]};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     destroy_extras(ctx);
@@ -638,59 +704,34 @@ extern "C" int polybin_get_triplets(polybin_ctx* ctx, int* abc, double* n_abc) {
     return POLYBIN_OK;
 }
 
-// Continuous-normalisation P_ell (eq. fish-ideal-continuous) from the numerators of one field.
-static void pk_normalise(const polybin_ctx* ctx, const std::vector<double>& num, double* o) {
-    const int nb = ctx->nb, nell = ctx->nell;
-    const double N = (double)ctx->ncell;
-    for (int b = 0; b < nb; ++b)
-        for (int l = 0; l < nell; ++l)
-            o[(size_t)l * nb + b] = ctx->counts[b] > 0 ? (4 * l + 1) * (ctx->vol / (N * N)) * num[(size_t)l * nb + b] / ctx->counts[b]
-                                                      : NAN;
-}
-
+// Ideal bispectrum and/or continuous-normalisation P_ell of `batch` fields: per field one forward transform, then
+// the P binning and its normalisation (eq. fish-ideal-continuous) and the shell maps, triplet sums and their
+// normalisation B = (V^2 / N^3) S / T (Sec. 4.4.1), all on the device; one read-back and one synchronisation per
+// field.
 template <typename T>
 static int bk_pk_t(polybin_ctx* ctx, const float* delta, int batch, double* bk_out, double* pk_out) {
     int rc;
-    const int nb = ctx->nb;
+    const int nb = ctx->nb, nell = ctx->nell;
     const size_t nt = ctx->Nabc.size();
-    std::vector<double> S(std::max(nt, (size_t)1)), num;
-    const double pref = ctx->vol * ctx->vol / ((double)ctx->ncell * (double)ctx->ncell * (double)ctx->ncell);
     for (int f = 0; f < batch; ++f) {
         const float* in;
         if ((rc = resolve_input(ctx, delta + (size_t)f * ctx->ncell, ctx->ncell, &in))) return rc;
         Work& w = ctx->w;
         if ((rc = run_forward<T, float, float>(ctx, in, (const float*)nullptr, (const float*)nullptr, (C<T>*)w.t1, (C<T>*)w.t2, (C<T>*)w.box))) return rc;
         if (pk_out) {
-            if ((rc = run_pkbin<T>(ctx, (const C<T>*)w.box, num))) return rc;
-            pk_normalise(ctx, num, pk_out + (size_t)f * ctx->nell * nb);
+            if ((rc = run_pkbin_dev<T>(ctx, (const C<T>*)w.box))) return rc;
+            if ((rc = run_pk_normalise(ctx, ctx->d_pkout))) return rc;
+            PB_CUDA_OK(cudaMemcpyAsync(pk_out + (size_t)f * nell * nb, ctx->d_pkout, sizeof(double) * nell * nb,
+                                       cudaMemcpyDeviceToHost, ctx->stream));
         }
-        if (!bk_out || nt == 0) continue;
-        if ((rc = run_shells<T>(ctx, (const C<T>*)w.box, (C<T>*)w.u1, (C<T>*)w.u2, (T*)w.g, 0))) return rc;
-        if ((rc = run_triplet_sums<T>(ctx, (const T*)w.g, ctx->d_S))) return rc;
-        PB_CUDA_OK(cudaMemcpyAsync(S.data(), ctx->d_S, sizeof(double) * nt, cudaMemcpyDeviceToHost, ctx->stream));
+        if (bk_out && nt > 0) {
+            if ((rc = run_shells<T>(ctx, (const C<T>*)w.box, (C<T>*)w.u1, (C<T>*)w.u2, (T*)w.g, 0, ctx->cg))) return rc;
+            if ((rc = run_triplet_sums<T>(ctx, (const T*)w.g, ctx->d_S))) return rc;
+            if ((rc = run_bk_normalise(ctx, ctx->d_S, ctx->d_B))) return rc;
+            PB_CUDA_OK(cudaMemcpyAsync(bk_out + (size_t)f * nt, ctx->d_B, sizeof(double) * nt, cudaMemcpyDeviceToHost,
+                                       ctx->stream));
+        }
         PB_CUDA_OK(cudaStreamSynchronize(ctx->stream));
-        for (size_t t = 0; t < nt; ++t) bk_out[(size_t)f * nt + t] = pref * S[t] / ctx->Tabc[t];
-    }
-    return POLYBIN_OK;
-}
-
-template <typename T>
-static int bk_ideal_t(polybin_ctx* ctx, const float* delta, int batch, double* bk_out) {
-    int rc;
-    const size_t nt = ctx->Nabc.size();
-    std::vector<double> S(std::max(nt, (size_t)1));
-    const double pref = ctx->vol * ctx->vol / ((double)ctx->ncell * (double)ctx->ncell * (double)ctx->ncell);
-    if (nt == 0) return POLYBIN_OK;
-    for (int f = 0; f < batch; ++f) {
-        const float* in;
-        if ((rc = resolve_input(ctx, delta + (size_t)f * ctx->ncell, ctx->ncell, &in))) return rc;
-        Work& w = ctx->w;
-        if ((rc = run_forward<T, float, float>(ctx, in, (const float*)nullptr, (const float*)nullptr, (C<T>*)w.t1, (C<T>*)w.t2, (C<T>*)w.box))) return rc;
-        if ((rc = run_shells<T>(ctx, (const C<T>*)w.box, (C<T>*)w.u1, (C<T>*)w.u2, (T*)w.g, 0))) return rc;
-        if ((rc = run_triplet_sums<T>(ctx, (const T*)w.g, ctx->d_S))) return rc;
-        PB_CUDA_OK(cudaMemcpyAsync(S.data(), ctx->d_S, sizeof(double) * nt, cudaMemcpyDeviceToHost, ctx->stream));
-        PB_CUDA_OK(cudaStreamSynchronize(ctx->stream));
-        for (size_t t = 0; t < nt; ++t) bk_out[(size_t)f * nt + t] = pref * S[t] / ctx->Tabc[t];
     }
     return POLYBIN_OK;
 }
@@ -699,12 +740,14 @@ extern "C" int polybin_bk_ideal(polybin_ctx* ctx, const float* delta, int batch,
     if (!ctx || !delta || !bk_out || batch < 0) return fail(ctx, POLYBIN_EINVAL, "polybin_bk_ideal: bad argument");
     int rc = ensure_triplets(ctx);
     if (rc) return rc;
-    return ctx->prec == POLYBIN_FP64 ? bk_ideal_t<double>(ctx, delta, batch, bk_out)
-                                     : bk_ideal_t<float>(ctx, delta, batch, bk_out);
+    return ctx->prec == POLYBIN_FP64 ? bk_pk_t<double>(ctx, delta, batch, bk_out, nullptr)
+                                     : bk_pk_t<float>(ctx, delta, batch, bk_out, nullptr);
 }
 
+// Discrete-Fisher P_ell (eq. pk-limit): p = F^-1 p_num per bin, p_num = (1/2)(1/N) num, F = (1/2) sum L L' (a 3 x 3
+// solve per bin on the host), physical units x V/N.
 template <typename T>
-static int pk_t(polybin_ctx* ctx, const float* delta, int batch, bool discrete, double* pk_out) {
+static int pk_discrete_t(polybin_ctx* ctx, const float* delta, int batch, double* pk_out) {
     int rc;
     const int nb = ctx->nb, nell = ctx->nell;
     std::vector<double> num;
@@ -717,19 +760,14 @@ static int pk_t(polybin_ctx* ctx, const float* delta, int batch, bool discrete, 
         double* o = pk_out + (size_t)f * nell * nb;
         const double N = (double)ctx->ncell;
         for (int b = 0; b < nb; ++b) {
-            if (!discrete) {
-                if (b == 0) pk_normalise(ctx, num, o);
-            } else {
-                // p = F^-1 p_num per bin, p_num = (1/2)(1/N) num, F = (1/2) sum L L'; physical units x V/N.
-                double A[3][4];
-                for (int l = 0; l < nell; ++l) {
-                    for (int l2 = 0; l2 < nell; ++l2) A[l][l2] = ctx->fish_disc[((size_t)b * nell + l) * nell + l2];
-                    A[l][nell] = 0.5 * num[(size_t)l * nb + b] / N;
-                }
-                double x[3] = {0, 0, 0};
-                if (!solve_small(A, nell, x)) for (int l = 0; l < nell; ++l) x[l] = NAN;
-                for (int l = 0; l < nell; ++l) o[(size_t)l * nb + b] = x[l] * ctx->vol / N;
+            double A[3][4];
+            for (int l = 0; l < nell; ++l) {
+                for (int l2 = 0; l2 < nell; ++l2) A[l][l2] = ctx->fish_disc[((size_t)b * nell + l) * nell + l2];
+                A[l][nell] = 0.5 * num[(size_t)l * nb + b] / N;
             }
+            double x[3] = {0, 0, 0};
+            if (!solve_small(A, nell, x)) for (int l = 0; l < nell; ++l) x[l] = NAN;
+            for (int l = 0; l < nell; ++l) o[(size_t)l * nb + b] = x[l] * ctx->vol / N;
         }
     }
     return POLYBIN_OK;
@@ -737,12 +775,14 @@ static int pk_t(polybin_ctx* ctx, const float* delta, int batch, bool discrete, 
 
 extern "C" int polybin_pk(polybin_ctx* ctx, const float* delta, int batch, double* pk_out) {
     if (!ctx || !delta || !pk_out || batch < 0) return fail(ctx, POLYBIN_EINVAL, "polybin_pk: bad argument");
-    return ctx->prec == POLYBIN_FP64 ? pk_t<double>(ctx, delta, batch, false, pk_out) : pk_t<float>(ctx, delta, batch, false, pk_out);
+    return ctx->prec == POLYBIN_FP64 ? bk_pk_t<double>(ctx, delta, batch, nullptr, pk_out)
+                                     : bk_pk_t<float>(ctx, delta, batch, nullptr, pk_out);
 }
 
 extern "C" int polybin_pk_discrete(polybin_ctx* ctx, const float* delta, int batch, double* pk_out) {
     if (!ctx || !delta || !pk_out || batch < 0) return fail(ctx, POLYBIN_EINVAL, "polybin_pk_discrete: bad argument");
-    return ctx->prec == POLYBIN_FP64 ? pk_t<double>(ctx, delta, batch, true, pk_out) : pk_t<float>(ctx, delta, batch, true, pk_out);
+    return ctx->prec == POLYBIN_FP64 ? pk_discrete_t<double>(ctx, delta, batch, pk_out)
+                                     : pk_discrete_t<float>(ctx, delta, batch, pk_out);
 }
 
 extern "C" int polybin_mode_counts(const polybin_ctx* ctx, double* counts) {
@@ -776,9 +816,9 @@ extern "C" int polybin_shell_maps(polybin_ctx* ctx, const void* spec, void* g_ou
     int rc;
     Work& w = ctx->w;
     if (ctx->prec == POLYBIN_FP64)
-        rc = run_shells<double>(ctx, (const double2*)spec, (double2*)w.u1, (double2*)w.u2, (double*)g_out, 0);
+        rc = run_shells<double>(ctx, (const double2*)spec, (double2*)w.u1, (double2*)w.u2, (double*)g_out, 0, ctx->fg);
     else
-        rc = run_shells<float>(ctx, (const float2*)spec, (float2*)w.u1, (float2*)w.u2, (float*)g_out, 0);
+        rc = run_shells<float>(ctx, (const float2*)spec, (float2*)w.u1, (float2*)w.u2, (float*)g_out, 0, ctx->fg);
     if (rc) return rc;
     PB_CUDA_OK(cudaStreamSynchronize(ctx->stream));
     return POLYBIN_OK;
@@ -792,9 +832,11 @@ extern "C" int polybin_contract(polybin_ctx* ctx, const void* g, int n_g, const 
     Work& w = ctx->w;
     const size_t nout = (size_t)n_g * (n_g + 1) / 2 * n_h;
     if (ctx->prec == POLYBIN_FP64)
-        rc = run_contract_any<double>(ctx, (const double*)g, n_g, (const double*)h, n_h, w.partial, w.partial_cap, w.mout);
+        rc = run_contract_any<double>(ctx, (const double*)g, n_g, (const double*)h, n_h, w.partial, w.partial_cap, w.mout,
+                                      ctx->ncell);
     else
-        rc = run_contract_any<float>(ctx, (const float*)g, n_g, (const float*)h, n_h, w.partial, w.partial_cap, w.mout);
+        rc = run_contract_any<float>(ctx, (const float*)g, n_g, (const float*)h, n_h, w.partial, w.partial_cap, w.mout,
+                                     ctx->ncell);
     if (rc) return rc;
     PB_CUDA_OK(cudaMemcpyAsync(m_out, w.mout, sizeof(double) * nout, cudaMemcpyDeviceToHost, ctx->stream));
     PB_CUDA_OK(cudaStreamSynchronize(ctx->stream));

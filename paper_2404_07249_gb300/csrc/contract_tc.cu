@@ -886,14 +886,15 @@ static const char* layout_plan(Plan& pl, long ncell, int nsm, int ng, int nh, in
     return nullptr;
 }
 
-static int build_plan(polybin_ctx* ctx, Plan& pl, int ng, int nh, int hsep, std::vector<NeedPair> need, int n_out) {
+static int build_plan(polybin_ctx* ctx, Plan& pl, long ncell, int ng, int nh, int hsep, std::vector<NeedPair> need,
+                      int n_out) {
     int dev = 0, nsm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return fail_cuda(ctx, e, "cudaDeviceGetAttribute", __FILE__, __LINE__);
     std::vector<short2> rows;
     std::vector<int> gidx;
-    const char* msg = layout_plan(pl, ctx->ncell, nsm, ng, nh, hsep, std::move(need), n_out, rows, gidx);
+    const char* msg = layout_plan(pl, ncell, nsm, ng, nh, hsep, std::move(need), n_out, rows, gidx);
     if (msg) return fail(ctx, POLYBIN_EINVAL, "%s", msg);
     PB_CUDA_OK(cudaMalloc(&pl.d_rows, sizeof(short2) * rows.size()));
     PB_CUDA_OK(cudaMemcpy(pl.d_rows, rows.data(), sizeof(short2) * rows.size(), cudaMemcpyHostToDevice));
@@ -906,7 +907,7 @@ static int build_plan(polybin_ctx* ctx, Plan& pl, int ng, int nh, int hsep, std:
 }
 
 struct PlanCache {
-    std::map<std::tuple<int, int, int, int>, Plan*> plans;   // (ng, nh, hsep, kind)
+    std::map<std::tuple<int, int, int, int, long>, Plan*> plans;   // (ng, nh, hsep, kind, ncell)
     ~PlanCache() {
         for (auto& kv : plans) delete kv.second;
     }
@@ -930,12 +931,12 @@ static EncodeTiledFn encode_fn() {
 }
 
 // 2D map over `rows` maps of ncell floats (map-major): box = 32 cells x all maps, 128-byte swizzle.
-static int make_map(polybin_ctx* ctx, CUtensorMap* m, const float* base, int rows) {
+static int make_map(polybin_ctx* ctx, CUtensorMap* m, const float* base, int rows, long ncell) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return fail(ctx, POLYBIN_ECUDA, "contract_tc: cuTensorMapEncodeTiled is not available");
     if (reinterpret_cast<uintptr_t>(base) % 16) return fail(ctx, POLYBIN_EINVAL, "contract_tc: maps must be 16-byte aligned");
-    const cuuint64_t dims[2] = {(cuuint64_t)ctx->ncell, (cuuint64_t)rows};
-    const cuuint64_t strides[1] = {(cuuint64_t)ctx->ncell * sizeof(float)};
+    const cuuint64_t dims[2] = {(cuuint64_t)ncell, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ncell * sizeof(float)};
     const cuuint32_t box[2] = {(cuuint32_t)kSlotCells, (cuuint32_t)rows};
     const cuuint32_t estr[2] = {1, 1};
     const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
@@ -947,10 +948,10 @@ static int make_map(polybin_ctx* ctx, CUtensorMap* m, const float* base, int row
 
 static int launch(polybin_ctx* ctx, Plan& pl, const float* g, const float* h, double* d_out) {
     CUtensorMap mg, mh;
-    int rc = make_map(ctx, &mg, g, pl.ng);
+    int rc = make_map(ctx, &mg, g, pl.ng, pl.base.ncell);
     if (rc) return rc;
     if (pl.hsep) {
-        if ((rc = make_map(ctx, &mh, h, pl.nh))) return rc;
+        if ((rc = make_map(ctx, &mh, h, pl.nh, pl.base.ncell))) return rc;
     } else {
         mh = mg;
     }
@@ -999,9 +1000,9 @@ static PlanCache* cache_of(polybin_ctx* ctx) {
 }
 
 // Plan of all pairs (j <= k) of ng maps against the nh singles [0, nh), output M[(j, k)][i] pair-major.
-static int full_plan(polybin_ctx* ctx, int ng, int nh, int hsep, Plan** out) {
+static int full_plan(polybin_ctx* ctx, long ncell, int ng, int nh, int hsep, Plan** out) {
     PlanCache* pc = cache_of(ctx);
-    auto key = std::make_tuple(ng, nh, hsep, 0);
+    auto key = std::make_tuple(ng, nh, hsep, 0, ncell);
     auto it = pc->plans.find(key);
     if (it != pc->plans.end()) { *out = it->second; return POLYBIN_OK; }
     std::vector<NeedPair> need;
@@ -1013,19 +1014,19 @@ static int full_plan(polybin_ctx* ctx, int ng, int nh, int hsep, Plan** out) {
             need.push_back(std::move(np));
         }
     Plan* pl = new Plan();
-    int rc = build_plan(ctx, *pl, ng, nh, hsep, std::move(need), p * nh);
+    int rc = build_plan(ctx, *pl, ncell, ng, nh, hsep, std::move(need), p * nh);
     if (rc) { delete pl; return rc; }
     pc->plans[key] = pl;
     *out = pl;
     return POLYBIN_OK;
 }
 
-// Plan of the closed triplets of the context: triplet a <= b <= c from pair (b, c) and single a, output S in
-// triplet order.
+// Plan of the closed triplets of the context on the contraction grid: triplet a <= b <= c from pair (b, c) and
+// single a, output S' in triplet order.
 static int triplet_plan(polybin_ctx* ctx, Plan** out) {
     PlanCache* pc = cache_of(ctx);
     const int nb = ctx->nb;
-    auto key = std::make_tuple(nb, nb, 0, 1);
+    auto key = std::make_tuple(nb, nb, 0, 1, ctx->cg.ncell);
     auto it = pc->plans.find(key);
     if (it != pc->plans.end()) { *out = it->second; return POLYBIN_OK; }
     std::map<std::pair<int, int>, NeedPair> m;
@@ -1041,7 +1042,7 @@ static int triplet_plan(polybin_ctx* ctx, Plan** out) {
     std::vector<NeedPair> need;
     for (auto& kv : m) need.push_back(std::move(kv.second));
     Plan* pl = new Plan();
-    int rc = build_plan(ctx, *pl, nb, nb, 0, std::move(need), nt);
+    int rc = build_plan(ctx, *pl, ctx->cg.ncell, nb, nb, 0, std::move(need), nt);
     if (rc) { delete pl; return rc; }
     pc->plans[key] = pl;
     *out = pl;
@@ -1067,19 +1068,19 @@ int ensure_err_flag(polybin_ctx* ctx) {
 }
 
 // Shapes the tensor-core kernel takes: <= 512 pairs, <= 32 singles, cells a multiple of 4, 16-byte aligned maps.
-bool tc_shape_ok(polybin_ctx* ctx, const float* g, int ng, const float* h, int nh) {
+bool tc_shape_ok(long ncell, const float* g, int ng, const float* h, int nh) {
     if (ng < 1 || ng * (ng + 1) / 2 > 512 || nh < 1 || nh > 32) return false;
-    if (ctx->ncell % 4 || ctx->ncell > 0x7fffffffL) return false;
+    if (ncell % 4 || ncell > 0x7fffffffL) return false;
     if (reinterpret_cast<uintptr_t>(g) % 16 || (h && reinterpret_cast<uintptr_t>(h) % 16)) return false;
     return true;
 }
 
-// M[(j <= k)][i] (pair-major, device) of ng maps g against nh singles h (h == nullptr: h = g).
-int run_contract_tc(polybin_ctx* ctx, const float* g, int ng, const float* h, int nh, double*, size_t, double* d_out) {
+// M[(j <= k)][i] (pair-major, device) of ng maps g against nh singles h (h == nullptr: h = g), over ncell cells.
+int run_contract_tc(polybin_ctx* ctx, const float* g, int ng, const float* h, int nh, double* d_out, long ncell) {
     const int hsep = (h && h != g) ? 1 : 0;
     if (!hsep) nh = ng;
     tc::Plan* pl = nullptr;
-    int rc = tc::full_plan(ctx, ng, nh, hsep, &pl);
+    int rc = tc::full_plan(ctx, ncell, ng, nh, hsep, &pl);
     if (rc) return rc;
     return tc::launch(ctx, *pl, g, hsep ? h : g, d_out);
 }
@@ -1090,7 +1091,7 @@ int prepare_triplet_tc(polybin_ctx* ctx) {
     return tc::triplet_plan(ctx, &pl);
 }
 
-// S_abc of every closed triplet (device, triplet order) from the shell maps g.
+// S'_abc of every closed triplet (device, triplet order) from the shell maps g on the contraction grid.
 int run_triplet_sums_tc(polybin_ctx* ctx, const float* g, double* d_S) {
     tc::Plan* pl = nullptr;
     int rc = tc::triplet_plan(ctx, &pl);

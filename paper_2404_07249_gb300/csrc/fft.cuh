@@ -150,8 +150,9 @@ __device__ C<T>* fft_lines(C<T>* src, C<T>* dst, int L, int ES, const FftPlan& p
 
 
 // ------------------------------------------------------------------------------------------------
-// Compile-time specialisation for power-of-two lengths (64 .. 1024): radices, strides and line counts are
-// constants, so the index arithmetic is shifts and masks and every radix loop is fully unrolled.
+// Compile-time specialisation for the lengths listed in PB_WITH_NT: radices, strides and line counts are
+// constants, so the index arithmetic folds and every radix loop is fully unrolled.  The radix order is that of
+// make_plan (8s, then 4, 2, 3s, 5s).
 template <typename T> __host__ __device__ constexpr int lines_per_cta_of(int n) {
     int lp = 16;
     while (lp > 1 && 2 * (long)n * (lp + 1) * (long)sizeof(C<T>) > 96 * 1024) lp >>= 1;
@@ -162,24 +163,26 @@ template <typename T> __host__ __device__ constexpr int cols_per_cta_of(int n) {
     while (tk > 1 && 2 * (long)n * tk * (long)sizeof(C<T>) > 64 * 1024) tk >>= 1;
     return tk;
 }
-__host__ __device__ constexpr int p2_radix(int n, int pass) {
-    int m = n;
-    for (int p = 0; p < pass; ++p) m /= (m % 8 == 0) ? 8 : ((m % 4 == 0) ? 4 : 2);
-    return m <= 1 ? 1 : ((m % 8 == 0) ? 8 : ((m % 4 == 0) ? 4 : 2));
+__host__ __device__ constexpr int ct_next_radix(int m) {
+    return m % 8 == 0 ? 8 : (m % 4 == 0 ? 4 : (m % 2 == 0 ? 2 : (m % 3 == 0 ? 3 : (m % 5 == 0 ? 5 : 1))));
 }
-__host__ __device__ constexpr int p2_passes(int n) {
+__host__ __device__ constexpr int ct_radix(int n, int pass) {
+    int m = n;
+    for (int p = 0; p < pass; ++p) m /= ct_next_radix(m);
+    return m <= 1 ? 1 : ct_next_radix(m);
+}
+__host__ __device__ constexpr int ct_passes(int n) {
     int c = 0;
-    while (p2_radix(n, c) > 1) ++c;
+    while (ct_radix(n, c) > 1) ++c;
     return c;
 }
-__host__ __device__ constexpr bool ct_length(int n) { return n == 64 || n == 128 || n == 256 || n == 512 || n == 1024; }
 
 template <typename T, int DIR, int N, int L, int ES, int NTHR, int PASS, int NS>
 __device__ __forceinline__ C<T>* fft_ct_pass(C<T>* src, C<T>* dst, const C<T>* __restrict__ tw, int tid) {
-    if constexpr (PASS == p2_passes(N)) {
+    if constexpr (PASS == ct_passes(N)) {
         return src;
     } else {
-        constexpr int R = p2_radix(N, PASS);
+        constexpr int R = ct_radix(N, PASS);
         constexpr int NBF = N / R;
         constexpr int TSTR = N / (NS * R);
         constexpr int TOTAL = NBF * L;
@@ -603,6 +606,23 @@ namespace pb {
         case 64: { constexpr int NTV = 64; __VA_ARGS__ } break;   \
         case 128: { constexpr int NTV = 128; __VA_ARGS__ } break; \
         case 256: { constexpr int NTV = 256; __VA_ARGS__ } break; \
+        case 512: { constexpr int NTV = 512; __VA_ARGS__ } break; \
+        case 1024: { constexpr int NTV = 1024; __VA_ARGS__ } break; \
+        default: { constexpr int NTV = 0; __VA_ARGS__ } break;    \
+    }
+// The inverse passes also run on the contraction grids (lengths 3m + 1 and up rounded to a 2-3-5 length):
+// compile-time versions of the common ones.
+#define PB_WITH_NT_INV(n, NTV, ...)                          \
+    switch (n) {                                             \
+        case 64: { constexpr int NTV = 64; __VA_ARGS__ } break;   \
+        case 80: { constexpr int NTV = 80; __VA_ARGS__ } break;   \
+        case 96: { constexpr int NTV = 96; __VA_ARGS__ } break;   \
+        case 128: { constexpr int NTV = 128; __VA_ARGS__ } break; \
+        case 160: { constexpr int NTV = 160; __VA_ARGS__ } break; \
+        case 192: { constexpr int NTV = 192; __VA_ARGS__ } break; \
+        case 256: { constexpr int NTV = 256; __VA_ARGS__ } break; \
+        case 288: { constexpr int NTV = 288; __VA_ARGS__ } break; \
+        case 320: { constexpr int NTV = 320; __VA_ARGS__ } break; \
         case 512: { constexpr int NTV = 512; __VA_ARGS__ } break; \
         case 1024: { constexpr int NTV = 1024; __VA_ARGS__ } break; \
         default: { constexpr int NTV = 0; __VA_ARGS__ } break;    \

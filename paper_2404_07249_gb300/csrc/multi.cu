@@ -43,9 +43,10 @@ static int capture_field(polybin_ctx* c, const float* field, double* host_dst) {
     if ((rc = run_forward<T, float, float>(c, field, (const float*)nullptr, (const float*)nullptr, (C<T>*)w.t1, (C<T>*)w.t2,
                                            (C<T>*)w.box)))
         return rc;
-    if ((rc = run_shells<T>(c, (const C<T>*)w.box, (C<T>*)w.u1, (C<T>*)w.u2, (T*)w.g, 0))) return rc;
+    if ((rc = run_shells<T>(c, (const C<T>*)w.box, (C<T>*)w.u1, (C<T>*)w.u2, (T*)w.g, 0, c->cg))) return rc;
     if ((rc = run_triplet_sums<T>(c, (const T*)w.g, c->d_S))) return rc;
-    cudaError_t e = cudaMemcpyAsync(host_dst, c->d_S, sizeof(double) * nt, cudaMemcpyDeviceToHost, c->stream);
+    if ((rc = run_bk_normalise(c, c->d_S, c->d_B))) return rc;
+    cudaError_t e = cudaMemcpyAsync(host_dst, c->d_B, sizeof(double) * nt, cudaMemcpyDeviceToHost, c->stream);
     if (e != cudaSuccess) return fail_cuda(c, e, "capture copy", __FILE__, __LINE__);
     return POLYBIN_OK;
 }
@@ -143,10 +144,8 @@ extern "C" int polybin_bk_ideal_multi(polybin_ctx* const* ctxs, const float* con
             PB_CUDA_OK(cudaMemcpy(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
         }
         if (herr) return fail(c0, POLYBIN_ETIMEOUT, "polybin_bk_ideal_multi: a pipeline wait timed out (field %d)", i);
-        const double* S = m->host + m->off[i];
-        const double pref = c->vol * c->vol / ((double)c->ncell * (double)c->ncell * (double)c->ncell);
-        const size_t nt = c->Nabc.size();
-        for (size_t t = 0; t < nt; ++t) bk_out[i][t] = pref * S[t] / c->Tabc[t];
+        const double* B = m->host + m->off[i];
+        std::memcpy(bk_out[i], B, sizeof(double) * c->Nabc.size());
     }
     return POLYBIN_OK;
 }

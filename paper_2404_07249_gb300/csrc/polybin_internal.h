@@ -21,6 +21,20 @@ struct BinBox {
     long u1_off, u2_off;
 };
 
+// A grid the shell maps are evaluated on: its lengths, FFT plans and twiddles, and every bin's bounding box with
+// the offsets of that bin's inverse-transform intermediates.  Two are kept per context: the data grid (maps
+// returned to the caller, maps that are multiplied by a mask in real space) and the contraction grid, the
+// smallest 2-3-5 grid on which the triple product of three band-limited maps is alias-free (see plan_bins).
+struct InvGrid {
+    int N[3] = {0, 0, 0};
+    long ncell = 0;
+    FftPlan plan[3];
+    const void* tw_f[3] = {nullptr, nullptr, nullptr};   // float2 e^{-2 pi i m / N_a}
+    const void* tw_d[3] = {nullptr, nullptr, nullptr};   // double2
+    std::vector<BinBox> bbox;
+    long u1_total = 0, u2_total = 0;
+};
+
 // Device workspace of one compute precision.
 struct Work {
     size_t elem = 0;
@@ -39,7 +53,7 @@ int fail(polybin_ctx* ctx, int status, const char* fmt, ...);
 int fail_cuda(polybin_ctx* ctx, cudaError_t e, const char* what, const char* file, int line);
 
 inline int pair_index(int nb, int a, int b) { return a * nb - a * (a - 1) / 2 + (b - a); }
-inline long pairs_offset(int n) { return (long)(n - 1) * n * (n + 1) / 6; }  // sum_{m<n} m(m+1)/2
+__host__ __device__ inline long pairs_offset(int n) { return (long)(n - 1) * n * (n + 1) / 6; }  // sum_{m<n} m(m+1)/2
 
 // Gaussian elimination with partial pivoting on an n x (n+1) augmented matrix (n <= 3).
 inline bool solve_small(double A[3][4], int n, double* x) {
@@ -67,24 +81,32 @@ ContractGeom contract_geom(int nb, int nh, long ncell);
 
 template <typename T, typename TIN, typename TM>
 int run_forward(polybin_ctx*, const TIN*, const TM*, const TM*, C<T>*, C<T>*, C<T>*);
-template <typename T> int run_shells(polybin_ctx*, const C<T>*, C<T>*, C<T>*, T*, int ell);
+// Shell maps of all bins on grid `ig` (the data grid ctx->fg or the contraction grid ctx->cg), normalised with the
+// 1/N of the data grid's inverse DFT, so that maps on either grid sample the same band-limited function.
+template <typename T> int run_shells(polybin_ctx*, const C<T>*, C<T>*, C<T>*, T*, int ell, const InvGrid& ig);
 template <typename T> int run_pkbin(polybin_ctx*, const C<T>*, std::vector<double>&);
-template <typename T> int run_contract(polybin_ctx*, const T*, int, const T*, int, double*, size_t, double*);
+// Contractions over `ncell` cells (maps of the data grid or of the contraction grid).
+template <typename T> int run_contract(polybin_ctx*, const T*, int, const T*, int, double*, size_t, double*, long ncell);
 // Contraction dispatch: the tensor-core kernel in POLYBIN_SPLIT_TF32X3 mode, the SIMT kernel otherwise.
-template <typename T> int run_contract_any(polybin_ctx*, const T*, int, const T*, int, double*, size_t, double*);
+template <typename T> int run_contract_any(polybin_ctx*, const T*, int, const T*, int, double*, size_t, double*, long ncell);
 template <typename T> int alloc_work(polybin_ctx*, Work&);
 int alloc_work_shells_double(polybin_ctx*, Work&);
 void free_work(Work&);
 int resolve_input(polybin_ctx*, const float*, size_t, const float**);
 int ensure_triplets(polybin_ctx*);
 bool split_tc_available();
-bool tc_shape_ok(polybin_ctx*, const float* g, int ng, const float* h, int nh);
-int run_contract_tc(polybin_ctx*, const float*, int, const float*, int, double*, size_t, double*);
+bool tc_shape_ok(long ncell, const float* g, int ng, const float* h, int nh);
+int run_contract_tc(polybin_ctx*, const float*, int, const float*, int, double*, long ncell);
 int prepare_triplet_tc(polybin_ctx*);
 int run_triplet_sums_tc(polybin_ctx*, const float* g, double* d_S);
 void destroy_tc(polybin_ctx*);
-// S_abc of every closed triplet (device, triplet order) from the nb shell maps g of the context.
+// S'_abc of every closed triplet (device, triplet order) from the nb shell maps g on the contraction grid; the
+// data-grid sum is S_abc = cg_ratio S'_abc.
 template <typename T> int run_triplet_sums(polybin_ctx*, const T* g, double* d_S);
+// B_abc = scale S'_abc / T_abc on the device (FP64), scale = (V^2 / N^3) cg_ratio.
+int run_bk_normalise(polybin_ctx*, const double* d_S, double* d_B);
+// P_ell(b) from the P binning partials on the device (FP64): (2 ell + 1) (V / N^2) num / N_b.
+int run_pk_normalise(polybin_ctx*, double* d_P);
 void destroy_extras(polybin_ctx*);
 void destroy_unwindowed(polybin_ctx*);
 void destroy_multi(polybin_ctx*);
@@ -105,8 +127,10 @@ struct polybin_ctx {
 
     // planner
     pb::AxisRange gx{0, 0}, gy{0, 0}, gz{0, 0};
-    std::vector<pb::BinBox> bbox;
-    long u1_total = 0, u2_total = 0;
+    pb::InvGrid fg;              // inverse transforms on the data grid
+    pb::InvGrid cg;              // inverse transforms on the contraction grid
+    double cg_ratio = 1.0;       // ncell / cg.ncell
+    void* d_ctw[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};   // contraction-grid twiddles (f, d)
     int smax = 0;
     std::vector<int16_t> lut;
     int16_t* d_lut = nullptr;
@@ -126,6 +150,8 @@ struct polybin_ctx {
     double* d_coef = nullptr;
     int* d_bin_start = nullptr;
     double* d_pkpart = nullptr;
+    double* d_pkout = nullptr;   // normalised P_ell [nell][nb]
+    double* d_counts = nullptr;  // N_b
     int pk_seg_len = 0, pk_nseg = 0;
     std::vector<double> counts;
     std::vector<double> fish_disc;   // [nb][nell][nell]
@@ -136,6 +162,8 @@ struct polybin_ctx {
     std::vector<int> trip;
     std::vector<double> Tabc, Nabc;
     double* d_S = nullptr;
+    double* d_B = nullptr;       // normalised bispectrum of the last field
+    double* d_T = nullptr;       // T_abc (data grid)
     int* d_trip_m = nullptr;
     // tensor-core contraction plans
     void* tc = nullptr;
@@ -153,6 +181,8 @@ struct polybin_ctx {
     int tused = 0;        // slots recorded since the last read-back
     bool topen = false;   // a stage bracket is open (brackets do not nest)
 
+    // the contraction kernel that ran last (polybin_contract_path values), -1 before the first contraction
+    int last_path = -1;
     // device error flag of the kernels with bounded waits
     int* d_err = nullptr;
     // stream capture in progress: kernels are enqueued without host synchronisation or read-backs

@@ -438,7 +438,7 @@ static int pk_fisher_draw(polybin_ctx* ctx, const float* n, const float* w, unsi
     std::vector<double> cross;
     T* q = (T*)u->g2;
     for (int il = 0; il < nell; ++il) {
-        if ((rc = run_shells<T>(ctx, SA, (C<T>*)W.u1, (C<T>*)W.u2, q, 2 * il))) return rc;
+        if ((rc = run_shells<T>(ctx, SA, (C<T>*)W.u1, (C<T>*)W.u2, q, 2 * il, ctx->fg))) return rc;
         for (int b = 0; b < nb; ++b) {
             C<T>* X = (C<T>*)u->spec[2];
             if ((rc = run_forward<T, T, float>(ctx, q + (size_t)b * N, w, n, (C<T>*)W.t1, (C<T>*)W.t2, X))) return rc;
@@ -463,7 +463,7 @@ static int pair_spectra(polybin_ctx* ctx, const C<T>* U, C<T>* out) {
     const int nb = ctx->nb;
     int rc;
     T* g = (T*)u->g2;
-    if ((rc = run_shells<T>(ctx, U, (C<T>*)W.u1, (C<T>*)W.u2, g, 0))) return rc;
+    if ((rc = run_shells<T>(ctx, U, (C<T>*)W.u1, (C<T>*)W.u2, g, 0, ctx->fg))) return rc;
     int p = 0;
     for (int x = 0; x < nb; ++x)
         for (int y = x; y < nb; ++y, ++p)
@@ -756,27 +756,31 @@ static int bk_unwindowed_t(polybin_ctx* ctx, const float* d, const float* w, con
     const long N = ctx->ncell;
     const int nb = ctx->nb, np = nb * (nb + 1) / 2;
     const int nt = (int)ctx->Nabc.size();
-    // u = w d -> g[u] (kept in W.g)
+    // u = w d -> g[u] (kept in W.g), on the contraction grid: every sum below is cg_ratio times its value there
+    const double rho = ctx->cg_ratio;
+    const long cn = ctx->cg.ncell;
     if ((rc = run_forward<T, float, float>(ctx, d, w, (const float*)nullptr, (C<T>*)W.t1, (C<T>*)W.t2, (C<T>*)W.box))) return rc;
-    if ((rc = run_shells<T>(ctx, (const C<T>*)W.box, (C<T>*)W.u1, (C<T>*)W.u2, (T*)W.g, 0))) return rc;
+    if ((rc = run_shells<T>(ctx, (const C<T>*)W.box, (C<T>*)W.u1, (C<T>*)W.u2, (T*)W.g, 0, ctx->cg))) return rc;
     std::vector<double> S(std::max(nt, 1), 0.0), lin(nt, 0.0), Mv((size_t)np * nb);
     if (nt > 0) {
         if ((rc = run_triplet_sums<T>(ctx, (const T*)W.g, ctx->d_S))) return rc;
         PB_CUDA_OK(cudaMemcpyAsync(S.data(), ctx->d_S, sizeof(double) * nt, cudaMemcpyDeviceToHost, ctx->stream));
         PB_CUDA_OK(cudaStreamSynchronize(ctx->stream));
+        for (int t = 0; t < nt; ++t) S[t] *= rho;
     }
     for (int i = 0; i < n_mocks; ++i) {
         const float* mock = mocks + (size_t)i * N;
         if ((rc = run_forward<T, float, float>(ctx, mock, w, (const float*)nullptr, (C<T>*)W.t1, (C<T>*)W.t2, (C<T>*)W.box))) return rc;
-        if ((rc = run_shells<T>(ctx, (const C<T>*)W.box, (C<T>*)W.u1, (C<T>*)W.u2, (T*)u->g2, 0))) return rc;
+        if ((rc = run_shells<T>(ctx, (const C<T>*)W.box, (C<T>*)W.u1, (C<T>*)W.u2, (T*)u->g2, 0, ctx->cg))) return rc;
         // M[(j<=k) over v][i over u] = sum_x g_j[v] g_k[v] g_i[u]
-        if ((rc = run_contract_any<T>(ctx, (const T*)u->g2, nb, (const T*)W.g, nb, W.partial, W.partial_cap, W.mout))) return rc;
+        if ((rc = run_contract_any<T>(ctx, (const T*)u->g2, nb, (const T*)W.g, nb, W.partial, W.partial_cap, W.mout, cn)))
+            return rc;
         PB_CUDA_OK(cudaMemcpyAsync(Mv.data(), W.mout, sizeof(double) * Mv.size(), cudaMemcpyDeviceToHost, ctx->stream));
         PB_CUDA_OK(cudaStreamSynchronize(ctx->stream));
         for (int t = 0; t < nt; ++t) {
             const int a = ctx->trip[3 * t], b = ctx->trip[3 * t + 1], c = ctx->trip[3 * t + 2];
-            lin[t] += Mv[(size_t)pair_index(nb, b, c) * nb + a] + Mv[(size_t)pair_index(nb, a, c) * nb + b] +
-                      Mv[(size_t)pair_index(nb, a, b) * nb + c];
+            lin[t] += rho * (Mv[(size_t)pair_index(nb, b, c) * nb + a] + Mv[(size_t)pair_index(nb, a, c) * nb + b] +
+                             Mv[(size_t)pair_index(nb, a, b) * nb + c]);
         }
     }
     std::vector<double> bnum(nt);

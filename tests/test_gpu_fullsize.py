@@ -1,11 +1,14 @@
-"""Full-size parity on sampled outputs, in the launch configuration the benchmark times.
+"""Full-size parity in the launch configuration the benchmark times, against the FP64 oracle.
 
-* 512^3 lognormal + Kaiser field, 30 bins to 0.3 h/Mpc, split-TF32 path (the benchmark default): every N_abc of a
-  sample of triplets equals the oracle's exactly; B_abc of the sample within 1e-6 relative wherever
-  kappa <= 10 and 1e-6 of sum|g g g| everywhere; P_0, P_2 of every bin within 1e-6 of P_0.
+* 256^3 lognormal field, 20 bins to 0.2 h/Mpc, split-TF32 path: EVERY one of the closed triplets.
+* 512^3 lognormal + Kaiser field, 30 bins to 0.3 h/Mpc, split-TF32 path (the benchmark default): every closed
+  triplet among 9 of the 30 bins (first, last and seven spread between; the oracle's 512^3 FP64 maps take ~1 GB
+  each), N_abc exact, and P_0, P_2 of every bin.
+Bispectrum criterion (tests/bk_criterion.py): e_norm <= 1e-6 for every triplet, e_rel <= 1e-6 for every triplet
+with kappa <= 10, and every triplet above 1e-6 listed with its kappa.
 * 256^3 masked workload (shell with holes, FKP weights, 24 P bins x ell 0,2,4, 16 B bins): the full P Fisher term
   of one draw, and a sampled block of the B Fisher term of one draw pair, within 1e-6 of sqrt(F_aa F_bb).
-The oracle computes only the maps these samples need (FP64, all host cores).
+The oracle computes only the maps these checks need (FP64, all host cores).
 """
 import numpy as np
 import pytest
@@ -14,6 +17,8 @@ torch = pytest.importorskip("torch")
 
 from oracle import _fft, binning, ideal, unwindowed
 from paper_2404_07249_gb300 import synth
+
+from bk_criterion import bk_errors, check, report
 
 pytestmark = pytest.mark.gpu
 
@@ -27,40 +32,76 @@ def pkg():
     return pkg
 
 
-def test_config3_sampled_bispectrum_and_pk(pkg):
+def test_config2_every_triplet(pkg):
+    w = synth.WORKLOADS[2]
+    grid, box, edges = w.grid, w.box, w.bk_edges
+    field = synth.workload_field(2, 0)
+    pb = pkg.PolyBin(grid, box, edges, prec="split")
+    B = pb.bk_ideal(torch.from_numpy(field).cuda())[0]
+    assert pb.last_path() == pkg.PATH_TENSOR_SPLIT_TF32X3
+    abc, nabc = pb.triplets()
+    cgrid = pb.contraction_grid()
+    pb.close()
+    ref = ideal.bk_ideal(field, box, edges)
+    trip = [tuple(t) for t in abc.tolist()]
+    assert trip == ref["triplets"]
+    assert np.array_equal(nabc, ref["N_abc"])
+    nb = len(edges) - 1
+    bins = binning.bin_grid(grid, box, edges)
+    g = ideal.shell_maps(ideal.forward(field), bins, nb)
+    absS_full = ideal.triple_sums(np.abs(g))
+    absS = np.array([absS_full[a, b, c] for a, b, c in trip])
+    e_rel, e_norm, kappa = bk_errors(B, ref["B"], ref["S"], absS)
+    s = check(trip, e_rel, e_norm, kappa, label="256^3 all triplets")
+    print(report(s, f"256^3, 20 bins, split, contraction grid {cgrid}"))
+
+
+def _subset_triplets(trip, keep):
+    return [i for i, t in enumerate(trip) if set(t) <= keep]
+
+
+def test_config3_bispectrum_subset_and_pk(pkg):
     w = synth.WORKLOADS[3]
     grid, box, edges = w.grid, w.box, w.bk_edges
     field = synth.workload_field(3, 0)
     pb = pkg.PolyBin(grid, box, edges, lmax=2, prec="split")
     B, P = pb.bk_pk(torch.from_numpy(field).cuda())
+    assert pb.last_path() == pkg.PATH_TENSOR_SPLIT_TF32X3
     abc, nabc = pb.triplets()
+    cgrid = pb.contraction_grid()
     pb.close()
     B, P = B[0], P[0]
     trip = [tuple(t) for t in abc.tolist()]
     N = field.size
     vol = box ** 3
-    # sample: first, last, all-equal, two-equal and a few spread out
-    pick = sorted({0, len(trip) - 1, trip.index((0, 0, 0)) if (0, 0, 0) in trip else 0,
-                   len(trip) // 7, len(trip) // 3, len(trip) // 2, (2 * len(trip)) // 3})
+    keep = {0, 1, 4, 9, 14, 19, 24, 27, 29}
+    pick = _subset_triplets(trip, keep)
+    assert len(pick) > 80
     D = ideal.forward(field)
     bins = binning.bin_grid(grid, box, edges).astype(np.int16)
-    need = sorted({b for i in pick for b in trip[i]})
     g, t = {}, {}
-    for b in need:
+    for b in sorted(keep):
         sel = bins == b
         g[b] = _fft.ifftn(np.where(sel, D, 0.0)).real
         t[b] = _fft.ifftn(sel.astype(np.complex128)).real
-    for i in pick:
-        a, b, c = trip[i]
-        S = np.sum(g[a] * g[b] * g[c])
-        T = np.sum(t[a] * t[b] * t[c])
-        absS = np.sum(np.abs(g[a] * g[b] * g[c]))
-        assert np.rint(N * N * T) == nabc[i], (trip[i], N * N * T, nabc[i])
-        Bref = vol * vol / float(N) ** 3 * S / T
-        e_norm = abs(B[i] - Bref) / (vol * vol / float(N) ** 3 * absS / T)
-        assert e_norm < 1e-6, (trip[i], e_norm)
-        if absS / abs(S) <= 10:
-            assert abs(B[i] - Bref) / abs(Bref) < 1e-6, (trip[i], B[i], Bref)
+    # one pair product per (b, c), dotted with every single a it closes with
+    S, T, absS = np.zeros(len(pick)), np.zeros(len(pick)), np.zeros(len(pick))
+    by_pair = {}
+    for q, i in enumerate(pick):
+        by_pair.setdefault(trip[i][1:], []).append((q, trip[i][0]))
+    for (b, c), items in by_pair.items():
+        pg, pt = (g[b] * g[c]).ravel(), (t[b] * t[c]).ravel()
+        pa = np.abs(pg)
+        for q, a in items:
+            S[q] = np.dot(g[a].ravel(), pg)
+            T[q] = np.dot(t[a].ravel(), pt)
+            absS[q] = np.dot(np.abs(g[a]).ravel(), pa)
+        del pg, pt, pa
+    assert np.array_equal(np.rint(N * N * T), nabc[pick])
+    Bref = vol * vol / float(N) ** 3 * S / T
+    e_rel, e_norm, kappa = bk_errors(B[pick], Bref, S, absS)
+    s = check([trip[i] for i in pick], e_rel, e_norm, kappa, label="512^3 subset")
+    print(report(s, f"512^3, 30 bins, split, bins {sorted(keep)}, contraction grid {cgrid}"))
     del g, t
     # P_ell over every bin (ell = 0, 2)
     pw = np.abs(D) ** 2
