@@ -36,7 +36,15 @@ def _stale(target, deps):
 
 
 def build(verbose: bool = False, force: bool = False, extra_flags=()) -> str:
+    """Compile stale translation units and link.  Extra nvcc flags (argument, or the POLYBIN_NVCC_FLAGS environment
+    variable) are recorded in a stamp file: a change of flags rebuilds everything."""
+    extra_flags = tuple(extra_flags) + tuple(f for f in os.environ.get("POLYBIN_NVCC_FLAGS", "").split() if f)
     os.makedirs(BUILD, exist_ok=True)
+    stamp = os.path.join(BUILD, "flags.txt")
+    want = " ".join(extra_flags)
+    have = open(stamp).read() if os.path.exists(stamp) else None
+    if have != want:
+        force = True
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     headers.append(os.path.join(ROOT, "include", "polybin.h"))
     srcs = sources()
@@ -65,6 +73,8 @@ def build(verbose: bool = False, force: bool = False, extra_flags=()) -> str:
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+    with open(stamp, "w") as f:
+        f.write(want)
     return LIB
 
 

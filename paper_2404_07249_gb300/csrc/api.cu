@@ -73,17 +73,9 @@ static int launch_check(polybin_ctx* ctx, const char* what) {
     return POLYBIN_OK;
 }
 
-// Lines per CTA of the z-passes and columns per CTA of the strided passes, sized for ~64-96 KB of smem.
-template <typename T> static int lines_per_cta(int n) {
-    int lp = 16;
-    while (lp > 1 && 2 * (size_t)n * (lp + 1) * sizeof(C<T>) > 96 * 1024) lp >>= 1;
-    return lp;
-}
-template <typename T> static int cols_per_cta(int n) {
-    int tk = 16;
-    while (tk > 1 && 2 * (size_t)n * tk * sizeof(C<T>) > 64 * 1024) tk >>= 1;
-    return tk;
-}
+// Lines per CTA of the z-passes and columns per CTA of the strided passes (the kernels' compile-time choice).
+template <typename T> static int lines_per_cta(int n) { return lines_per_cta_of<T>(n); }
+template <typename T> static int cols_per_cta(int n) { return cols_per_cta_of<T>(n); }
 
 template <typename T> static const C<T>* twiddles(polybin_ctx* ctx, int axis);
 template <> const float2* twiddles<float>(polybin_ctx* ctx, int axis) { return (const float2*)ctx->d_tw_f[axis]; }
@@ -480,9 +472,9 @@ int alloc_work(polybin_ctx* ctx, Work& w) {
     PB_CUDA_OK_C(cudaMalloc(&w.t1, sizeof(C<T>) * N0 * N1 * Bz));
     PB_CUDA_OK_C(cudaMalloc(&w.t2, sizeof(C<T>) * N0 * By * Bz));
     PB_CUDA_OK_C(cudaMalloc(&w.box, sizeof(C<T>) * Bx * By * Bz));
-    PB_CUDA_OK_C(cudaMalloc(&w.u1, sizeof(C<T>) * std::max(ctx->fg.u1_total, ctx->cg.u1_total)));
-    PB_CUDA_OK_C(cudaMalloc(&w.u2, sizeof(C<T>) * std::max(ctx->fg.u2_total, ctx->cg.u2_total)));
-    PB_CUDA_OK_C(cudaMalloc(&w.g, sizeof(T) * (size_t)ctx->nb * ctx->ncell));
+    PB_CUDA_OK_C(cudaMalloc(&w.u1, sizeof(C<T>) * ctx->cg.u1_total));
+    PB_CUDA_OK_C(cudaMalloc(&w.u2, sizeof(C<T>) * ctx->cg.u2_total));
+    PB_CUDA_OK_C(cudaMalloc(&w.g, sizeof(T) * (size_t)ctx->nb * ctx->cg.ncell));
     const int np = 64 * 65 / 2;
     ContractGeom G = contract_geom(std::max(ctx->nb, 1), std::max(ctx->nb, 1), ctx->ncell);
     w.partial_cap = (size_t)G.ncb * G.npairs * G.nh;
@@ -494,8 +486,19 @@ int alloc_work(polybin_ctx* ctx, Work& w) {
     return POLYBIN_OK;
 }
 
+template <typename T>
+int ensure_fine_inv(polybin_ctx* ctx) {
+    Work& w = ctx->w;
+    if (w.u1f && w.u2f) return POLYBIN_OK;
+    PB_CUDA_OK(cudaMalloc(&w.u1f, sizeof(C<T>) * ctx->fg.u1_total));
+    PB_CUDA_OK(cudaMalloc(&w.u2f, sizeof(C<T>) * ctx->fg.u2_total));
+    return POLYBIN_OK;
+}
+template int ensure_fine_inv<float>(polybin_ctx*);
+template int ensure_fine_inv<double>(polybin_ctx*);
+
 void free_work(Work& w) {
-    void* ptrs[] = {w.t1, w.t2, w.box, w.u1, w.u2, w.g, w.partial, w.mout};
+    void* ptrs[] = {w.t1, w.t2, w.box, w.u1, w.u2, w.u1f, w.u2f, w.g, w.partial, w.mout};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     w = Work();
@@ -815,10 +818,13 @@ extern "C" int polybin_shell_maps(polybin_ctx* ctx, const void* spec, void* g_ou
     if (!ctx || !spec || !g_out) return fail(ctx, POLYBIN_EINVAL, "polybin_shell_maps: NULL argument");
     int rc;
     Work& w = ctx->w;
-    if (ctx->prec == POLYBIN_FP64)
-        rc = run_shells<double>(ctx, (const double2*)spec, (double2*)w.u1, (double2*)w.u2, (double*)g_out, 0, ctx->fg);
-    else
-        rc = run_shells<float>(ctx, (const float2*)spec, (float2*)w.u1, (float2*)w.u2, (float*)g_out, 0, ctx->fg);
+    if (ctx->prec == POLYBIN_FP64) {
+        if ((rc = ensure_fine_inv<double>(ctx))) return rc;
+        rc = run_shells<double>(ctx, (const double2*)spec, (double2*)w.u1f, (double2*)w.u2f, (double*)g_out, 0, ctx->fg);
+    } else {
+        if ((rc = ensure_fine_inv<float>(ctx))) return rc;
+        rc = run_shells<float>(ctx, (const float2*)spec, (float2*)w.u1f, (float2*)w.u2f, (float*)g_out, 0, ctx->fg);
+    }
     if (rc) return rc;
     PB_CUDA_OK(cudaStreamSynchronize(ctx->stream));
     return POLYBIN_OK;

@@ -153,14 +153,22 @@ __device__ C<T>* fft_lines(C<T>* src, C<T>* dst, int L, int ES, const FftPlan& p
 // Compile-time specialisation for the lengths listed in PB_WITH_NT: radices, strides and line counts are
 // constants, so the index arithmetic folds and every radix loop is fully unrolled.  The radix order is that of
 // make_plan (8s, then 4, 2, 3s, 5s).
+// Shared-memory budgets of the staged passes (ping-pong buffers of one CTA): they set the lines a z-pass CTA and
+// the columns a strided-pass CTA transform, and with them how many CTAs an SM holds.
+#ifndef PB_LINES_SMEM
+#define PB_LINES_SMEM (48 * 1024)
+#endif
+#ifndef PB_COLS_SMEM
+#define PB_COLS_SMEM (64 * 1024)
+#endif
 template <typename T> __host__ __device__ constexpr int lines_per_cta_of(int n) {
     int lp = 16;
-    while (lp > 1 && 2 * (long)n * (lp + 1) * (long)sizeof(C<T>) > 96 * 1024) lp >>= 1;
+    while (lp > 1 && 2 * (long)n * (lp + 1) * (long)sizeof(C<T>) > PB_LINES_SMEM) lp >>= 1;
     return lp;
 }
 template <typename T> __host__ __device__ constexpr int cols_per_cta_of(int n) {
     int tk = 16;
-    while (tk > 1 && 2 * (long)n * tk * (long)sizeof(C<T>) > 64 * 1024) tk >>= 1;
+    while (tk > 1 && 2 * (long)n * tk * (long)sizeof(C<T>) > PB_COLS_SMEM) tk >>= 1;
     return tk;
 }
 __host__ __device__ constexpr int ct_next_radix(int m) {

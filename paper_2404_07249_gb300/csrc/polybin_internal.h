@@ -41,9 +41,11 @@ struct Work {
     void* t1 = nullptr;      // forward z-pass output [N0*N1][Bz]
     void* t2 = nullptr;      // forward y-pass output [N0][By][Bz]
     void* box = nullptr;     // pruned spectrum [Bx][By][Bz]
-    void* u1 = nullptr;      // inverse x-pass outputs, all bins
-    void* u2 = nullptr;      // inverse y-pass outputs, all bins
-    void* g = nullptr;       // shell maps [nb][N]
+    void* u1 = nullptr;      // inverse x-pass outputs, all bins (contraction grid)
+    void* u2 = nullptr;      // inverse y-pass outputs, all bins (contraction grid)
+    void* u1f = nullptr;     // the same on the data grid, allocated on first use (ensure_fine_inv)
+    void* u2f = nullptr;
+    void* g = nullptr;       // shell maps [nb][cg.ncell] on the contraction grid
     double* partial = nullptr;
     size_t partial_cap = 0;
     double* mout = nullptr;  // contraction result [npairs][nh]
@@ -90,6 +92,8 @@ template <typename T> int run_contract(polybin_ctx*, const T*, int, const T*, in
 // Contraction dispatch: the tensor-core kernel in POLYBIN_SPLIT_TF32X3 mode, the SIMT kernel otherwise.
 template <typename T> int run_contract_any(polybin_ctx*, const T*, int, const T*, int, double*, size_t, double*, long ncell);
 template <typename T> int alloc_work(polybin_ctx*, Work&);
+// Data-grid intermediates of the inverse transforms (ctx->w.u1f, u2f), allocated on first use.
+template <typename T> int ensure_fine_inv(polybin_ctx*);
 int alloc_work_shells_double(polybin_ctx*, Work&);
 void free_work(Work&);
 int resolve_input(polybin_ctx*, const float*, size_t, const float**);

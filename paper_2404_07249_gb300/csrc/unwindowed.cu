@@ -438,7 +438,8 @@ static int pk_fisher_draw(polybin_ctx* ctx, const float* n, const float* w, unsi
     std::vector<double> cross;
     T* q = (T*)u->g2;
     for (int il = 0; il < nell; ++il) {
-        if ((rc = run_shells<T>(ctx, SA, (C<T>*)W.u1, (C<T>*)W.u2, q, 2 * il, ctx->fg))) return rc;
+        if ((rc = ensure_fine_inv<T>(ctx))) return rc;
+        if ((rc = run_shells<T>(ctx, SA, (C<T>*)W.u1f, (C<T>*)W.u2f, q, 2 * il, ctx->fg))) return rc;
         for (int b = 0; b < nb; ++b) {
             C<T>* X = (C<T>*)u->spec[2];
             if ((rc = run_forward<T, T, float>(ctx, q + (size_t)b * N, w, n, (C<T>*)W.t1, (C<T>*)W.t2, X))) return rc;
@@ -463,7 +464,8 @@ static int pair_spectra(polybin_ctx* ctx, const C<T>* U, C<T>* out) {
     const int nb = ctx->nb;
     int rc;
     T* g = (T*)u->g2;
-    if ((rc = run_shells<T>(ctx, U, (C<T>*)W.u1, (C<T>*)W.u2, g, 0, ctx->fg))) return rc;
+    if ((rc = ensure_fine_inv<T>(ctx))) return rc;
+    if ((rc = run_shells<T>(ctx, U, (C<T>*)W.u1f, (C<T>*)W.u2f, g, 0, ctx->fg))) return rc;
     int p = 0;
     for (int x = 0; x < nb; ++x)
         for (int y = x; y < nb; ++y, ++p)
