@@ -204,6 +204,14 @@ int run_shells(polybin_ctx* ctx, const C<T>* box, C<T>* u1, C<T>* u2, T* g, int 
             const int lpc = 16;
             dim3 grid512((unsigned)(((nlines + 1) / 2 + lpc - 1) / lpc), nb, 1);
             k_inv_z512<T><<<grid512, 256, 0, ctx->stream>>>(b, nlines, T(1), (const T*)nullptr, tw(2), lpc);
+        } else if (N2 == 288 && sizeof(T) == 4) {
+            // register-resident 288-point transform, 128 line pairs per CTA (8 rounds of 16, input staged with
+            // cp.async one round ahead)
+            const int ppc = 128;
+            dim3 grid288((unsigned)(((nlines + 1) / 2 + ppc - 1) / ppc), nb, 1);
+            if ((rc = set_smem<T>(ctx, (const void*)k_inv_z288, kZ288Smem))) return rc;
+            k_inv_z288<<<grid288, kZ288Threads, kZ288Smem, ctx->stream>>>(b, nlines, 1.f, (const float*)nullptr,
+                                                                         (const float2*)tw(2), ppc);
         } else {
             dim3 grid((unsigned)((nlines + 2 * LP - 1) / (2 * LP)), nb, 1);
             PB_WITH_NT_INV(N2, NT, {

@@ -475,6 +475,218 @@ __global__ void __launch_bounds__(256) k_inv_z512(ZInvBatch batch, long nlines, 
 }
 
 // ------------------------------------------------------------------------------------------------
+// z-pass, inverse (C2R), length 288 = 12 x 24, register-resident: the same result as k_inv_z (packing of line pairs,
+// kz = 0 and n/2 treatment) as a two-stage Cooley-Tukey transform.  With k = t + 12 j and n = n1 + 24 n2,
+//   z[n1 + 24 n2] = sum_t w12^(t n2) [ w288^(t n1) sum_j Z[t + 12 j] w24^(j n1) ]      (w_m = e^{+2 pi i / m}),
+// so a group of 12 threads transforms one packed line pair: thread t takes the 24-point DFT over j of its points
+// (in registers, as 3 x 8) and the twiddles w288^(t n1) (read once per thread from the table and kept in registers),
+// the groups exchange through shared memory, and thread t takes the 12-point DFTs (as 3 x 4) of rows n1 = t and
+// t + 12; a last exchange through shared memory makes the two real output lines coalesced (16-byte stores).  A CTA
+// of 192 threads takes 16 line pairs per round and `ppc` line pairs of one item (blockIdx.y) in all.
+
+// e^{i m pi / 12} for m = 0 .. 14 (multiples of 15 degrees; closed forms of cos / sin 15, 30, 45 degrees)
+__host__ __device__ constexpr double root24_re(int m) {
+    constexpr double c15 = 0.96592582628906829, s15 = 0.25881904510252076, c30 = 0.86602540378443865,
+                     c45 = 0.70710678118654752;
+    constexpr double t[15] = {1.0, c15, c30, c45, 0.5, s15, 0.0, -s15, -0.5, -c45, -c30, -c15, -1.0, -c15, -c30};
+    return t[m];
+}
+__host__ __device__ constexpr double root24_im(int m) {
+    constexpr double c15 = 0.96592582628906829, s15 = 0.25881904510252076, c30 = 0.86602540378443865,
+                     c45 = 0.70710678118654752;
+    constexpr double t[15] = {0.0, s15, 0.5, c45, c30, c15, 1.0, c15, c30, c45, 0.5, s15, 0.0, -s15, -0.5};
+    return t[m];
+}
+// a * e^{DIR 2 pi i m / 24}
+template <typename T, int DIR>
+__device__ __forceinline__ C<T> rot24(C<T> a, int m) {
+    const T c = T(root24_re(m)), s = T(DIR * root24_im(m));
+    return mk<T>(a.x * c - a.y * s, a.x * s + a.y * c);
+}
+
+// X[n] = sum_j x[j] e^{DIR 2 pi i j n / 24}, natural order in and out: j = 3a + b, n = c + 8d.
+template <typename T, int DIR>
+__device__ __forceinline__ void dft24(C<T>* x) {
+    C<T> A[3][8];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+#pragma unroll
+        for (int a = 0; a < 8; ++a) A[b][a] = x[3 * a + b];
+        dft<T, DIR>(A[b], 8);
+    }
+#pragma unroll
+    for (int b = 1; b < 3; ++b)
+#pragma unroll
+        for (int c = 1; c < 8; ++c) A[b][c] = rot24<T, DIR>(A[b][c], b * c);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        C<T> y[3] = {A[0][c], A[1][c], A[2][c]};
+        dft<T, DIR>(y, 3);
+        x[c] = y[0];
+        x[c + 8] = y[1];
+        x[c + 16] = y[2];
+    }
+}
+
+// X[n] = sum_j x[j] e^{DIR 2 pi i j n / 12}, natural order: j = 3a + b, n = c + 4d (w12^m = w24^(2m)).
+template <typename T, int DIR>
+__device__ __forceinline__ void dft12(C<T>* x) {
+    C<T> A[3][4];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a) A[b][a] = x[3 * a + b];
+        dft<T, DIR>(A[b], 4);
+    }
+#pragma unroll
+    for (int b = 1; b < 3; ++b)
+#pragma unroll
+        for (int c = 1; c < 4; ++c) A[b][c] = rot24<T, DIR>(A[b][c], 2 * b * c);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        C<T> y[3] = {A[0][c], A[1][c], A[2][c]};
+        dft<T, DIR>(y, 3);
+        x[c] = y[0];
+        x[c + 4] = y[1];
+        x[c + 8] = y[2];
+    }
+}
+
+// 16-byte and 8-byte asynchronous global -> shared copies (cp.async; completion by commit / wait_group).
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Copies the `bytes` (a multiple of 8) at src to dst with the CTA's threads: 16-byte pieces, then an 8-byte tail.
+__device__ __forceinline__ void stage_block(unsigned char* dst, const unsigned char* src, long bytes, int tid, int nthr) {
+    const long n16 = bytes >> 4;
+    for (long i = tid; i < n16; i += nthr) cp_async16(dst + 16 * i, src + 16 * i);
+    if ((bytes & 15) && tid == 0) cp_async8(dst + 16 * n16, src + 16 * n16);
+    cp_async_commit();
+}
+
+constexpr int kZ288Threads = 192, kZ288Pairs = 16, kZ288Kmax = 145;
+constexpr int kZ288Rs = 13, kZ288Gs = 24 * kZ288Rs;
+// dynamic shared memory: exchange buffers [16][24 x 13] float2, input stage [32 lines][<= 145] float2
+constexpr size_t kZ288Smem = (size_t)(kZ288Pairs * kZ288Gs + 2 * kZ288Pairs * kZ288Kmax) * sizeof(float2);
+
+static __global__ void __launch_bounds__(192) k_inv_z288(ZInvBatch batch, long nlines, float scale,
+                                                        const float* __restrict__ mulout, const float2* __restrict__ twg,
+                                                        int ppc) {
+    constexpr int N = 288, TG = 12, P = 24, G = kZ288Pairs, RS = kZ288Rs, GS = kZ288Gs;
+    extern __shared__ __align__(16) float2 z288_smem[];
+    float2* sbuf = z288_smem;                         // exchange buffers
+    float2* stage = z288_smem + G * GS;               // the round's input lines, [2 G][kin]
+    const ZInvItem item = batch.it[blockIdx.y];
+    const float2* __restrict__ in = static_cast<const float2*>(item.in);
+    float* __restrict__ out = static_cast<float*>(item.out);
+    const int kin = item.kin;                         // <= 145 (the Hermitian half of 288 points)
+    const int tid = threadIdx.x, g = tid / TG, t = tid - g * TG;
+    float2* buf = sbuf + g * GS;
+    // stage-1 twiddles w288^(t n1) = conj(tw[t n1 mod N])
+    float2 w1[P];
+#pragma unroll
+    for (int n1 = 1; n1 < P; ++n1) {
+        const float2 w = twg[(t * n1) % N];
+        w1[n1] = make_float2(w.x, -w.y);
+    }
+    const long npairs = (nlines + 1) / 2;
+    const long p_beg = (long)blockIdx.x * ppc;
+    const long p_end = min(npairs, p_beg + ppc);
+    // the input lines of the round starting at pair q: lines 2q .. min(2 (q + G), nlines) - 1, contiguous
+    auto issue = [&](long q) {
+        const long l0 = 2 * q, l1 = min(2 * min(q + G, p_end), nlines);
+        stage_block(reinterpret_cast<unsigned char*>(stage), reinterpret_cast<const unsigned char*>(in + l0 * kin),
+                    (l1 - l0) * kin * (long)sizeof(float2), tid, kZ288Threads);
+    };
+    if (p_beg < p_end) issue(p_beg);
+    for (long p0 = p_beg; p0 < p_end; p0 += G) {
+        const long p = p0 + g;
+        const bool act = p < p_end;
+        cp_async_wait_all();
+        __syncthreads();                              // the round's lines are in `stage`
+        float2 v[P];
+        {
+            const bool has2 = act && 2 * p + 1 < nlines;
+            const float2* in1 = stage + (2 * g) * kin;
+            const float2* in2 = in1 + kin;
+#pragma unroll
+            for (int j = 0; j < P; ++j) {
+                const int k = t + TG * j;
+                float2 z = make_float2(0.f, 0.f);
+                if (act) {
+                    if (k == 0 || 2 * k == N) {
+                        if (k < kin) z = make_float2(in1[k].x, has2 ? in2[k].x : 0.f);
+                    } else if (k < kin) {
+                        const float2 a = in1[k];
+                        const float2 b = has2 ? in2[k] : make_float2(0.f, 0.f);
+                        z = make_float2(a.x - b.y, a.y + b.x);
+                    } else if (N - k < kin) {
+                        const float2 a = in1[N - k];
+                        const float2 b = has2 ? in2[N - k] : make_float2(0.f, 0.f);
+                        z = make_float2(a.x + b.y, b.x - a.y);
+                    }
+                }
+                v[j] = z;
+            }
+        }
+        __syncthreads();                              // every thread has its points: refill `stage`
+        if (p0 + G < p_end) issue(p0 + G);
+        // stage 1: 24-point DFT over j, twiddle w288^(t n1); rows n1 of the group's exchange buffer
+        dft24<float, +1>(v);
+#pragma unroll
+        for (int n1 = 1; n1 < P; ++n1) v[n1] = mul<float>(v[n1], w1[n1]);
+#pragma unroll
+        for (int n1 = 0; n1 < P; ++n1) buf[n1 * RS + t] = v[n1];
+        __syncthreads();
+        // stage 2: 12-point DFTs over t of rows n1 = t and t + 12
+        float2 o[2][TG];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+#pragma unroll
+            for (int u = 0; u < TG; ++u) o[h][u] = buf[(t + 12 * h) * RS + u];
+            dft12<float, +1>(o[h]);
+        }
+        __syncthreads();
+        // outputs: z[n1 + 24 n2] -> real parts to line 2p, imaginary parts to line 2p + 1 (staged for coalescing)
+        float* re = reinterpret_cast<float*>(buf);
+        float* im = re + N;
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int n2 = 0; n2 < TG; ++n2) {
+                const int n = t + 12 * h + 24 * n2;
+                re[n] = o[h][n2].x * scale;
+                im[n] = o[h][n2].y * scale;
+            }
+        __syncthreads();
+        constexpr int Q = N / 4;                         // float4 per line
+        for (int q = tid; q < G * 2 * Q; q += kZ288Threads) {
+            const int gg = q / (2 * Q), r = q - gg * 2 * Q;
+            const int side = r / Q, e4 = r - side * Q;
+            const long pp = p0 + gg;
+            const long l = 2 * pp + side;
+            if (pp >= p_end || l >= nlines) continue;
+            float4 a = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(sbuf + gg * GS) + side * N + 4 * e4);
+            if (mulout) {
+                const float* m = mulout + l * N + 4 * e4;
+                a.x *= m[0]; a.y *= m[1]; a.z *= m[2]; a.w *= m[3];
+            }
+            *reinterpret_cast<float4*>(out + l * N + 4 * e4) = a;
+        }
+        // (the next round's first __syncthreads orders these reads of sbuf before its writes)
+    }
+    cp_async_wait_all();
+}
+
+// ------------------------------------------------------------------------------------------------
 // Strided column pass (y or x axis).  Each CTA transforms TK consecutive columns of one outer slab.
 //   forward (DIR = -1): input positions 0..n-1 at in[o*in_os + i*in_es + c]; keeps wave numbers
 //                       f in out_rng, stored at out[o*out_os + (f - lo)*out_es + c].

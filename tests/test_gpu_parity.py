@@ -50,6 +50,8 @@ CASES = [
     ((16, 16, 16), 500.0, np.array([0.5, 3.0, 6.0, 9.5, 14.0]), "lognormal"),  # bins beyond Nyquist (full axes)
     ((16, 8, 512), 2000.0, 1.0 + 6.0 * np.arange(8), "lognormal"),    # 512-point z lines, few z modes
     ((8, 4, 512), 2000.0, 1.0 + 40.0 * np.arange(8), "lognormal"),    # 512-point z lines up to the z Nyquist
+    ((8, 6, 288), 2000.0, 1.0 + 20.0 * np.arange(8), "lognormal"),    # 288-point z lines (register-resident pass)
+    ((8, 8, 512), 2000.0, 0.5 + 11.9375 * np.arange(9), "lognormal"), # m = 95: contraction grid 8 x 8 x 288
 ]
 
 
@@ -126,7 +128,7 @@ def test_contraction(pkg, prec, nh_same, shape):
 
 
 @pytest.mark.parametrize("prec", ["fp32", "split", "fp64"])
-@pytest.mark.parametrize("case", [0, 1, 3, 4])
+@pytest.mark.parametrize("case", [0, 1, 3, 4, 8])
 def test_bk_ideal_and_nabc(pkg, case, prec):
     grid, box, ek, kind = CASES[case]
     edges = _kf(box) * ek
