@@ -1,7 +1,8 @@
 """Ideal-limit estimators (oracle; FP64): uniform density, global line of sight, P_fid = nbar = m = 1.
 
 Sec. 3.4.1 (eq. pk-limit, eq. fish-ideal-continuous) for P_ell; Sec. 4.3.1 (eqs. beta-def, g-ell-def,
-N-ell-def) and Sec. 4.4.1 (eqs. bk-num-ideal, bk-fish-ideal2) for the bispectrum.
+N-ell-def) and Sec. 4.4.1 (eqs. bk-num-ideal, bk-fish-ideal2) for the bispectrum; Sec. 4.1 (eqs. Bk-Yam, ideal-bk)
+for its multipoles ell = 2, 4 about the global line of sight.
 
 Pixel convention: D = fftn(delta); IFT = ifftn (includes 1/N).  With V the box volume and N the number of
 cells, the physical outputs are
@@ -22,6 +23,16 @@ def forward(delta: np.ndarray) -> np.ndarray:
     """D(k) = sum_x e^{-i k.x} delta(x): the discrete form of the paper's FT (Sec. 1, Fourier conventions).
     The input is promoted to float64 exactly."""
     return _fft.fftn(np.asarray(delta, dtype=np.float64))
+
+
+def shell_maps_ell(D: np.ndarray, bins: np.ndarray, nb: int, ell: int, mu2: np.ndarray) -> np.ndarray:
+    """g_{b,ell}(x) = IFT[Theta_b L_ell(k.n) D](x) with the global line of sight n = z (Sec. 4.3.1, eq. g-ell-def,
+    distant-observer form; the conjugate is dropped as for ell = 0, see shell_maps)."""
+    L = binning.legendre(ell, mu2)
+    out = np.empty((nb,) + D.shape, dtype=np.float64)
+    for b in range(nb):
+        out[b] = _fft.ifftn(np.where(bins == b, L * D, 0.0)).real
+    return out
 
 
 def shell_maps(D: np.ndarray, bins: np.ndarray, nb: int, which=None) -> np.ndarray:
@@ -96,6 +107,38 @@ def bk_ideal(delta: np.ndarray, box: float, edges) -> dict:
     Nabc = np.rint(ncell * ncell * Tv)
     B = (vol * vol / float(ncell) ** 3) * Sv / Tv
     return {"triplets": trip, "S": Sv, "T": Tv, "N_abc": Nabc, "B": B, "S_full": S, "T_full": T}
+
+
+def bk_ideal_multipoles(delta: np.ndarray, box: float, edges, lmax: int) -> dict:
+    """Ideal bispectrum multipoles ell = 0, 2, .., lmax with a global line of sight (Sec. 4.1 eq. ideal-bk, which
+    defines b_alpha; Sec. 4.4.1 with the continuous Fisher of eq. bk-fish-ideal2, under which Delta_alpha cancels):
+
+        B_ell(a, b, c) = (2 ell + 1) (V^2 / N^3) S^ell_abc / T_abc,   S^ell_abc = sum_x g_a g_b g_{c,ell},
+
+    the Legendre weight L_ell(k3.n) on the mode of the third (largest) bin, T_abc and the closed triplets as in
+    bk_ideal (N_0 = N^2 T_abc).  Returns B[ell index][triplet] and the sums S[ell index][triplet]."""
+    grid = delta.shape
+    ncell = int(np.prod(grid))
+    vol = float(box) ** 3
+    nb = len(edges) - 1
+    ells = list(range(0, lmax + 1, 2))
+    bins = binning.bin_grid(grid, box, edges)
+    mu2 = binning.mu2_grid(grid)
+    D = forward(delta)
+    g = shell_maps(D, bins, nb)
+    T = triple_sums(unit_maps(bins, nb))
+    trip = closed_triplets(T, ncell)
+    Tv = np.array([T[a, b, c] for a, b, c in trip])
+    G = g.reshape(nb, -1)
+    S = np.zeros((len(ells), len(trip)))
+    for il, ell in enumerate(ells):
+        gl = g if ell == 0 else shell_maps_ell(D, bins, nb, ell, mu2)
+        GL = gl.reshape(nb, -1)
+        # M[a, b, c] = sum_x g_a g_b g_{c,ell}: for each a the matrix product (g_a * G) GL^T
+        for t, (a, b, c) in enumerate(trip):
+            S[il, t] = np.dot(G[a] * G[b], GL[c])
+    B = np.array([(2 * ell + 1) * (vol * vol / float(ncell) ** 3) * S[il] / Tv for il, ell in enumerate(ells)])
+    return {"triplets": trip, "ells": ells, "S": S, "T": Tv, "N_abc": np.rint(ncell * ncell * Tv), "B": B}
 
 
 def pk_ideal(delta: np.ndarray, box: float, edges, lmax: int) -> dict:

@@ -302,3 +302,47 @@ def test_fisher_solve_inverts():
     b = rng.standard_normal(40)
     x = unwindowed.solve(F, b)
     assert np.max(np.abs(F @ x - b)) < 1e-12
+
+
+@pytest.mark.parametrize("ell", [2, 4])
+def test_bispectrum_multipole_equals_brute_force_triangle_sum(ell):
+    """S^ell_abc = sum_x g_a g_b g_{c,ell} equals (1/N^2) sum over closed triangles (k1 in a, k2 in b, k3 in c) of
+    D(k1) D(k2) L_ell(k3.z) D(k3): the Legendre weight rides on the third mode (Sec. 4.1, eq. ideal-bk), which the
+    brute-force sum applies through its third spectrum L_ell D."""
+    grid, kf, edges = _cubic(16, 1000.0, [1, 2.5, 4, 5.5, 7.0])
+    f = synth.lognormal_field(grid, (1000.0,) * 3, 9, kaiser_beta=0.5).astype(np.float32)
+    N = f.size
+    vol = 1000.0 ** 3
+    ref = ideal.bk_ideal_multipoles(f, 1000.0, edges, ell)
+    D = ideal.forward(f)
+    mu2 = binning.mu2_grid(grid)
+    cnt, sdd = brute.brute_bk(D, grid, kf, edges, D2=D, D3=binning.legendre(ell, mu2) * D)
+    il = ref["ells"].index(ell)
+    want = np.array([sdd[t] for t in ref["triplets"]]) / N ** 2
+    assert np.max(np.abs(ref["S"][il] - want)) <= 1e-11 * np.max(np.abs(want))
+    # normalisation: (2 ell + 1) (V^2 / N^3) S / T with N^2 T the brute-force count of the same triangles
+    counts = np.array([cnt[t] for t in ref["triplets"]])
+    assert np.array_equal(ref["N_abc"], counts)
+    B = (2 * ell + 1) * vol * vol / float(N) ** 3 * want * N ** 2 / counts
+    assert np.max(np.abs(ref["B"][il] - B)) <= 1e-10 * np.max(np.abs(B))
+    # the monopole of the same call is the ell = 0 bispectrum
+    assert np.max(np.abs(ref["B"][0] - ideal.bk_ideal(f, 1000.0, edges)["B"])) <= 1e-12 * np.max(np.abs(ref["B"][0]))
+
+
+def test_bispectrum_quadrupole_of_transverse_modes():
+    """A field whose modes all lie in the k_z = 0 plane has mu = 0 on every mode, L_2 = -1/2 and L_4 = 3/8: its
+    multipoles are fixed multiples of the monopole, B_2 = 5 (-1/2) B_0 and B_4 = 9 (3/8) B_0 (eq. ideal-bk)."""
+    grid = (16, 16, 16)
+    box = 1000.0
+    kf = binning.kf_of(box)
+    edges = kf * np.array([1.0, 2.5, 4.0, 5.5, 7.0])
+    rng = np.random.Generator(np.random.PCG64(4))
+    plane = rng.standard_normal(grid[:2])
+    f = np.repeat(np.exp(plane)[:, :, None], grid[2], axis=2)      # independent of z: only k_z = 0 modes
+    f = (f / f.mean() - 1.0).astype(np.float32)
+    ref = ideal.bk_ideal_multipoles(f, box, edges, 4)
+    B0, B2, B4 = ref["B"]
+    scale = np.max(np.abs(B0))
+    assert scale > 0
+    assert np.max(np.abs(B2 - 5 * (-0.5) * B0)) <= 1e-12 * scale
+    assert np.max(np.abs(B4 - 9 * 0.375 * B0)) <= 1e-12 * scale
