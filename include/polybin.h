@@ -81,6 +81,17 @@ int polybin_get_triplets(polybin_ctx* ctx, int* abc, double* n_abc);
  * F = N_abc / (N Delta) in pixel units, so Delta cancels).  bk_out: host [batch][n_triplets]. */
 int polybin_bk_ideal(polybin_ctx* ctx, const float* delta, int batch, double* bk_out);
 
+/* Ideal bispectrum multipoles ell = 0, 2, .., lmax_b (lmax_b = 0, 2 or 4) about the global line of sight (the last
+ * grid axis), Sec. 4.1 eqs. Bk-Yam and ideal-bk with the ideal continuous Fisher of Sec. 4.4.1 (eq. bk-fish-ideal2,
+ * under which Delta_alpha cancels):
+ *   B_ell(a, b, c) = (2 ell + 1) (V^2 / N^3) S^ell_abc / T_abc,  S^ell_abc = sum_x g_a g_b g_{c,ell},
+ *   g_{c,ell} = IFT[Theta_c L_ell(mu) D]  (eq. g-ell-def, global line of sight; mu = k_z / |k| of the mode in the
+ *   third bin c, the largest, as eq. ideal-bk places it),
+ * over the closed triplets of polybin_get_triplets (N_0 = N_abc).  ell = 0 is polybin_bk_ideal.  delta: as
+ * polybin_bk_ideal; bk_out: host [batch][lmax_b / 2 + 1][n_triplets].  The Legendre-weighted maps take a second
+ * set of contraction-grid maps (allocated on the first call with lmax_b > 0). */
+int polybin_bk_ideal_multipoles(polybin_ctx* ctx, const float* delta, int batch, int lmax_b, double* bk_out);
+
 /* Ideal bispectra of n_fields fields on possibly different grids (e.g. a batch of 96^3, 128^3 and 160^3
  * realisations).  ctxs[i] is the context of field i (fields on one grid share a context; all contexts must use
  * one stream, that of ctxs[0]); fields[i]: device float32 [N0][N1][N2] of ctxs[i]; bk_out[i]: host

@@ -60,6 +60,8 @@ _SIGS = {
     "polybin_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
                                      ctypes.c_void_p]),
     "polybin_last_path": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
+    "polybin_bk_ideal_multipoles": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                                   ctypes.c_void_p]),
     "polybin_contraction_grid": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
 }
 
@@ -168,6 +170,15 @@ class PolyBin:
         batch = delta.shape[0] if delta.ndim == 4 else 1
         out = np.zeros((batch, self.num_triplets()), dtype=np.float64)
         self._check(self.lib.polybin_bk_ideal(self.ctx, _ptr(delta), batch, _ptr(out)), "polybin_bk_ideal")
+        return out
+
+    def bk_multipoles(self, delta, lmax_b: int = 2) -> np.ndarray:
+        """B_ell for ell = 0, 2, .., lmax_b: array [batch][lmax_b / 2 + 1][n_triplets]."""
+        delta = _f32(delta)
+        batch = delta.shape[0] if delta.ndim == 4 else 1
+        out = np.zeros((batch, lmax_b // 2 + 1, self.num_triplets()), dtype=np.float64)
+        self._check(self.lib.polybin_bk_ideal_multipoles(self.ctx, _ptr(delta), batch, int(lmax_b), _ptr(out)),
+                    "polybin_bk_ideal_multipoles")
         return out
 
     # ---- power spectrum

@@ -506,7 +506,7 @@ template int ensure_fine_inv<float>(polybin_ctx*);
 template int ensure_fine_inv<double>(polybin_ctx*);
 
 void free_work(Work& w) {
-    void* ptrs[] = {w.t1, w.t2, w.box, w.u1, w.u2, w.u1f, w.u2f, w.g, w.partial, w.mout};
+    void* ptrs[] = {w.t1, w.t2, w.box, w.u1, w.u2, w.u1f, w.u2f, w.g, w.g2, w.partial, w.mout};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     w = Work();
@@ -745,6 +745,48 @@ static int bk_pk_t(polybin_ctx* ctx, const float* delta, int batch, double* bk_o
         PB_CUDA_OK(cudaStreamSynchronize(ctx->stream));
     }
     return POLYBIN_OK;
+}
+
+// Bispectrum multipoles ell = 0, 2, .., lmax_b of `batch` fields (Sec. 4.1, eq. ideal-bk): one forward transform,
+// the ell = 0 shell maps g and, per ell > 0, the Legendre-weighted maps g_{c,ell} = IFT[Theta_c L_ell D]; the sums
+// S^ell_abc = sum_x g_a g_b g_{c,ell} and B_ell = (2 ell + 1) (V^2 / N^3) S^ell / T_abc on the device.
+template <typename T>
+static int bk_multipoles_t(polybin_ctx* ctx, const float* delta, int batch, int lmax_b, double* bk_out) {
+    int rc;
+    const size_t nt = ctx->Nabc.size();
+    const int nl = lmax_b / 2 + 1;
+    Work& w = ctx->w;
+    if (lmax_b > 0 && !w.g2) PB_CUDA_OK(cudaMalloc(&w.g2, sizeof(T) * (size_t)ctx->nb * ctx->cg.ncell));
+    for (int f = 0; f < batch; ++f) {
+        const float* in;
+        if ((rc = resolve_input(ctx, delta + (size_t)f * ctx->ncell, ctx->ncell, &in))) return rc;
+        if ((rc = run_forward<T, float, float>(ctx, in, (const float*)nullptr, (const float*)nullptr, (C<T>*)w.t1, (C<T>*)w.t2, (C<T>*)w.box))) return rc;
+        if (nt == 0) continue;
+        if ((rc = run_shells<T>(ctx, (const C<T>*)w.box, (C<T>*)w.u1, (C<T>*)w.u2, (T*)w.g, 0, ctx->cg))) return rc;
+        for (int il = 0; il < nl; ++il) {
+            const int ell = 2 * il;
+            if (ell == 0) {
+                if ((rc = run_triplet_sums<T>(ctx, (const T*)w.g, ctx->d_S))) return rc;
+            } else {
+                if ((rc = run_shells<T>(ctx, (const C<T>*)w.box, (C<T>*)w.u1, (C<T>*)w.u2, (T*)w.g2, ell, ctx->cg))) return rc;
+                if ((rc = run_triplet_sums_ell<T>(ctx, (const T*)w.g, (const T*)w.g2, ctx->d_S))) return rc;
+            }
+            if ((rc = run_bk_normalise(ctx, ctx->d_S, ctx->d_B, 2.0 * ell + 1.0))) return rc;
+            PB_CUDA_OK(cudaMemcpyAsync(bk_out + ((size_t)f * nl + il) * nt, ctx->d_B, sizeof(double) * nt,
+                                       cudaMemcpyDeviceToHost, ctx->stream));
+        }
+        PB_CUDA_OK(cudaStreamSynchronize(ctx->stream));
+    }
+    return POLYBIN_OK;
+}
+
+extern "C" int polybin_bk_ideal_multipoles(polybin_ctx* ctx, const float* delta, int batch, int lmax_b, double* bk_out) {
+    if (!ctx || !delta || !bk_out || batch < 0 || lmax_b < 0 || lmax_b > 4 || lmax_b % 2)
+        return fail(ctx, POLYBIN_EINVAL, "polybin_bk_ideal_multipoles: bad argument (lmax_b must be 0, 2 or 4)");
+    int rc = ensure_triplets(ctx);
+    if (rc) return rc;
+    return ctx->prec == POLYBIN_FP64 ? bk_multipoles_t<double>(ctx, delta, batch, lmax_b, bk_out)
+                                     : bk_multipoles_t<float>(ctx, delta, batch, lmax_b, bk_out);
 }
 
 extern "C" int polybin_bk_ideal(polybin_ctx* ctx, const float* delta, int batch, double* bk_out) {

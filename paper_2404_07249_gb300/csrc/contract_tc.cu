@@ -768,8 +768,10 @@ static std::vector<std::pair<int, int>> cut_tiles(const std::vector<NeedPair>& P
 
 // Pure host layout of a plan (no CUDA calls): tiles, row groups, TMEM / shared-memory layout, the row table and the
 // gather index of every output.  Returns nullptr or an error message.
+// sing_g = 1 with hsep = 1: the slot holds the g rows and the h rows (pairs may take one map from each, h rows at
+// index h_row0 + i) and the singles are the g rows.
 static const char* layout_plan(Plan& pl, long ncell, int nsm, int ng, int nh, int hsep, std::vector<NeedPair> need,
-                               int n_out, std::vector<short2>& rows, std::vector<int>& gidx) {
+                               int n_out, std::vector<short2>& rows, std::vector<int>& gidx, int sing_g = 0) {
     pl.ng = ng; pl.nh = nh; pl.hsep = hsep; pl.n_out = n_out;
     std::stable_sort(need.begin(), need.end(), [](const NeedPair& a, const NeedPair& b) {
         return std::tie(a.hi, a.lo) < std::tie(b.hi, b.lo);
@@ -811,8 +813,9 @@ static const char* layout_plan(Plan& pl, long ncell, int nsm, int ng, int nh, in
     const int grows = (ng + 7) / 8 * 8;
     P.h_row0 = grows;
     P.slot_bytes = (grows + (hsep ? (nh + 7) / 8 * 8 : 0)) * 128;
-    const int srows = hsep ? (nh + 7) / 8 * 8 : grows;     // rows of the singles region of a slot
-    P.s_off = hsep ? grows * 128 : 0;
+    const bool sh = hsep && !sing_g;                        // singles from the h rows
+    const int srows = sh ? (nh + 7) / 8 * 8 : grows;       // rows of the singles region of a slot
+    P.s_off = sh ? grows * 128 : 0;
     P.s_chunks = srows * 8;
     if (P.s_chunks > 256 * kBloItems) return "contract_tc: more than 64 rows of singles";
     int max_b = 0, max_units = 0;
@@ -887,14 +890,14 @@ static const char* layout_plan(Plan& pl, long ncell, int nsm, int ng, int nh, in
 }
 
 static int build_plan(polybin_ctx* ctx, Plan& pl, long ncell, int ng, int nh, int hsep, std::vector<NeedPair> need,
-                      int n_out) {
+                      int n_out, int sing_g = 0) {
     int dev = 0, nsm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return fail_cuda(ctx, e, "cudaDeviceGetAttribute", __FILE__, __LINE__);
     std::vector<short2> rows;
     std::vector<int> gidx;
-    const char* msg = layout_plan(pl, ncell, nsm, ng, nh, hsep, std::move(need), n_out, rows, gidx);
+    const char* msg = layout_plan(pl, ncell, nsm, ng, nh, hsep, std::move(need), n_out, rows, gidx, sing_g);
     if (msg) return fail(ctx, POLYBIN_EINVAL, "%s", msg);
     PB_CUDA_OK(cudaMalloc(&pl.d_rows, sizeof(short2) * rows.size()));
     PB_CUDA_OK(cudaMemcpy(pl.d_rows, rows.data(), sizeof(short2) * rows.size(), cudaMemcpyHostToDevice));
@@ -1049,6 +1052,36 @@ static int triplet_plan(polybin_ctx* ctx, Plan** out) {
     return POLYBIN_OK;
 }
 
+// Plan of the closed triplets for a multipole ell > 0 (Sec. 4.1, eq. ideal-bk: L_ell on the third bin): triplet
+// a <= b <= c from the pair (g_b, g_{c,ell}) -- g_b a row of the g maps, g_{c,ell} a row of the h maps in the
+// same slot -- and the single g_a, output S^ell' in triplet order.  Same pairs and windows as the ell = 0 plan.
+static int ell_plan(polybin_ctx* ctx, Plan** out) {
+    PlanCache* pc = cache_of(ctx);
+    const int nb = ctx->nb;
+    auto key = std::make_tuple(nb, nb, 1, 2, ctx->cg.ncell);
+    auto it = pc->plans.find(key);
+    if (it != pc->plans.end()) { *out = it->second; return POLYBIN_OK; }
+    const int h0 = (nb + 7) / 8 * 8;
+    std::map<std::pair<int, int>, NeedPair> m;
+    const int nt = (int)ctx->Nabc.size();
+    for (int t = 0; t < nt; ++t) {
+        const int a = ctx->trip[3 * t], b = ctx->trip[3 * t + 1], c = ctx->trip[3 * t + 2];
+        auto f = m.find({b, c});
+        if (f == m.end()) f = m.emplace(std::make_pair(b, c), NeedPair{b, h0 + c, a, a, {}}).first;
+        f->second.lo = std::min(f->second.lo, a);
+        f->second.hi = std::max(f->second.hi, a);
+        f->second.outs.push_back({a, t});
+    }
+    std::vector<NeedPair> need;
+    for (auto& kv : m) need.push_back(std::move(kv.second));
+    Plan* pl = new Plan();
+    int rc = build_plan(ctx, *pl, ctx->cg.ncell, nb, nb, 1, std::move(need), nt, 1);
+    if (rc) { delete pl; return rc; }
+    pc->plans[key] = pl;
+    *out = pl;
+    return POLYBIN_OK;
+}
+
 }  // namespace tc
 
 bool split_tc_available() { return true; }
@@ -1089,6 +1122,15 @@ int run_contract_tc(polybin_ctx* ctx, const float* g, int ng, const float* h, in
 int prepare_triplet_tc(polybin_ctx* ctx) {
     tc::Plan* pl = nullptr;
     return tc::triplet_plan(ctx, &pl);
+}
+
+// S^ell'_abc = sum g_a g_b g_{c,ell} of every closed triplet (device, triplet order) from the shell maps g and the
+// Legendre-weighted maps gl on the contraction grid.
+int run_triplet_sums_ell_tc(polybin_ctx* ctx, const float* g, const float* gl, double* d_S) {
+    tc::Plan* pl = nullptr;
+    int rc = tc::ell_plan(ctx, &pl);
+    if (rc) return rc;
+    return tc::launch(ctx, *pl, g, gl, d_S);
 }
 
 // S'_abc of every closed triplet (device, triplet order) from the shell maps g on the contraction grid.

@@ -65,6 +65,37 @@ int run_triplet_sums<float>(polybin_ctx* ctx, const float* g, double* d_S) {
     return triplet_sums_from_pairs<float>(ctx, g, d_S);
 }
 
+// S^ell' from pairs of the g maps and singles of the Legendre-weighted maps gl (M[(a <= b)][c], gathered).
+template <typename T>
+static int triplet_sums_ell_from_pairs(polybin_ctx* ctx, const T* g, const T* gl, double* d_S) {
+    const int nb = ctx->nb, nt = (int)ctx->Nabc.size();
+    Work& w = ctx->w;
+    int rc = run_contract_any<T>(ctx, g, nb, gl, nb, w.partial, w.partial_cap, w.mout, ctx->cg.ncell);
+    if (rc) return rc;
+    k_gather_triplets<<<(nt + 255) / 256, 256, 0, ctx->stream>>>(w.mout, ctx->d_trip_m, nt, d_S);
+    ctx->launches += 1;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail_cuda(ctx, e, "k_gather_triplets", __FILE__, __LINE__);
+    return POLYBIN_OK;
+}
+
+template <>
+int run_triplet_sums_ell<float>(polybin_ctx* ctx, const float* g, const float* gl, double* d_S) {
+    if (ctx->Nabc.empty()) return POLYBIN_OK;
+    if (ctx->prec == POLYBIN_SPLIT_TF32X3 && tc_shape_ok(ctx->cg.ncell, g, ctx->nb, gl, ctx->nb)) {
+        ctx->last_path = POLYBIN_PATH_TENSOR_SPLIT_TF32X3;
+        return run_triplet_sums_ell_tc(ctx, g, gl, d_S);
+    }
+    return triplet_sums_ell_from_pairs<float>(ctx, g, gl, d_S);
+}
+
+template <>
+int run_triplet_sums_ell<double>(polybin_ctx* ctx, const double* g, const double* gl, double* d_S) {
+    if (ctx->Nabc.empty()) return POLYBIN_OK;
+    ctx->last_path = POLYBIN_PATH_SIMT_FP64;
+    return triplet_sums_ell_from_pairs<double>(ctx, g, gl, d_S);
+}
+
 template <>
 int run_triplet_sums<double>(polybin_ctx* ctx, const double* g, double* d_S) {
     if (ctx->Nabc.empty()) return POLYBIN_OK;
@@ -79,11 +110,11 @@ static __global__ void k_bk_normalise(const double* __restrict__ S, const double
     if (t < nt) B[t] = scale * S[t] / T[t];
 }
 
-int run_bk_normalise(polybin_ctx* ctx, const double* d_S, double* d_B) {
+int run_bk_normalise(polybin_ctx* ctx, const double* d_S, double* d_B, double fac) {
     const int nt = (int)ctx->Nabc.size();
     if (nt == 0) return POLYBIN_OK;
     const double n = (double)ctx->ncell;
-    const double scale = ctx->vol * ctx->vol / (n * n * n) * ctx->cg_ratio;
+    const double scale = fac * (ctx->vol * ctx->vol / (n * n * n)) * ctx->cg_ratio;
     k_bk_normalise<<<(nt + 255) / 256, 256, 0, ctx->stream>>>(d_S, ctx->d_T, nt, scale, d_B);
     ctx->launches += 1;
     cudaError_t e = cudaGetLastError();

@@ -46,6 +46,7 @@ struct Work {
     void* u1f = nullptr;     // the same on the data grid, allocated on first use (ensure_fine_inv)
     void* u2f = nullptr;
     void* g = nullptr;       // shell maps [nb][cg.ncell] on the contraction grid
+    void* g2 = nullptr;      // Legendre-weighted shell maps [nb][cg.ncell] (bispectrum multipoles), on first use
     double* partial = nullptr;
     size_t partial_cap = 0;
     double* mout = nullptr;  // contraction result [npairs][nh]
@@ -103,12 +104,16 @@ bool tc_shape_ok(long ncell, const float* g, int ng, const float* h, int nh);
 int run_contract_tc(polybin_ctx*, const float*, int, const float*, int, double*, long ncell);
 int prepare_triplet_tc(polybin_ctx*);
 int run_triplet_sums_tc(polybin_ctx*, const float* g, double* d_S);
+int run_triplet_sums_ell_tc(polybin_ctx*, const float* g, const float* gl, double* d_S);
 void destroy_tc(polybin_ctx*);
 // S'_abc of every closed triplet (device, triplet order) from the nb shell maps g on the contraction grid; the
 // data-grid sum is S_abc = cg_ratio S'_abc.
 template <typename T> int run_triplet_sums(polybin_ctx*, const T* g, double* d_S);
-// B_abc = scale S'_abc / T_abc on the device (FP64), scale = (V^2 / N^3) cg_ratio.
-int run_bk_normalise(polybin_ctx*, const double* d_S, double* d_B);
+// S^ell'_abc = sum_x g_a g_b g_{c,ell} (gl: the maps g_{c,ell} = IFT[Theta_c L_ell D]) on the contraction grid.
+template <typename T> int run_triplet_sums_ell(polybin_ctx*, const T* g, const T* gl, double* d_S);
+// B_abc = fac scale S'_abc / T_abc on the device (FP64), scale = (V^2 / N^3) cg_ratio (fac = 2 ell + 1 for a
+// multipole).
+int run_bk_normalise(polybin_ctx*, const double* d_S, double* d_B, double fac = 1.0);
 // P_ell(b) from the P binning partials on the device (FP64): (2 ell + 1) (V / N^2) num / N_b.
 int run_pk_normalise(polybin_ctx*, double* d_P);
 void destroy_extras(polybin_ctx*);

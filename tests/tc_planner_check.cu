@@ -24,20 +24,25 @@ static int n_fail = 0;
         }                                                       \
     } while (0)
 
-static void check(const char* name, long ncell, int ng, int nh, int hsep, std::vector<NeedPair> need, int n_out) {
+static void check(const char* name, long ncell, int ng, int nh, int hsep, std::vector<NeedPair> need, int n_out,
+                  int sing_g = 0) {
     std::map<int, std::tuple<int, int, int>> want;   // output -> (j, k, single)
     for (const NeedPair& p : need)
         for (auto& so : p.outs) want[so.second] = std::make_tuple(p.j, p.k, so.first);
     Plan pl;   // layout only: its device pointers stay null
     std::vector<short2> rows;
     std::vector<int> gidx;
-    const char* msg = layout_plan(pl, ncell, 148, ng, nh, hsep, need, n_out, rows, gidx);
+    const char* msg = layout_plan(pl, ncell, 148, ng, nh, hsep, need, n_out, rows, gidx, sing_g);
     REQUIRE(msg == nullptr, "layout_plan: %s", msg ? msg : "");
     const Params& P = pl.base;
     REQUIRE(pl.smem <= 227 * 1024, "shared memory %zu", pl.smem);
     REQUIRE(P.s_chunks <= 256 * kBloItems, "B_lo chunks %d", P.s_chunks);
     REQUIRE(P.slot_bytes % 1024 == 0 && P.off_b % 1024 == 0, "slot / B_lo stage not 1024-aligned");
     REQUIRE(pl.ngroups >= 1 && pl.ngroups <= kMaxGroups, "groups %d", pl.ngroups);
+    // singles region: the h rows when they are separate (unless the singles are the g rows), else the g rows
+    const int grows = (ng + 7) / 8 * 8;
+    REQUIRE(P.s_off == ((hsep && !sing_g) ? grows * 128 : 0), "singles region offset %d", P.s_off);
+    REQUIRE(P.slot_bytes == (grows + (hsep ? (nh + 7) / 8 * 8 : 0)) * 128, "slot bytes %d", P.slot_bytes);
     REQUIRE((long)pl.ncta * pl.cells_cta >= ncell && pl.cells_cta % kSlotCells == 0, "cell split");
     int units = 0;
     for (int gi = 0; gi < pl.ngroups; ++gi) {
@@ -86,7 +91,9 @@ static void check(const char* name, long ncell, int ng, int nh, int hsep, std::v
         REQUIRE(jk.x == std::get<0>(w->second) && jk.y == std::get<1>(w->second) && s == std::get<2>(w->second),
                 "output %d: row (%d, %d) single %d, wanted (%d, %d) single %d", o, jk.x, jk.y, s,
                 std::get<0>(w->second), std::get<1>(w->second), std::get<2>(w->second));
-        REQUIRE(s < nh, "output %d: single %d >= %d", o, s, nh);
+        REQUIRE(s < (sing_g ? ng : nh), "output %d: single %d out of range", o, s);
+        REQUIRE(jk.x < grows + (hsep ? (nh + 7) / 8 * 8 : 0) && jk.y < grows + (hsep ? (nh + 7) / 8 * 8 : 0),
+                "output %d: pair row beyond the slot", o);
     }
 }
 
@@ -127,6 +134,28 @@ static void triplets(long ncell, int nb, int gap, const std::vector<int>* keep =
     check(name, ncell, nb, nb, 0, std::move(need), nt);
 }
 
+// closed triplets for a multipole: pair (g_b, h_c) with h_c at slot row h0 + c, single g_a (singles = g rows)
+static void ell_triplets(long ncell, int nb, int gap) {
+    const int h0 = (nb + 7) / 8 * 8;
+    std::map<std::pair<int, int>, NeedPair> m;
+    int nt = 0;
+    for (int a = 0; a < nb; ++a)
+        for (int b = a; b < nb; ++b)
+            for (int c = b; c < nb && c <= a + b + gap; ++c) {
+                auto f = m.find({b, c});
+                if (f == m.end()) f = m.emplace(std::make_pair(b, c), NeedPair{b, h0 + c, a, a, {}}).first;
+                f->second.lo = std::min(f->second.lo, a);
+                f->second.hi = std::max(f->second.hi, a);
+                f->second.outs.push_back({a, nt++});
+            }
+    std::vector<NeedPair> need;
+    for (auto& kv : m) need.push_back(std::move(kv.second));
+    char name[64];
+    std::snprintf(name, sizeof name, "ell triplets nb=%d gap=%d", nb, gap);
+    if (need.empty()) return;
+    check(name, ncell, nb, nb, 1, std::move(need), nt, 1);
+}
+
 int main() {
     int cases = 0;
     for (long ncell : {32L * 32 * 32, 512L * 512 * 512, 96L * 96 * 96}) {
@@ -136,7 +165,7 @@ int main() {
             for (int nh : {1, 7, 16, 17, 32}) { full(ncell, ng, nh, 1); ++cases; }
         }
         for (int nb = 2; nb <= 32; ++nb)
-            for (int gap : {0, 1, 2}) { triplets(ncell, nb, gap); ++cases; }
+            for (int gap : {0, 1, 2}) { triplets(ncell, nb, gap); ell_triplets(ncell, nb, gap); cases += 2; }
         std::mt19937 rng(12345);
         for (int rep = 0; rep < 40; ++rep) {
             std::vector<int> keep(37);

@@ -198,3 +198,35 @@ def test_batch_and_stream(pkg):
         pr = ideal.pk_ideal(fs[i], box, edges, 2)["P"]
         assert np.max(np.abs(P[i, 0] - pr[0]) / np.abs(pr[0])) < 1e-6
     pb.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "split", "fp64"])
+@pytest.mark.parametrize("case", [1, 8])
+def test_bk_multipoles(pkg, case, prec):
+    """B_ell, ell = 0, 2, 4, of a redshift-space (Kaiser) field against the oracle (Sec. 4.1, eq. ideal-bk), triplet by
+    triplet with the criterion of tests/bk_criterion.py (kappa from sum_x |g_a g_b g_{c,ell}|)."""
+    grid, box, ek, _ = CASES[case]
+    edges = _kf(box) * ek
+    f = synth.lognormal_field(grid, (box,) * 3, 60 + case, kaiser_beta=0.5).astype(np.float32)
+    ref = ideal.bk_ideal_multipoles(f, box, edges, 4)
+    pb = pkg.PolyBin(grid, box, edges, prec=prec)
+    Bl = pb.bk_multipoles(torch.from_numpy(f).cuda(), 4)[0]
+    if prec == "split":
+        assert pb.last_path() == pkg.PATH_TENSOR_SPLIT_TF32X3
+    abc, _ = pb.triplets()
+    assert [tuple(t) for t in abc.tolist()] == ref["triplets"]
+    # ell = 0 of this call is the monopole of polybin_bk_ideal, bit for bit
+    assert np.array_equal(Bl[0], pb.bk_ideal(torch.from_numpy(f).cuda())[0])
+    nb = len(edges) - 1
+    bins = binning.bin_grid(grid, box, edges)
+    mu2 = binning.mu2_grid(grid)
+    D = ideal.forward(f)
+    G = ideal.shell_maps(D, bins, nb).reshape(nb, -1)
+    for il, ell in enumerate(ref["ells"]):
+        GL = G if ell == 0 else ideal.shell_maps_ell(D, bins, nb, ell, mu2).reshape(nb, -1)
+        absS = np.array([np.dot(np.abs(G[a] * G[b]), np.abs(GL[c])) for a, b, c in ref["triplets"]])
+        e_rel, e_norm, kappa = bk_errors(Bl[il], ref["B"][il], ref["S"][il], absS)
+        s = check(ref["triplets"], e_rel, e_norm, kappa, norm_tol=TOL[prec]["norm"], rel_tol=TOL[prec]["rel"],
+                  kappa_max=TOL[prec]["kappa_max"], label=f"case {case} {prec} ell {ell}")
+        print(report(s, f"multipole ell={ell} case {case} {prec} contraction grid {pb.contraction_grid()}"))
+    pb.close()
