@@ -118,12 +118,20 @@ def _workload(cfg: int):
     return w, edges
 
 
-def cpu_baseline(cfg: int, field: np.ndarray, edges, box: float, budget_s: float = 25.0) -> dict:
+ORACLE_BINS = (0, 1, 4, 9, 14, 19, 24, 27, 29)   # bins of the sampled oracle comparison (all triplets among them)
+
+
+def cpu_baseline(cfg: int, field: np.ndarray, edges, box: float, gpu=None) -> dict:
     """The FP64 oracle as it stands, timed on the host cores on a bounded sample of the same workload:
     one forward FFT of the field, one shell map (filter + inverse FFT) and the oracle's triple-sum routine on
     all n_b shell maps restricted to a contiguous slab of cells; the per-estimate time is
-    t_forward + n_b t_shell + t_triple (N / N_slab) (every step of the oracle pipeline scales linearly in these)."""
-    from oracle import binning, ideal
+    t_forward + n_b t_shell + t_triple (N / N_slab) (every step of the oracle pipeline scales linearly in these).
+
+    gpu = (B, triplets) of the GPU path on the same field: the oracle then also evaluates B_abc of every closed
+    triplet among the bins ORACLE_BINS (shell and unit maps of those bins on the data grid, one pair product per
+    pair) and the comparison is returned under "B_rel_err_vs_oracle" (tests/bk_criterion.py statistics, with the
+    triplets above 1e-6 listed)."""
+    from oracle import _fft, binning, ideal
     nb = len(edges) - 1
     N = field.size
     t0 = time.perf_counter()
@@ -133,7 +141,6 @@ def cpu_baseline(cfg: int, field: np.ndarray, edges, box: float, budget_s: float
     t0 = time.perf_counter()
     g0 = ideal.shell_maps(D, bins, nb, which=[nb // 2])
     t_shell = time.perf_counter() - t0
-    del D
     slab = max(1, min(field.shape[0], int(field.shape[0] * min(1.0, 2.0e6 / N * 4))))
     rng = np.random.Generator(np.random.PCG64(1))
     gs = rng.standard_normal((nb, slab) + field.shape[1:])
@@ -142,10 +149,44 @@ def cpu_baseline(cfg: int, field: np.ndarray, edges, box: float, budget_s: float
     t_tri = (time.perf_counter() - t0) * (field.shape[0] / slab)
     del g0, gs
     per = t_fwd + nb * t_shell + t_tri
-    return {"value": 1.0 / per, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"FP64 oracle, 1 forward FFT + 1 of {nb} shell maps + triple sums of {nb} maps over "
-                      f"{slab}/{field.shape[0]} slabs, scaled to one {field.shape[0]}^3 estimate "
-                      f"(t_fwd {t_fwd:.2f}s, t_shell {t_shell:.2f}s, t_triple {t_tri:.2f}s)"}
+    out = {"value": 1.0 / per, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+           "sample": f"FP64 oracle, 1 forward FFT + 1 of {nb} shell maps + triple sums of {nb} maps over "
+                     f"{slab}/{field.shape[0]} slabs, scaled to one {field.shape[0]}^3 estimate "
+                     f"(t_fwd {t_fwd:.2f}s, t_shell {t_shell:.2f}s, t_triple {t_tri:.2f}s)",
+           "extrapolated": True}
+    if gpu is not None:
+        sys.path.insert(0, os.path.join(ROOT, "tests"))
+        from bk_criterion import bk_errors, summarise
+        B, trip = gpu
+        keep = set(b for b in ORACLE_BINS if b < nb)
+        pick = [i for i, t in enumerate(trip) if set(t) <= keep]
+        t0 = time.perf_counter()
+        g, tm = {}, {}
+        for b in sorted(keep):
+            sel = bins == b
+            g[b] = _fft.ifftn(np.where(sel, D, 0.0)).real
+            tm[b] = _fft.ifftn(sel.astype(np.complex128)).real
+        S, T, A = np.zeros(len(pick)), np.zeros(len(pick)), np.zeros(len(pick))
+        by_pair = {}
+        for q, i in enumerate(pick):
+            by_pair.setdefault(trip[i][1:], []).append((q, trip[i][0]))
+        for (b, c), items in by_pair.items():
+            pg, pt = (g[b] * g[c]).ravel(), (tm[b] * tm[c]).ravel()
+            pa = np.abs(pg)
+            for q, a in items:
+                S[q] = np.dot(g[a].ravel(), pg)
+                T[q] = np.dot(tm[a].ravel(), pt)
+                A[q] = np.dot(np.abs(g[a]).ravel(), pa)
+        del g, tm
+        vol = float(box) ** 3
+        Bref = vol * vol / float(N) ** 3 * S / T
+        e_rel, e_norm, kappa = bk_errors(np.asarray(B)[pick], Bref, S, A)
+        cmp_ = summarise([trip[i] for i in pick], e_rel, e_norm, kappa)
+        cmp_["sample"] = (f"every closed triplet among bins {sorted(keep)} ({len(pick)} of {len(trip)}), FP64 oracle on "
+                          f"the {'x'.join(str(n) for n in field.shape)} data grid ({time.perf_counter() - t0:.1f} s)")
+        out["B_rel_err_vs_oracle"] = cmp_
+    del D
+    return out
 
 
 def run_reference(args) -> None:
@@ -186,6 +227,33 @@ def _time(fn, reps=1):
     return (time.perf_counter() - t0) / reps
 
 
+def cufft_comparison(field_dev, cgrid, nb, stream) -> dict:
+    """cuFFT (through torch.fft) on the transforms the hot path replaces, timed with CUDA events on `stream`: the
+    full R2C of the data grid (the path's forward stage computes only the reachable box) and n_b full C2R onto the
+    contraction grid (the path's shell stage: n_b pruned inverse transforms).  A timed comparison only."""
+    import torch
+    out = {}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    with torch.cuda.stream(stream):
+        out["r2c_data_grid_ms"] = timed(lambda: torch.fft.rfftn(field_dev))
+        half = torch.zeros((nb,) + tuple(cgrid[:2]) + (cgrid[2] // 2 + 1,), dtype=torch.complex64, device=field_dev.device)
+        out[f"c2r_{nb}x_contraction_grid_ms"] = timed(lambda: torch.fft.irfftn(half, s=tuple(cgrid), dim=(1, 2, 3)))
+        del half
+    out["library"] = "cuFFT via torch.fft (full, unpruned transforms)"
+    return out
+
+
 def other_workloads(pkg, synth, stream, dev) -> dict:
     """Throughput of the remaining standard workloads (host-timed around synchronising C-ABI calls)."""
     import torch
@@ -206,7 +274,8 @@ def other_workloads(pkg, synth, stream, dev) -> dict:
     pb = pkg.PolyBin(w.grid, w.box, w.bk_edges, prec="split", stream=stream.cuda_stream)
     pb.num_triplets()
     t = _time(lambda: pb.bk_ideal(f), 5)
-    out["lognormal256_split"] = {"bk_per_s": 1 / t, "n_triplets": pb.num_triplets()}
+    out["lognormal256_split"] = {"bk_per_s": 1 / t, "n_triplets": pb.num_triplets(),
+                                 "contraction_grid": list(pb.contraction_grid())}
     pb.close()
     del f
     # 64 fields of 96^3 / 128^3 / 160^3, 12 bins, one CUDA graph
@@ -255,8 +324,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", type=int, nargs=3, default=None,
                     help="profiling only: run the workload's field model, box and bins on another grid")
-    ap.add_argument("--all-configs", action="store_true",
-                    help="also time the other workloads (64^3 FP64, 256^3, batched uneven grids, masked 256^3)")
+    ap.add_argument("--no-other-workloads", action="store_true",
+                    help="skip the other workloads (64^3 FP64, 256^3, batched uneven grids, masked 256^3)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -350,28 +419,34 @@ def main():
     Nc = float(np.prod(cgrid))
     nb = len(edges) - 1
     # dominant kernel: the triplet contraction over the cells of the alias-free contraction grid.  Algorithmic
-    # work: 2 flops per closed triplet per cell.
+    # work per launch: 2 flops per closed triplet per cell; algorithmic bytes: the n_b float32 maps read once.  The
+    # intensity (2 ntrip / (4 n_b) flop per byte, ~47 at 30 bins) is below the TF32 ridge (peak TF/s over peak
+    # TB/s, ~129), so the binding roof is HBM; the tensor-side rate is reported next to it.
     algo_flops = 2.0 * ntrip * Nc
+    algo_bytes = 4.0 * nb * Nc
     t_con = stage_ms["contract"] / 1000.0
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    hbm = float(peaks["hbm_gbs"])
+    roof = {"bound": "hbm", "unit": "GB/s", "peak": hbm, "peak_source": f"{peak_src} hbm_gbs (copy bandwidth)"}
+    roof["achieved"] = algo_bytes / t_con / 1e9 if t_con > 0 else None
+    roof["frac"] = roof["achieved"] / roof["peak"] if roof["achieved"] else None
     if args.prec == "split":
         peak_tf = float(peaks["bf16_tflops_sustained"]) / 2.0        # TF32 dense = bf16 / 2 (nominal ratio)
-        roof = {"bound": "tensor", "unit": "TFLOP/s", "peak": peak_tf,
-                "peak_source": f"{peak_src} bf16 sustained x 1/2 (TF32/bf16 nominal ratio)"}
+        roof["tensor_side"] = {"achieved_tflops": algo_flops / t_con / 1e12 if t_con > 0 else None,
+                               "peak_tflops": peak_tf,
+                               "peak_source": f"{peak_src} bf16 sustained x 1/2 (TF32/bf16 nominal ratio)"}
     else:
         alu = 152 * 128 * 2 * sm_max * 1e6 / 1e12 if args.prec == "fp32" else 152 * 2 * 2 * sm_max * 1e6 / 1e12
-        roof = {"bound": "alu", "unit": "TFLOP/s", "peak": alu,
-                "peak_source": ("152 SMs x 128 FP32 lanes x 2 flop x max SM clock" if args.prec == "fp32"
-                                else "152 SMs x 2 FP64 FMA/clk x 2 flop x max SM clock")}
-    roof["achieved"] = algo_flops / t_con / 1e12 if t_con > 0 else None
-    roof["frac"] = roof["achieved"] / roof["peak"] if roof["achieved"] else None
+        roof["alu_side"] = {"achieved_tflops": algo_flops / t_con / 1e12 if t_con > 0 else None, "peak_tflops": alu}
+    roof["ridge_flop_per_byte"] = (roof.get("tensor_side", roof.get("alu_side"))["peak_tflops"] * 1e12) / (hbm * 1e9)
+    roof["intensity_flop_per_byte"] = algo_flops / algo_bytes
     roof["traffic"] = _captured_traffic(w.name, args.prec)
-    roof["kernel"] = "k_contract (triplet contraction, a3)"
-    roof["algorithmic"] = (f"2 x {ntrip} closed triplets x {int(Nc)} cells of the {cgrid} contraction grid = "
-                           f"{algo_flops:.3e} flop per launch (the same sums over the {int(N)} data-grid cells "
-                           f"would be {2.0 * ntrip * N:.3e})")
+    roof["kernel"] = ("k_contract_tc (triplet contraction, a3)" if args.prec == "split"
+                      else "k_contract (triplet contraction, a3)")
+    roof["algorithmic"] = (f"{nb} maps x {int(Nc)} cells x 4 B = {algo_bytes:.3e} B and 2 x {ntrip} closed triplets x "
+                           f"{int(Nc)} cells = {algo_flops:.3e} flop per launch on the {cgrid} contraction grid (the "
+                           f"same sums over the {int(N)} data-grid cells would be {2.0 * ntrip * N:.3e} flop)")
     roof["stage_ms"] = stage_ms
-    hbm = float(peaks["hbm_gbs"])
     roof["hbm_gbs_of_stages"] = {
         "forward": (N * 4 + 0) / (stage_ms["forward"] / 1e3) / 1e9 if stage_ms["forward"] else None,
         "shells_write_g": (nb * Nc * 4) / (stage_ms["shells"] / 1e3) / 1e9 if stage_ms["shells"] else None,
@@ -408,13 +483,28 @@ def main():
         rel = np.abs(B32[0] - B64[0]) / np.abs(B64[0])
         line["fp64_gpu_path"] = {"value": world * 1000.0 / ms64, "unit": UNIT, "ms_per_step": ms64,
                                  "speedup_of_value": (world * 1000.0 / ms) / (world * 1000.0 / ms64),
+                                 "work": "same closed-triplet pairs and windows on the same contraction grid, FP64 "
+                                         "FFTs and FP64 SIMT contraction",
                                  "B_rel_err_vs_fp64_gpu": {"max": float(rel.max()), "median": float(np.median(rel)),
                                                            "frac_le_1e-6": float(np.mean(rel <= 1e-6))}}
         pb64.close()
 
+    # bispectrum quadrupole (ell = 2) of the same field: B_0 and B_2 from one forward transform
+    t_mp = _time(lambda: pb.bk_multipoles(d, 2), max(1, args.steps // 2))
+    line["bk_multipoles_ell_0_2"] = {"value": world / t_mp, "unit": "estimates/s (B_0 and B_2 of one field)",
+                                     "ms_per_estimate": 1000.0 * t_mp}
+    line["cufft_comparison"] = cufft_comparison(d, cgrid, nb, stream)
+    line["cufft_comparison"]["ours_forward_ms"] = stage_ms["forward"]
+    line["cufft_comparison"]["ours_shells_ms"] = stage_ms["shells"]
+    B_last, _ = step(d)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(args.config, field, edges, box)
-    if args.all_configs and world == 1:
+        abc, _ = pb.triplets()
+        cb = cpu_baseline(args.config, field, edges, box, gpu=(B_last[0], [tuple(t) for t in abc.tolist()]))
+        cmp_ = cb.pop("B_rel_err_vs_oracle", None)
+        line["cpu_baseline"] = cb
+        if cmp_ is not None:
+            line["B_rel_err_vs_oracle"] = cmp_
+    if not args.no_other_workloads and world == 1 and not args.grid:
         del d
         torch.cuda.empty_cache()
         line["other_workloads"] = other_workloads(pkg, synth, stream, dev)

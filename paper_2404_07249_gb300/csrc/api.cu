@@ -572,17 +572,12 @@ int ensure_triplets(polybin_ctx* ctx) {
                 }
             }
     const size_t nt = ctx->Nabc.size();
-    std::vector<int> m(std::max(nt, (size_t)1), 0);
-    for (size_t t = 0; t < nt; ++t)
-        m[t] = pair_index(nb, ctx->trip[3 * t], ctx->trip[3 * t + 1]) * nb + ctx->trip[3 * t + 2];
     std::vector<double> Tv(std::max(nt, (size_t)1), 1.0);
     for (size_t t = 0; t < nt; ++t) Tv[t] = ctx->Tabc[t];
     polybin_ctx* c = ctx;
-    PB_CUDA_OK_C(cudaMalloc(&c->d_S, sizeof(double) * m.size()));
-    PB_CUDA_OK_C(cudaMalloc(&c->d_B, sizeof(double) * m.size()));
-    PB_CUDA_OK_C(cudaMalloc(&c->d_T, sizeof(double) * m.size()));
-    PB_CUDA_OK_C(cudaMalloc(&c->d_trip_m, sizeof(int) * m.size()));
-    PB_CUDA_OK_C(cudaMemcpy(c->d_trip_m, m.data(), sizeof(int) * m.size(), cudaMemcpyHostToDevice));
+    PB_CUDA_OK_C(cudaMalloc(&c->d_S, sizeof(double) * Tv.size()));
+    PB_CUDA_OK_C(cudaMalloc(&c->d_B, sizeof(double) * Tv.size()));
+    PB_CUDA_OK_C(cudaMalloc(&c->d_T, sizeof(double) * Tv.size()));
     PB_CUDA_OK_C(cudaMemcpy(c->d_T, Tv.data(), sizeof(double) * Tv.size(), cudaMemcpyHostToDevice));
     ctx->trip_ready = true;
     // the tensor-core plan is built now, outside any later stream capture

@@ -165,17 +165,16 @@ struct polybin_ctx {
     std::vector<double> counts;
     std::vector<double> fish_disc;   // [nb][nell][nell]
 
-    // closed triplets (lexicographic), T_abc and N_abc; on the device: S_abc of the last field and the index of
-    // each triplet's entry in the pair-major contraction M[(a <= b)][c]
+    // closed triplets (lexicographic), T_abc and N_abc; on the device: S_abc and B_abc of the last field, T_abc
     bool trip_ready = false;
     std::vector<int> trip;
     std::vector<double> Tabc, Nabc;
     double* d_S = nullptr;
     double* d_B = nullptr;       // normalised bispectrum of the last field
     double* d_T = nullptr;       // T_abc (data grid)
-    int* d_trip_m = nullptr;
-    // tensor-core contraction plans
+    // tensor-core contraction plans; closed-triplet SIMT plans (FP32 / FP64 modes)
     void* tc = nullptr;
+    void* simt = nullptr;
 
     // instrumentation: kernel launches issued, and (when enabled) per-stage device time from CUDA events.
     // Stage brackets are recorded without blocking into tev (start, stop pairs) and read back lazily: when the
