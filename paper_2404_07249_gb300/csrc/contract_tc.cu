@@ -716,6 +716,230 @@ __global__ void k_wait_selftest(int* err, unsigned limit) {
     }
 }
 
+// ------------------------------------------------------------------------------------------------ Gram
+// Tensor-core Gram matrix of the bispectrum Fisher (Sec. 4.3.4, eq. bk-fish-def in Fourier space):
+//   part[s][i][j] = sum_{k in split s} A[i][k] B[j][k],  A = Z (weighted), B = Y as float32 rows [n][K], K = 2 M
+// (real and imaginary parts of the binned modes interleaved: re*re + im*im is the real part of conj(Z) Y).
+// A CTA takes a 128 x 32 output tile and a contiguous range of K.  Arithmetic as in the triplet contraction:
+// A = A_hi + A_lo (A_hi rounded to TF32 by the producers, written to tensor memory), B_hi = the raw TMA tile (read as
+// TF32 by truncation), B_lo = (B - trunc B) rounded to TF32; D_hh += A_hi B_hi, D_c += A_hi B_lo + A_lo B_hi; D restarts
+// every 64 K (8 MMAs a column), FP32 register sums, FP64 register sums every 2048 K; FP64 partials per K split.
+namespace gram {
+constexpr int kBM = 128, kBN = 32, kKC = 32, kStages = 6, kPeriod = 2, kSpill = 32;
+constexpr int kThreads = 384;   // warps 0 TMA/TMEM, 1 MMA, 2 B_lo, 3 idle, 4-7 A producers, 8-11 epilogue
+constexpr int kAStage = kBM * 128, kBStage = kBN * 128;   // raw tiles: 32 floats (128 B) a row
+constexpr int kSmem = kStages * (kAStage + 2 * kBStage) + 1024 + 256;
+
+struct GP {
+    long k_cta;       // K per CTA (multiple of kKC)
+    long K;           // row length (floats)
+    int nA, nB, nsplit;
+    double* part;     // [nsplit][nI*128][nJ*32]
+    long ldp;         // row stride of part (nJ * 32)
+    long split_stride;
+    int* err;
+};
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_gram_tc(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, const __grid_constant__ GP P) {
+    extern __shared__ __align__(1024) unsigned char gsm_raw[];
+    unsigned char* sm = gsm_raw + ((1024u - (smem_u32(gsm_raw) & 1023u)) & 1023u);
+    unsigned char* sA = sm;                                       // [kStages][kAStage]
+    unsigned char* sB = sA + kStages * kAStage;                   // [kStages][kBStage]
+    unsigned char* sBl = sB + kStages * kBStage;                  // [kStages][kBStage]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sBl + kStages * kBStage);
+    uint64_t* full = bars;                      // [kStages] TMA -> A producers, B_lo warp
+    uint64_t* ready = full + kStages;           // [kStages] A producers + B_lo -> MMA
+    uint64_t* empty = ready + kStages;          // [kStages] MMA commit -> TMA
+    uint64_t* d_full = empty + kStages;         // MMA -> epilogue (period done)
+    uint64_t* d_empty = d_full + 1;             // epilogue -> MMA
+    uint64_t* fin = d_empty + 1;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int warp = __shfl_sync(0xffffffffu, tid >> 5, 0);
+    const int i0 = blockIdx.y * kBM, j0 = blockIdx.x * kBN;
+    const long k0 = (long)blockIdx.z * P.k_cta;
+    const long k1 = min(P.K, k0 + P.k_cta);
+    const int nst = k0 < k1 ? (int)((k1 - k0 + kKC - 1) / kKC) : 0;
+    int* const err = P.err;
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&ready[s], 5);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(d_full, 1);
+        mbar_init(d_empty, 4);
+        mbar_init(fin, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    // TMEM columns: D_hh [0, 32), D_c [32, 64), A stage s: hi [64 + 64 s, +32), lo [+32, +64)
+    if (warp == 0) {
+        if (lane == 0 && nst > 0) {
+            int issued = 0;
+            for (int st = 0; st < nst; ++st) {
+                const int s = st % kStages;
+                if (st >= kStages && !thread_wait(&empty[s], (uint32_t)((st / kStages - 1) & 1), abort_flag, err)) break;
+                const int x = (int)(k0 + (long)st * kKC);
+                mbar_expect_tx(&full[s], (uint32_t)(kAStage + kBStage));
+                tma_load_2d(sA + (size_t)s * kAStage, &tA, x, i0, &full[s]);
+                tma_load_2d(sB + (size_t)s * kBStage, &tB, x, j0, &full[s]);
+                ++issued;
+            }
+            for (int st = max(0, issued - kStages); st < issued; ++st)
+                drain_wait(&full[st % kStages], (uint32_t)((st / kStages) & 1), err);
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // MMA issue (whole warp converged; the elected lane issues)
+        const bool tmem_ok = tmem == 0u;
+        if (!tmem_ok && lane == 0) { *abort_flag = 1; atomicExch(err, 1); }
+        const uint32_t idesc = idesc_tf32(kBM, kBN);
+        const uint64_t bh0 = sdesc_sw128(smem_u32(sB)), bl0 = sdesc_sw128(smem_u32(sBl));
+        const uint64_t bstep = (uint64_t)(kBStage >> 4);
+        int s = 0, pos = 0, per = 0;
+        uint32_t ph = 0;
+        uint32_t aa = 64u;
+        uint64_t bh = bh0, bl = bl0;
+        for (int st = 0; st < nst && tmem_ok; ++st) {
+            const bool pstart = pos == 0;
+            if (pstart && per >= 1 && !warp_wait(d_empty, (uint32_t)((per - 1) & 1), abort_flag, err)) break;
+            if (!warp_wait(&ready[s], ph, abort_flag, err)) break;
+            tc_fence_after();
+#pragma unroll
+            for (int ks = 0; ks < kKC / 8; ++ks) {
+                const uint32_t acc = (pstart && ks == 0) ? 0u : 1u;
+                mma_tf32(0u, aa + 8u * ks, bh + (uint64_t)(2 * ks), idesc, acc);          // A_hi B_hi
+                mma_tf32(32u, aa + 8u * ks, bl + (uint64_t)(2 * ks), idesc, acc);         // A_hi B_lo
+                mma_tf32(32u, aa + 32u + 8u * ks, bh + (uint64_t)(2 * ks), idesc, 1u);    // + A_lo B_hi
+            }
+            mma_commit(&empty[s]);
+            if (pos == kPeriod - 1 || st == nst - 1) mma_commit(d_full);
+            if (++s == kStages) { s = 0; ph ^= 1u; aa = 64u; bh = bh0; bl = bl0; } else { aa += 64u; bh += bstep; bl += bstep; }
+            if (++pos == kPeriod) { pos = 0; ++per; }
+        }
+        mma_commit(fin);
+        drain_wait(fin, 0, err);
+        __syncwarp();
+    } else if (warp == 2) {
+        // B_lo = (B - trunc B) rounded to TF32, same swizzled layout: 32 rows x 8 chunks, 8 chunks a lane
+        int s = 0;
+        uint32_t ph = 0;
+        for (int st = 0; st < nst; ++st) {
+            if (!warp_wait(&full[s], ph, abort_flag, err)) break;
+            const unsigned char* src = sB + (size_t)s * kBStage;
+            unsigned char* dst = sBl + (size_t)s * kBStage;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int i = lane + 32 * u;
+                const uint4 g = *reinterpret_cast<const uint4*>(src + 16 * i);
+                const uint64_t g01 = (uint64_t)g.x | ((uint64_t)g.y << 32);
+                const uint64_t g23 = (uint64_t)g.z | ((uint64_t)g.w << 32);
+                const uint64_t l01 = sub_x2(g01, g01 & 0xFFFFE000FFFFE000ull);
+                const uint64_t l23 = sub_x2(g23, g23 & 0xFFFFE000FFFFE000ull);
+                *reinterpret_cast<uint4*>(dst + 16 * i) =
+                    make_uint4(((uint32_t)l01 + 0x1000u) & 0xFFFFE000u, ((uint32_t)(l01 >> 32) + 0x1000u) & 0xFFFFE000u,
+                               ((uint32_t)l23 + 0x1000u) & 0xFFFFE000u, ((uint32_t)(l23 >> 32) + 0x1000u) & 0xFFFFE000u);
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ready[s]);
+            if (++s == kStages) { s = 0; ph ^= 1u; }
+        }
+    } else if (warp >= 4 && warp < 8) {
+        // A producers: thread = row r = 32 (warp % 4) + lane of the tile = TMEM lane r; hi / lo of the 32 K values
+        const int q = warp & 3, r = 32 * q + lane;
+        const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+        if (tmem == 0u) {
+            int s = 0;
+            uint32_t ph = 0;
+            uint32_t ac = 64u;
+            for (int st = 0; st < nst; ++st) {
+                if (!warp_wait(&full[s], ph, abort_flag, err)) break;
+                const unsigned char* row = sA + (size_t)s * kAStage;
+                uint32_t v[32], w[32];
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const float4 x = *ring_chunk(row, r, c);
+                    uint64_t h0, l0, h1, l1;
+                    split_x2(f2pack(x.x, x.y), h0, l0);
+                    split_x2(f2pack(x.z, x.w), h1, l1);
+                    v[4 * c + 0] = (uint32_t)h0; v[4 * c + 1] = (uint32_t)(h0 >> 32);
+                    v[4 * c + 2] = (uint32_t)h1; v[4 * c + 3] = (uint32_t)(h1 >> 32);
+                    w[4 * c + 0] = (uint32_t)l0; w[4 * c + 1] = (uint32_t)(l0 >> 32);
+                    w[4 * c + 2] = (uint32_t)l1; w[4 * c + 3] = (uint32_t)(l1 >> 32);
+                }
+                tmem_st32(lane_base + ac, v);
+                tmem_st32(lane_base + ac + 32u, w);
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&ready[s]);
+                if (++s == kStages) { s = 0; ph ^= 1u; ac = 64u; } else { ac += 64u; }
+            }
+        }
+    } else if (warp >= 8) {
+        // epilogue: lane r of the tile; every period add D_hh + D_c into FP32 sums, every kSpill periods into FP64
+        const int q = warp & 3, r = 32 * q + lane;
+        const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+        const int nper = (nst + kPeriod - 1) / kPeriod;
+        float acc[kBN];
+        double acc64[kBN];
+#pragma unroll
+        for (int j = 0; j < kBN; ++j) { acc[j] = 0.f; acc64[j] = 0.0; }
+        for (int per = 0; per < nper; ++per) {
+            if (!warp_wait(d_full, (uint32_t)(per & 1), abort_flag, err)) break;
+            tc_fence_after();
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                uint32_t a[16], b[16];
+                tmem_ld16(tmem + lane_base + 16u * h, a);
+                tmem_ld16(tmem + lane_base + 32u + 16u * h, b);
+                tmem_wait_ld32(a, b);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) acc[16 * h + j] += __uint_as_float(a[j]) + __uint_as_float(b[j]);
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(d_empty);
+            if ((per + 1) % kSpill == 0) {
+#pragma unroll
+                for (int j = 0; j < kBN; ++j) { acc64[j] += (double)acc[j]; acc[j] = 0.f; }
+            }
+        }
+        double* out = P.part + (size_t)blockIdx.z * P.split_stride + (size_t)(i0 + r) * P.ldp + j0;
+#pragma unroll
+        for (int j = 0; j < kBN; ++j) out[j] = acc64[j] + (double)acc[j];
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+}
+
+// out[i][j] += scale * sum_s part[s][i][j] (splits in order), i < nA, j < nB.
+__global__ void k_gram_reduce(const double* __restrict__ part, int nsplit, long split_stride, long ldp, int nA, int nB,
+                              double scale, double* __restrict__ out) {
+    const long o = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= (long)nA * nB) return;
+    const int i = (int)(o / nB), j = (int)(o - (long)i * nB);
+    double s = 0.0;
+    for (int q = 0; q < nsplit; ++q) s += part[(size_t)q * split_stride + (size_t)i * ldp + j];
+    out[o] += scale * s;
+}
+}  // namespace gram
+
 // ------------------------------------------------------------------------------------------------ host planner
 
 // A pair row with the range of singles it needs and where each of its outputs goes.
@@ -911,8 +1135,11 @@ static int build_plan(polybin_ctx* ctx, Plan& pl, long ncell, int ng, int nh, in
 
 struct PlanCache {
     std::map<std::tuple<int, int, int, int, long>, Plan*> plans;   // (ng, nh, hsep, kind, ncell)
+    double* gram_part = nullptr;                                   // Gram partials (K splits)
+    size_t gram_cap = 0;
     ~PlanCache() {
         for (auto& kv : plans) delete kv.second;
+        if (gram_part) cudaFree(gram_part);
     }
 };
 
@@ -946,6 +1173,24 @@ static int make_map(polybin_ctx* ctx, CUtensorMap* m, const float* base, int row
                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(ctx, POLYBIN_ECUDA, "contract_tc: cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return POLYBIN_OK;
+}
+
+// 2D map over a row-major float32 matrix [height][width] (row stride width floats), box = box_w x box_h,
+// 128-byte swizzle (box_w = 32 floats), out-of-range elements read as zero.
+static int make_map2(polybin_ctx* ctx, CUtensorMap* m, const float* base, long width, long height, int box_w, int box_h) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return fail(ctx, POLYBIN_ECUDA, "gram: cuTensorMapEncodeTiled is not available");
+    if (reinterpret_cast<uintptr_t>(base) % 16 || (width * (long)sizeof(float)) % 16)
+        return fail(ctx, POLYBIN_EINVAL, "gram: rows must be 16-byte aligned");
+    const cuuint64_t dims[2] = {(cuuint64_t)width, (cuuint64_t)height};
+    const cuuint64_t strides[1] = {(cuuint64_t)width * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)box_h};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(ctx, POLYBIN_ECUDA, "gram: cuTensorMapEncodeTiled failed (%d)", (int)r);
     return POLYBIN_OK;
 }
 
@@ -1131,6 +1376,60 @@ int run_triplet_sums_ell_tc(polybin_ctx* ctx, const float* g, const float* gl, d
     int rc = tc::ell_plan(ctx, &pl);
     if (rc) return rc;
     return tc::launch(ctx, *pl, g, gl, d_S);
+}
+
+// out[i][j] += scale sum_k A[i][k] B[j][k] for float32 rows A [nA][K], B [nB][K] (K a multiple of 4, 16-byte aligned
+// rows) on the tensor cores (3-term split TF32, FP64 sums across K splits in a fixed order).
+int run_gram_tc(polybin_ctx* ctx, const float* A, int nA, const float* B, int nB, long K, double scale, double* d_out) {
+    using namespace tc::gram;
+    if (nA < 1 || nB < 1 || K < 1) return POLYBIN_OK;
+    tc::PlanCache* pc = tc::cache_of(ctx);
+    CUtensorMap mA, mB;
+    int rc = tc::make_map2(ctx, &mA, A, K, nA, kKC, kBM);
+    if (rc) return rc;
+    if ((rc = tc::make_map2(ctx, &mB, B, K, nB, kKC, kBN))) return rc;
+    const int nI = (nA + kBM - 1) / kBM, nJ = (nB + kBN - 1) / kBN;
+    int dev = 0, nsm = 0;
+    PB_CUDA_OK(cudaGetDevice(&dev));
+    PB_CUDA_OK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const long kst = (K + kKC - 1) / kKC;
+    int nsplit = (int)std::max(1L, std::min(kst, (long)((2 * nsm + nI * nJ - 1) / (nI * nJ))));
+    const long k_cta = (kst + nsplit - 1) / nsplit * kKC;
+    nsplit = (int)((K + k_cta - 1) / k_cta);
+    const long ldp = (long)nJ * kBN, split_stride = (long)nI * kBM * ldp;
+    const size_t need = (size_t)nsplit * split_stride;
+    if (need > pc->gram_cap) {
+        if (pc->gram_part) cudaFree(pc->gram_part);
+        pc->gram_part = nullptr;
+        pc->gram_cap = 0;
+        PB_CUDA_OK(cudaMalloc(&pc->gram_part, sizeof(double) * need));
+        pc->gram_cap = need;
+    }
+    if ((rc = ensure_err_flag(ctx))) return rc;
+    PB_CUDA_OK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
+    PB_CUDA_OK(cudaFuncSetAttribute((const void*)k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
+    {
+        cudaFuncAttributes fa{};
+        PB_CUDA_OK(cudaFuncGetAttributes(&fa, (const void*)k_gram_tc));
+        if (fa.numRegs * kThreads > 65536)
+            return fail(ctx, POLYBIN_ECUDA, "gram: kernel built with %d registers a thread", fa.numRegs);
+    }
+    GP P;
+    P.k_cta = k_cta; P.K = K; P.nA = nA; P.nB = nB; P.nsplit = nsplit;
+    P.part = pc->gram_part; P.ldp = ldp; P.split_stride = split_stride; P.err = ctx->d_err;
+    k_gram_tc<<<dim3(nJ, nI, nsplit), kThreads, kSmem, ctx->stream>>>(mA, mB, P);
+    ctx->launches += 1;
+    PB_CUDA_OK(cudaGetLastError());
+    const long nout = (long)nA * nB;
+    k_gram_reduce<<<(unsigned)((nout + 255) / 256), 256, 0, ctx->stream>>>(pc->gram_part, nsplit, split_stride, ldp, nA, nB,
+                                                                          scale, d_out);
+    ctx->launches += 1;
+    PB_CUDA_OK(cudaGetLastError());
+    int herr = 0;
+    PB_CUDA_OK(cudaMemcpyAsync(&herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    PB_CUDA_OK(cudaStreamSynchronize(ctx->stream));
+    if (herr) return fail(ctx, POLYBIN_ETIMEOUT, "gram: a pipeline wait timed out");
+    return POLYBIN_OK;
 }
 
 // S'_abc of every closed triplet (device, triplet order) from the shell maps g on the contraction grid.

@@ -105,6 +105,7 @@ int run_contract_tc(polybin_ctx*, const float*, int, const float*, int, double*,
 int prepare_triplet_tc(polybin_ctx*);
 int run_triplet_sums_tc(polybin_ctx*, const float* g, double* d_S);
 int run_triplet_sums_ell_tc(polybin_ctx*, const float* g, const float* gl, double* d_S);
+int run_gram_tc(polybin_ctx*, const float* A, int nA, const float* B, int nB, long K, double scale, double* d_out);
 void destroy_tc(polybin_ctx*);
 // S'_abc of every closed triplet (device, triplet order) from the nb shell maps g on the contraction grid; the
 // data-grid sum is S_abc = cg_ratio S'_abc.

@@ -121,18 +121,22 @@ __global__ void k_qcomb(const C<T>* __restrict__ P1, const C<T>* __restrict__ P2
     }
 }
 
-// Compact copy of the binned modes of a box spectrum: out[m] = box[offs[m]].
+// Compact copy of the binned modes of a box spectrum: out[m] = box[offs[m]] (times wm[m] when wm is not NULL: the
+// half-spectrum weight, 1 or 2, exact in any precision).
 template <typename T>
-__global__ void k_gather(const C<T>* __restrict__ box, const int* __restrict__ offs, long M, C<T>* __restrict__ out) {
-    for (long m = (long)blockIdx.x * blockDim.x + threadIdx.x; m < M; m += (long)gridDim.x * blockDim.x)
-        out[m] = box[offs[m]];
+__global__ void k_gather(const C<T>* __restrict__ box, const int* __restrict__ offs, long M, C<T>* __restrict__ out,
+                         const double* __restrict__ wm = nullptr) {
+    for (long m = (long)blockIdx.x * blockDim.x + threadIdx.x; m < M; m += (long)gridDim.x * blockDim.x) {
+        const C<T> v = box[offs[m]];
+        out[m] = wm ? mk<T>(v.x * (T)wm[m], v.y * (T)wm[m]) : v;
+    }
 }
 
 // out[i][j] += scale * sum_m w_m Re(conj(Z[i][m]) Y[j][m])   (FP64 accumulation; 32 x 32 tile per CTA).
 template <typename T>
 __global__ void __launch_bounds__(256) k_gram(const C<T>* __restrict__ Z, const C<T>* __restrict__ Y,
-                                              const double* __restrict__ wm, int nA, int nB, long M, double scale,
-                                              double* __restrict__ out) {
+                                              const double* __restrict__ wm, int nA, int nB, long M, long ld,
+                                              double scale, double* __restrict__ out) {
     __shared__ double sz[32][65];   // 64 used (re, im interleaved) + 1 pad: conflict-free row access
     __shared__ double sy[32][65];
     const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
@@ -146,8 +150,8 @@ __global__ void __launch_bounds__(256) k_gram(const C<T>* __restrict__ Z, const 
             double wk = 0.0;
             if (m < M) {
                 wk = wm[m];
-                if (i0 + r < nA) z = Z[(long)(i0 + r) * M + m];
-                if (j0 + r < nB) y = Y[(long)(j0 + r) * M + m];
+                if (i0 + r < nA) z = Z[(long)(i0 + r) * ld + m];
+                if (j0 + r < nB) y = Y[(long)(j0 + r) * ld + m];
             }
             sz[r][2 * k] = wk * (double)z.x;
             sz[r][2 * k + 1] = wk * (double)z.y;
@@ -321,8 +325,14 @@ static int uw_alloc(polybin_ctx* ctx, bool need_b) {
         const size_t nt = ctx->Nabc.size();
         if ((rc = need(&u->pairs, sizeof(C<T>) * (size_t)4 * np * nbox))) return rc;
         if ((rc = need(&u->qbox, sizeof(C<T>) * nbox))) return rc;
-        if ((rc = need(&u->zc, sizeof(C<T>) * nt * std::max(ctx->nmodes, 1L)))) return rc;
-        if ((rc = need(&u->yc, sizeof(C<T>) * nt * std::max(ctx->nmodes, 1L)))) return rc;
+        const long Mp = (std::max(ctx->nmodes, 1L) + 1) / 2 * 2;   // even row stride: 16-byte aligned rows
+        const bool fresh = !u->zc;
+        if ((rc = need(&u->zc, sizeof(C<T>) * nt * Mp))) return rc;
+        if ((rc = need(&u->yc, sizeof(C<T>) * nt * Mp))) return rc;
+        if (fresh) {   // the padding column stays zero
+            PB_CUDA_OK(cudaMemset(u->zc, 0, sizeof(C<T>) * nt * Mp));
+            PB_CUDA_OK(cudaMemset(u->yc, 0, sizeof(C<T>) * nt * Mp));
+        }
         if ((rc = need(&u->v1, sizeof(C<T>) * (size_t)ctx->N[0] * ctx->gy.cnt * ctx->gz.cnt))) return rc;
         if ((rc = need(&u->v2, sizeof(C<T>) * (size_t)ctx->N[0] * ctx->N[1] * ctx->gz.cnt))) return rc;
     }
@@ -487,6 +497,9 @@ static int bk_fisher_draw(polybin_ctx* ctx, const float* n, const float* w, unsi
     const int nb = ctx->nb, np = nb * (nb + 1) / 2;
     const int nt = (int)ctx->Nabc.size();
     const long M = ctx->nmodes;
+    const long Mp = (std::max(M, 1L) + 1) / 2 * 2;   // row stride of the compact arrays
+    // the split mode takes the Gram on the tensor cores from weighted Z rows; the others weight inside k_gram
+    const bool tc_gram = ctx->prec == POLYBIN_SPLIT_TF32X3 && sizeof(T) == 4;
     int rc;
     T* a1 = (T*)u->a[0];
     T* a2 = (T*)u->a[1];
@@ -514,7 +527,7 @@ static int bk_fisher_draw(polybin_ctx* ctx, const float* n, const float* w, unsi
         uw::k_qcomb<T><<<grid1d(nbox), 256, 0, ctx->stream>>>(pairs + (size_t)2 * np * nbox, pairs + (size_t)3 * np * nbox,
                                                               pab, pbc, pac, a, b, c, T(2.0 / dl), ctx->gx, ctx->gy,
                                                               ctx->gz, ctx->d_lut, ctx->smax, q);
-        uw::k_gather<T><<<grid1d(M), 256, 0, ctx->stream>>>(q, ctx->d_offs, M, Yc + (size_t)t * M);
+        uw::k_gather<T><<<grid1d(M), 256, 0, ctx->stream>>>(q, ctx->d_offs, M, Yc + (size_t)t * Mp);
         // Z_a: fields s a1, s a2 -> real map -> times s -> forward -> compact
         uw::k_qcomb<T><<<grid1d(nbox), 256, 0, ctx->stream>>>(pairs, pairs + (size_t)np * nbox, pab, pbc, pac, a, b, c,
                                                               T(2.0 / dl), ctx->gx, ctx->gy, ctx->gz, ctx->d_lut,
@@ -522,11 +535,17 @@ static int bk_fisher_draw(polybin_ctx* ctx, const float* n, const float* w, unsi
         ctx->launches += 3;
         if ((rc = run_inverse_box<T>(ctx, q, (C<T>*)u->v1, (C<T>*)u->v2, (T*)u->xmap, (const T*)nullptr))) return rc;
         if ((rc = run_forward<T, T, float>(ctx, (const T*)u->xmap, w, n, (C<T>*)W.t1, (C<T>*)W.t2, q))) return rc;
-        uw::k_gather<T><<<grid1d(M), 256, 0, ctx->stream>>>(q, ctx->d_offs, M, Zc + (size_t)t * M);
+        uw::k_gather<T><<<grid1d(M), 256, 0, ctx->stream>>>(q, ctx->d_offs, M, Zc + (size_t)t * Mp,
+                                                            tc_gram ? ctx->d_coef : nullptr);
         ctx->launches++;
     }
+    if (tc_gram) {
+        // F += (1/24)(1/N) Re sum_m w_m conj(Z_a) Y_b as a real Gram over interleaved (re, im): K = 2 Mp
+        PB_CUDA_OK(cudaGetLastError());
+        return run_gram_tc(ctx, (const float*)Zc, nt, (const float*)Yc, nt, 2 * Mp, 1.0 / (24.0 * (double)N), u->dF);
+    }
     dim3 g((nt + 31) / 32, (nt + 31) / 32, 1);
-    uw::k_gram<T><<<g, 256, 0, ctx->stream>>>(Zc, Yc, ctx->d_coef, nt, nt, M, 1.0 / (24.0 * (double)N), u->dF);
+    uw::k_gram<T><<<g, 256, 0, ctx->stream>>>(Zc, Yc, ctx->d_coef, nt, nt, M, Mp, 1.0 / (24.0 * (double)N), u->dF);
     ctx->launches++;
     PB_CUDA_OK(cudaGetLastError());
     return POLYBIN_OK;
