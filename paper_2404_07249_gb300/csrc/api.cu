@@ -83,12 +83,15 @@ template <> const double2* twiddles<double>(polybin_ctx* ctx, int axis) { return
 
 // ----------------------------------------------------------------------------------------------- pipelines
 
-// a1: pruned forward transform of one real field (optionally times m1 * m2) into the box.
+// a1: pruned forward transform of one real field on grid ig (optionally times m1 * m2) into the box of the wave
+// numbers |n_i| <= m (the same box on every grid with more than 2m points per axis).
 template <typename T, typename TIN, typename TM>
-int run_forward(polybin_ctx* ctx, const TIN* in, const TM* m1, const TM* m2, C<T>* t1, C<T>* t2, C<T>* box) {
-    const int N0 = ctx->N[0], N1 = ctx->N[1], N2 = ctx->N[2];
+int run_forward(polybin_ctx* ctx, const TIN* in, const TM* m1, const TM* m2, C<T>* t1, C<T>* t2, C<T>* box,
+                const InvGrid& ig) {
+    const int N0 = ig.N[0], N1 = ig.N[1], N2 = ig.N[2];
     const int Bz = ctx->gz.cnt, By = ctx->gy.cnt;
     const long nlines = (long)N0 * N1;
+    auto tw = [&](int a) { return (const C<T>*)(sizeof(T) == 4 ? ig.tw_f[a] : ig.tw_d[a]); };
     int rc = POLYBIN_OK;
     StageTimer timer(ctx, kStageForward);
     {
@@ -97,8 +100,7 @@ int run_forward(polybin_ctx* ctx, const TIN* in, const TM* m1, const TM* m2, C<T
         const unsigned nblk = (unsigned)((nlines + 2 * LP - 1) / (2 * LP));
         PB_WITH_NT(N2, NT, {
             if ((rc = set_smem<T>(ctx, (const void*)k_fwd_z<T, TIN, TM, NT>, sm))) return rc;
-            k_fwd_z<T, TIN, TM, NT><<<nblk, 256, sm, ctx->stream>>>(in, m1, m2, t1, nlines, Bz, ctx->plan[2],
-                                                                    twiddles<T>(ctx, 2), LP);
+            k_fwd_z<T, TIN, TM, NT><<<nblk, 256, sm, ctx->stream>>>(in, m1, m2, t1, nlines, Bz, ig.plan[2], tw(2), LP);
         })
         if ((rc = launch_check(ctx, "k_fwd_z"))) return rc;
     }
@@ -113,7 +115,7 @@ int run_forward(polybin_ctx* ctx, const TIN* in, const TM* m1, const TM* m2, C<T
         dim3 grid((Bz + TK - 1) / TK, N0, 1);
         PB_WITH_NT(N1, NT, {
             if ((rc = set_smem<T>(ctx, (const void*)k_col<T, -1, NT>, sm))) return rc;
-            k_col<T, -1, NT><<<grid, 256, sm, ctx->stream>>>(b, ctx->plan[1], twiddles<T>(ctx, 1), TK);
+            k_col<T, -1, NT><<<grid, 256, sm, ctx->stream>>>(b, ig.plan[1], tw(1), TK);
         })
         if ((rc = launch_check(ctx, "k_col fwd y"))) return rc;
     }
@@ -129,11 +131,16 @@ int run_forward(polybin_ctx* ctx, const TIN* in, const TM* m1, const TM* m2, C<T
         dim3 grid((ncols + TK - 1) / TK, 1, 1);
         PB_WITH_NT(N0, NT, {
             if ((rc = set_smem<T>(ctx, (const void*)k_col<T, -1, NT>, sm))) return rc;
-            k_col<T, -1, NT><<<grid, 256, sm, ctx->stream>>>(b, ctx->plan[0], twiddles<T>(ctx, 0), TK);
+            k_col<T, -1, NT><<<grid, 256, sm, ctx->stream>>>(b, ig.plan[0], tw(0), TK);
         })
         if ((rc = launch_check(ctx, "k_col fwd x"))) return rc;
     }
     return POLYBIN_OK;
+}
+
+template <typename T, typename TIN, typename TM>
+int run_forward(polybin_ctx* ctx, const TIN* in, const TM* m1, const TM* m2, C<T>* t1, C<T>* t2, C<T>* box) {
+    return run_forward<T, TIN, TM>(ctx, in, m1, m2, t1, t2, box, ctx->fg);
 }
 
 // a2: shell maps g_b = IFT[Theta_b L_ell D] for all bins on grid ig (box == nullptr: unit spectrum, giving t_b).
@@ -285,6 +292,10 @@ int run_pkbin(polybin_ctx* ctx, const C<T>* box, std::vector<double>& num) {
 }
 
 template int run_forward<float, float, float>(polybin_ctx*, const float*, const float*, const float*, float2*, float2*, float2*);
+template int run_forward<float, float, float>(polybin_ctx*, const float*, const float*, const float*, float2*, float2*,
+                                              float2*, const InvGrid&);
+template int run_forward<double, double, double>(polybin_ctx*, const double*, const double*, const double*, double2*,
+                                                 double2*, double2*, const InvGrid&);
 template int run_forward<double, float, float>(polybin_ctx*, const float*, const float*, const float*, double2*, double2*, double2*);
 template int run_forward<double, double, double>(polybin_ctx*, const double*, const double*, const double*, double2*, double2*, double2*);
 template int run_forward<double, double, float>(polybin_ctx*, const double*, const float*, const float*, double2*, double2*, double2*);

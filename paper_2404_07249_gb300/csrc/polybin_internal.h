@@ -84,6 +84,9 @@ ContractGeom contract_geom(int nb, int nh, long ncell);
 
 template <typename T, typename TIN, typename TM>
 int run_forward(polybin_ctx*, const TIN*, const TM*, const TM*, C<T>*, C<T>*, C<T>*);
+// The same on grid ig (the data grid ctx->fg or the contraction grid ctx->cg; intermediates sized for it).
+template <typename T, typename TIN, typename TM>
+int run_forward(polybin_ctx*, const TIN*, const TM*, const TM*, C<T>*, C<T>*, C<T>*, const InvGrid& ig);
 // Shell maps of all bins on grid `ig` (the data grid ctx->fg or the contraction grid ctx->cg), normalised with the
 // 1/N of the data grid's inverse DFT, so that maps on either grid sample the same band-limited function.
 template <typename T> int run_shells(polybin_ctx*, const C<T>*, C<T>*, C<T>*, T*, int ell, const InvGrid& ig);

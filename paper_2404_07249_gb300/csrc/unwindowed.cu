@@ -464,23 +464,25 @@ static int pk_fisher_draw(polybin_ctx* ctx, const float* n, const float* w, unsi
 
 // ---------------------------------------------------------------------------------------------- B Fisher
 
-// Pair spectra P_xy = FT[g_x g_y] (x <= y, lexicographic) of the shell maps of one box spectrum.
+// Pair spectra P_xy(k) = FT[g_x g_y](k) (x <= y, lexicographic) on the box |n_i| <= m, of the shell maps of one box
+// spectrum.  The product g_x g_y has wave numbers |n_i| <= 2m, so for |k_i| <= m its transform on the contraction grid
+// (more than 3m points per axis: no alias reaches the box) is (N' / N) times the data-grid one: the maps and their
+// products are formed on the contraction grid and the caller multiplies the spectra by cg_ratio = N / N'.
 template <typename T>
 static int pair_spectra(polybin_ctx* ctx, const C<T>* U, C<T>* out) {
     UwState* u = static_cast<UwState*>(ctx->ext);
     Work& W = ctx->w;
-    const long N = ctx->ncell;
+    const long Nc = ctx->cg.ncell;
     const long nbox = (long)ctx->gx.cnt * ctx->gy.cnt * ctx->gz.cnt;
     const int nb = ctx->nb;
     int rc;
     T* g = (T*)u->g2;
-    if ((rc = ensure_fine_inv<T>(ctx))) return rc;
-    if ((rc = run_shells<T>(ctx, U, (C<T>*)W.u1f, (C<T>*)W.u2f, g, 0, ctx->fg))) return rc;
+    if ((rc = run_shells<T>(ctx, U, (C<T>*)W.u1, (C<T>*)W.u2, g, 0, ctx->cg))) return rc;
     int p = 0;
     for (int x = 0; x < nb; ++x)
         for (int y = x; y < nb; ++y, ++p)
-            if ((rc = run_forward<T, T, T>(ctx, g + (size_t)x * N, g + (size_t)y * N, (const T*)nullptr, (C<T>*)W.t1,
-                                           (C<T>*)W.t2, out + (size_t)p * nbox)))
+            if ((rc = run_forward<T, T, T>(ctx, g + (size_t)x * Nc, g + (size_t)y * Nc, (const T*)nullptr, (C<T>*)W.t1,
+                                           (C<T>*)W.t2, out + (size_t)p * nbox, ctx->cg)))
                 return rc;
     return POLYBIN_OK;
 }
@@ -525,13 +527,13 @@ static int bk_fisher_draw(polybin_ctx* ctx, const float* n, const float* w, unsi
                    pac = (long)pair_index(nb, a, c) * nbox;
         // Y_b: fields a1, a2 (compact binned modes)
         uw::k_qcomb<T><<<grid1d(nbox), 256, 0, ctx->stream>>>(pairs + (size_t)2 * np * nbox, pairs + (size_t)3 * np * nbox,
-                                                              pab, pbc, pac, a, b, c, T(2.0 / dl), ctx->gx, ctx->gy,
-                                                              ctx->gz, ctx->d_lut, ctx->smax, q);
+                                                              pab, pbc, pac, a, b, c, T(2.0 / dl * ctx->cg_ratio),
+                                                              ctx->gx, ctx->gy, ctx->gz, ctx->d_lut, ctx->smax, q);
         uw::k_gather<T><<<grid1d(M), 256, 0, ctx->stream>>>(q, ctx->d_offs, M, Yc + (size_t)t * Mp);
         // Z_a: fields s a1, s a2 -> real map -> times s -> forward -> compact
         uw::k_qcomb<T><<<grid1d(nbox), 256, 0, ctx->stream>>>(pairs, pairs + (size_t)np * nbox, pab, pbc, pac, a, b, c,
-                                                              T(2.0 / dl), ctx->gx, ctx->gy, ctx->gz, ctx->d_lut,
-                                                              ctx->smax, q);
+                                                              T(2.0 / dl * ctx->cg_ratio), ctx->gx, ctx->gy, ctx->gz,
+                                                              ctx->d_lut, ctx->smax, q);
         ctx->launches += 3;
         if ((rc = run_inverse_box<T>(ctx, q, (C<T>*)u->v1, (C<T>*)u->v2, (T*)u->xmap, (const T*)nullptr))) return rc;
         if ((rc = run_forward<T, T, float>(ctx, (const T*)u->xmap, w, n, (C<T>*)W.t1, (C<T>*)W.t2, q))) return rc;
