@@ -54,6 +54,9 @@ typedef enum {
  * l_max        : largest even Legendre order of the power spectrum (0, 2 or 4).
  * prec         : a polybin_prec value.
  * cuda_stream  : cudaStream_t to run on (NULL = legacy default stream).
+ * The first POLYBIN_SPLIT_TF32X3 context on a device runs a one-MMA self-check on known operands: the split scheme
+ * takes the tensor core's reading of an FP32 operand (its 13 low bits dropped) as the high part of the maps; if the
+ * device reads it otherwise, polybin_init returns POLYBIN_ETOL (for this and every later split context there).
  * On success *out receives the context (destroy with polybin_destroy); on failure *out is NULL and
  * polybin_last_error(NULL) describes the error. */
 int polybin_init(polybin_ctx** out, const int grid[3], const double boxsize[3], const double* k_edges,

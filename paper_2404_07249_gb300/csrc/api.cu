@@ -674,6 +674,7 @@ extern "C" int polybin_init(polybin_ctx** out, const int grid[3], const double b
     }
     if (!rc) rc = plan_pk(ctx);
     if (!rc) rc = (prec == POLYBIN_FP64) ? alloc_work<double>(ctx, ctx->w) : alloc_work<float>(ctx, ctx->w);
+    if (!rc && prec == POLYBIN_SPLIT_TF32X3) rc = tf32_selfcheck(ctx);
     if (rc) {
         g_init_error = ctx->err;
         polybin_destroy(ctx);

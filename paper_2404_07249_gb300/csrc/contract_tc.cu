@@ -41,6 +41,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstring>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -716,6 +717,70 @@ __global__ void k_wait_selftest(int* err, unsigned limit) {
     }
 }
 
+// ------------------------------------------------------------------------------------------------ self-check
+// What the split-TF32 scheme assumes of the tensor core, checked on known operands: an FP32 B operand is read as TF32
+// by dropping its 13 low bits (B_hi = the raw map), and a TF32 value written to tensor memory as the A operand is
+// used exactly.  A (tensor memory, M = 128, K = 8) has A[0][0] = 1 and A[1][0] = 1 + 2^-10; B (shared memory, N = 16,
+// 128-byte swizzle) has B[0][0] = 1 + 3 2^-12, three quarters of a TF32 unit above 1.  Truncation gives D[0][0] = 1
+// and D[1][0] = 1 + 2^-10; rounding to nearest would give 1 + 2^-10 and (1 + 2^-10)^2.  res: D[0][0], D[1][0] (FP32
+// bit patterns) and a timeout flag.
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t* v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr), "r"(v[0]),
+                 "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]));
+}
+
+__global__ void __launch_bounds__(128, 1) k_tf32_selfcheck(uint32_t* res) {
+    __shared__ __align__(1024) unsigned char sB[16 * 128];
+    __shared__ uint64_t bar;
+    __shared__ uint32_t tslot;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int warp = __shfl_sync(0xffffffffu, tid >> 5, 0);
+    for (int i = tid; i < 16 * 128 / 4; i += 128) reinterpret_cast<uint32_t*>(sB)[i] = 0u;
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_u32(&tslot)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    __syncthreads();
+    if (tid == 0) reinterpret_cast<float*>(sB)[0] = 1.0f + 3.0f * 0x1p-12f;   // row 0, chunk 0 (unswizzled position)
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tslot;
+    {
+        const int r = 32 * warp + lane;                  // TMEM lane of this thread
+        uint32_t v[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+        if (r == 0) v[0] = __float_as_uint(1.0f);
+        if (r == 1) v[0] = __float_as_uint(1.0f + 0x1p-10f);
+        tmem_st8(tmem + ((uint32_t)(32 * warp) << 16), v);
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) {
+        mma_tf32(tmem + 8u, tmem, sdesc_sw128(smem_u32(sB)), idesc_tf32(128, 16), 0u);
+        mma_commit(&bar);
+        unsigned it = 0;
+        for (; it < (1u << 20); ++it)
+            if (mbar_try(&bar, 0)) break;
+        if (lane == 0) res[2] = it == (1u << 20) ? 1u : 0u;
+        tc_fence_after();
+        uint32_t d[16];
+        tmem_ld16(tmem + 8u, d);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (lane < 2) res[lane] = d[0];
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem));
+}
+
 // ------------------------------------------------------------------------------------------------ Gram
 // Tensor-core Gram matrix of the bispectrum Fisher (Sec. 4.3.4, eq. bk-fish-def in Fourier space):
 //   part[s][i][j] = sum_{k in split s} A[i][k] B[j][k],  A = Z (weighted), B = Y as float32 rows [n][K], K = 2 M
@@ -1330,6 +1395,43 @@ static int ell_plan(polybin_ctx* ctx, Plan** out) {
 }  // namespace tc
 
 bool split_tc_available() { return true; }
+
+// Runs k_tf32_selfcheck once per device (the first split-TF32 context on it); POLYBIN_ETOL if the tensor core does
+// not read FP32 operands as the split scheme assumes.
+int tf32_selfcheck(polybin_ctx* ctx) {
+    static std::mutex mu;
+    static int state[256] = {};   // 0 unchecked, 1 ok, -1 failed
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail_cuda(ctx, e, "cudaGetDevice", __FILE__, __LINE__);
+    if (dev < 0 || dev >= 256) return POLYBIN_OK;
+    std::lock_guard<std::mutex> lock(mu);
+    if (state[dev] == 0) {
+        uint32_t* d = nullptr;
+        uint32_t h[3] = {0u, 0u, 1u};
+        e = cudaMalloc(&d, sizeof(h));
+        if (e == cudaSuccess) e = cudaMemsetAsync(d, 0, sizeof(h), ctx->stream);
+        if (e == cudaSuccess) {
+            tc::k_tf32_selfcheck<<<1, 128, 0, ctx->stream>>>(d);
+            ctx->launches += 1;
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (d) cudaFree(d);
+        if (e != cudaSuccess) return fail_cuda(ctx, e, "tf32 self-check", __FILE__, __LINE__);
+        float d00, d10;
+        std::memcpy(&d00, &h[0], 4);
+        std::memcpy(&d10, &h[1], 4);
+        state[dev] = (h[2] == 0u && d00 == 1.0f && d10 == 1.0f + 0x1p-10f) ? 1 : -1;
+        if (state[dev] < 0)
+            return fail(ctx, POLYBIN_ETOL, "tf32 self-check: D00 = %.9g, D10 = %.9g (expected 1 and 1 + 2^-10): the tensor "
+                        "core does not read FP32 operands as TF32 by truncation", (double)d00, (double)d10);
+    }
+    if (state[dev] < 0)
+        return fail(ctx, POLYBIN_ETOL, "tf32 self-check failed on this device: split-TF32 mode unavailable");
+    return POLYBIN_OK;
+}
 
 void destroy_tc(polybin_ctx* ctx) {
     delete static_cast<tc::PlanCache*>(ctx->tc);

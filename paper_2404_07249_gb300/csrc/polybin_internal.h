@@ -103,6 +103,7 @@ void free_work(Work&);
 int resolve_input(polybin_ctx*, const float*, size_t, const float**);
 int ensure_triplets(polybin_ctx*);
 bool split_tc_available();
+int tf32_selfcheck(polybin_ctx*);
 bool tc_shape_ok(long ncell, const float* g, int ng, const float* h, int nh);
 int run_contract_tc(polybin_ctx*, const float*, int, const float*, int, double*, long ncell);
 int prepare_triplet_tc(polybin_ctx*);
