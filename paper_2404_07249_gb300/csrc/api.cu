@@ -215,10 +215,13 @@ int run_shells(polybin_ctx* ctx, const C<T>* box, C<T>* u1, C<T>* u2, T* g, int 
             // register-resident 288-point transform, 128 line pairs per CTA (8 rounds of 16, input staged with
             // cp.async one round ahead)
             const int ppc = 128;
+            int kin_max = 1;
+            for (int i = 0; i < nb; ++i) kin_max = std::max(kin_max, b.it[i].kin);
+            const size_t smz = z288_smem(kin_max);
             dim3 grid288((unsigned)(((nlines + 1) / 2 + ppc - 1) / ppc), nb, 1);
-            if ((rc = set_smem<T>(ctx, (const void*)k_inv_z288, kZ288Smem))) return rc;
-            k_inv_z288<<<grid288, kZ288Threads, kZ288Smem, ctx->stream>>>(b, nlines, 1.f, (const float*)nullptr,
-                                                                         (const float2*)tw(2), ppc);
+            if ((rc = set_smem<T>(ctx, (const void*)k_inv_z288, smz))) return rc;
+            k_inv_z288<<<grid288, kZ288Threads, smz, ctx->stream>>>(b, nlines, 1.f, (const float*)nullptr,
+                                                                    (const float2*)tw(2), ppc);
         } else {
             dim3 grid((unsigned)((nlines + 2 * LP - 1) / (2 * LP)), nb, 1);
             PB_WITH_NT_INV(N2, NT, {

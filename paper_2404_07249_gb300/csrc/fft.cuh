@@ -573,30 +573,29 @@ __device__ __forceinline__ void stage_block(unsigned char* dst, const unsigned c
 }
 
 constexpr int kZ288Threads = 192, kZ288Pairs = 16, kZ288Kmax = 145;
-constexpr int kZ288Rs = 13, kZ288Gs = 24 * kZ288Rs;
-// dynamic shared memory: exchange buffers [16][24 x 13] float2, input stage [32 lines][<= 145] float2
-constexpr size_t kZ288Smem = (size_t)(kZ288Pairs * kZ288Gs + 2 * kZ288Pairs * kZ288Kmax) * sizeof(float2);
+// exchange buffer of a group: 24 rows of 13 (row stride 13: the 12 threads of a group read 12 rows conflict-free),
+// groups 316 float2 apart (316 = 12 mod 16: the two groups of a half-warp cover the 32 banks exactly)
+constexpr int kZ288Rs = 13, kZ288Gs = 316;
+// dynamic shared memory: twiddle table [288] float2, exchange buffers [16][316] float2, input stage [32 lines][kin]
+inline size_t z288_smem(int kin_max) {
+    return (size_t)(288 + kZ288Pairs * kZ288Gs + 2 * kZ288Pairs * kin_max) * sizeof(float2);
+}
 
-static __global__ void __launch_bounds__(192) k_inv_z288(ZInvBatch batch, long nlines, float scale,
-                                                        const float* __restrict__ mulout, const float2* __restrict__ twg,
-                                                        int ppc) {
+static __global__ void __launch_bounds__(192, 3) k_inv_z288(ZInvBatch batch, long nlines, float scale,
+                                                           const float* __restrict__ mulout,
+                                                           const float2* __restrict__ twg, int ppc) {
     constexpr int N = 288, TG = 12, P = 24, G = kZ288Pairs, RS = kZ288Rs, GS = kZ288Gs;
     extern __shared__ __align__(16) float2 z288_smem[];
-    float2* sbuf = z288_smem;                         // exchange buffers
-    float2* stage = z288_smem + G * GS;               // the round's input lines, [2 G][kin]
+    float2* stw = z288_smem;                          // e^{-2 pi i m / 288}
+    float2* sbuf = z288_smem + N;                     // exchange buffers
+    float2* stage = sbuf + G * GS;                    // the round's input lines, [2 G][kin]
     const ZInvItem item = batch.it[blockIdx.y];
     const float2* __restrict__ in = static_cast<const float2*>(item.in);
     float* __restrict__ out = static_cast<float*>(item.out);
-    const int kin = item.kin;                         // <= 145 (the Hermitian half of 288 points)
+    const int kin = item.kin;                         // <= kin_max of the launch (<= 145, the Hermitian half)
     const int tid = threadIdx.x, g = tid / TG, t = tid - g * TG;
     float2* buf = sbuf + g * GS;
-    // stage-1 twiddles w288^(t n1) = conj(tw[t n1 mod N])
-    float2 w1[P];
-#pragma unroll
-    for (int n1 = 1; n1 < P; ++n1) {
-        const float2 w = twg[(t * n1) % N];
-        w1[n1] = make_float2(w.x, -w.y);
-    }
+    for (int i = tid; i < N; i += kZ288Threads) stw[i] = twg[i];   // visible after the first round's barrier
     const long npairs = (nlines + 1) / 2;
     const long p_beg = (long)blockIdx.x * ppc;
     const long p_end = min(npairs, p_beg + ppc);
@@ -641,8 +640,9 @@ static __global__ void __launch_bounds__(192) k_inv_z288(ZInvBatch batch, long n
         if (p0 + G < p_end) issue(p0 + G);
         // stage 1: 24-point DFT over j, twiddle w288^(t n1); rows n1 of the group's exchange buffer
         dft24<float, +1>(v);
+        // twiddle w288^(t n1) = conj(tw[t n1 mod N])
 #pragma unroll
-        for (int n1 = 1; n1 < P; ++n1) v[n1] = mul<float>(v[n1], w1[n1]);
+        for (int n1 = 1; n1 < P; ++n1) v[n1] = mulc<float>(v[n1], stw[(t * n1) % N]);
 #pragma unroll
         for (int n1 = 0; n1 < P; ++n1) buf[n1 * RS + t] = v[n1];
         __syncthreads();
