@@ -33,10 +33,12 @@ UNIT = "estimates/s"
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the contraction kernel, from one ncu
 # capture of the named workload and precision, keyed by the SHA-256 of the kernel source the capture ran.  The
-# figure is reported only while that source is unchanged; otherwise traffic is null.
+# figure is reported only while that source is unchanged; otherwise traffic is null.  The capture ran the 512^3
+# workload's bins, field model and box on a 320^3 data grid, whose contraction grid (288^3) is the 512^3 workload's:
+# the contraction launch is the same (the same 30 maps of 288^3 cells).
 CAPTURED_TRAFFIC = {
-    ("b76286c85437e78f11ec142b57b46b0877f178388128e169eab534287419c00f", "lognormal_kaiser512", "split"):
-        16111293184 + 5062400,
+    ("26e64de9d9ac80a10c998e59800f90c7f9ff51f7483631f93ad3917397310211", "lognormal_kaiser512", "split"):
+        2866895616 + 3286016,
 }
 
 
