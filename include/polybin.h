@@ -133,7 +133,7 @@ int polybin_bk_pk_ideal(polybin_ctx* ctx, const float* delta, int batch, double*
  * power-spectrum Fisher draws.  Parameter index alpha: power spectrum (ell, b) ell-major, index
  * (ell / 2) * n_kbins + b; bispectrum the closed triplets in polybin_get_triplets order. */
 
-enum { POLYBIN_FISHER_PK = 0, POLYBIN_FISHER_BK = 1 };
+enum { POLYBIN_FISHER_PK = 0, POLYBIN_FISHER_BK = 1, POLYBIN_FISHER_PK_LOCAL = 2 };
 
 /* w = 1 / (n P_FKP + 1) (Sec. 2.4, eq. Sinv-fkp), evaluated in FP64 and stored as float32 (device arrays). */
 int polybin_fkp_weights(polybin_ctx* ctx, const float* n_dev, double p_fkp, float* w_dev);
@@ -159,6 +159,29 @@ int polybin_fisher_draws(polybin_ctx* ctx, const float* n_dev, const float* w_de
 
 /* Install a Fisher matrix computed elsewhere (host [n_alpha][n_alpha]); its inverse is computed in FP64 on the GPU. */
 int polybin_set_fisher(polybin_ctx* ctx, int which, const double* fisher);
+
+/* ---- local (Yamamoto) line of sight, Sec. 3.1 eqs. cf-pk-def, xi-p-alpha-deriv and Sec. 3.3 ----------------------
+ * The line of sight of a pair is taken at each end point, x / |x| from the observer, symmetrised; the Legendre
+ * polynomials are expanded in normalised real spherical harmonics, sum_m Ybar_lm(a) Ybar_lm(b) = L_l(a.b) (the set of
+ * the footnote of Sec. 3.3.1 up to signs within each l, which cancel in every sum the estimators take).  Cell centres
+ * are at (i + 1/2) L / N_a - L / 2 (the box centred on the origin).  Even multipoles ell = 0 .. l_max. */
+
+/* Observer position in box coordinates (Mpc/h, box centred on the origin; default (0, 0, 0), the box centre).  A
+ * local Fisher matrix computed for another observer is discarded. */
+int polybin_set_observer(polybin_ctx* ctx, const double pos[3]);
+
+/* which = POLYBIN_FISHER_PK_LOCAL in polybin_fisher / polybin_fisher_draws / polybin_set_fisher: the P Fisher matrix
+ * with the local line of sight (Sec. 3.3.2, eq. fish-from-Q with Q_alpha of eq. Q-alpha-local and the asymmetric
+ * Q^asym_alpha[a](k) = Theta_b sum_m Ybar_lm(k) FT[Ybar_lm a](k)), alpha as for POLYBIN_FISHER_PK.  Per draw it takes
+ * (l_max + 1)^2 forward transforms of the draw, as many of S^-1 P a, 2 l + 2 sets of n_kbins inverse transforms per
+ * ell > 0 and one forward transform per alpha. */
+
+/* Unwindowed P_ell with a local line of sight: p_num_alpha = 1/2 (1/N) sum_{k in b} sum_m Ybar_lm(k)
+ * Re(conj(FT[Ybar_lm w d](k)) FT[w d](k)) (Sec. 3.3.1, eq. pk-num-fft, pixel units), p = F^-1 p_num with the local
+ * Fisher matrix, pk_out = p V / N (host [n_alpha], may be NULL; needs polybin_fisher(POLYBIN_FISHER_PK_LOCAL) or
+ * polybin_set_fisher first).  pnum_out: host [n_alpha] or NULL.  d, w: device arrays as for polybin_pk_unwindowed. */
+int polybin_pk_unwindowed_local(polybin_ctx* ctx, const float* d_dev, const float* w_dev, double* pk_out,
+                                double* pnum_out);
 
 /* Unwindowed P_ell (Sec. 3.2, eq. pk-estimator-def; no bias term in this data model):
  * p_num_alpha = 1/2 (1/N) sum_{k in b} L_ell |FT[w d]|^2 (pixel units), p = F^-1 p_num, pk_out = p V / N

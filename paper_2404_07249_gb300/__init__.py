@@ -60,12 +60,15 @@ _SIGS = {
     "polybin_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
                                      ctypes.c_void_p]),
     "polybin_last_path": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
+    "polybin_set_observer": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "polybin_pk_unwindowed_local": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                   ctypes.c_void_p]),
     "polybin_bk_ideal_multipoles": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                                    ctypes.c_void_p]),
     "polybin_contraction_grid": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
 }
 
-FISHER_PK, FISHER_BK = 0, 1
+FISHER_PK, FISHER_BK, FISHER_PK_LOCAL = 0, 1, 2
 PATH_SIMT_FP64, PATH_SIMT_FP32, PATH_TENSOR_SPLIT_TF32X3 = 0, 1, 2
 
 STAGES = ("forward", "shells", "contract", "pk_bin")
@@ -235,7 +238,21 @@ class PolyBin:
 
     # ---- masked estimators
     def n_alpha(self, which: int) -> int:
-        return (self.lmax // 2 + 1) * self.nb if which == FISHER_PK else self.num_triplets()
+        return self.num_triplets() if which == FISHER_BK else (self.lmax // 2 + 1) * self.nb
+
+    def set_observer(self, pos):
+        """Observer of the local line of sight, box coordinates centred on the origin (Mpc/h)."""
+        p = np.ascontiguousarray(pos, dtype=np.float64)
+        self._check(self.lib.polybin_set_observer(self.ctx, _ptr(p)), "polybin_set_observer")
+
+    def pk_unwindowed_local(self, d_dev, w_dev, with_estimate: bool = True):
+        na = self.n_alpha(FISHER_PK_LOCAL)
+        p = np.zeros(na)
+        pnum = np.zeros(na)
+        self._check(self.lib.polybin_pk_unwindowed_local(self.ctx, _ptr(_f32(d_dev)), _ptr(_f32(w_dev)),
+                                                         _ptr(p) if with_estimate else None, _ptr(pnum)),
+                    "polybin_pk_unwindowed_local")
+        return (p if with_estimate else None), pnum
 
     def fkp_weights(self, n_dev, p_fkp: float):
         import torch

@@ -148,6 +148,11 @@ int run_forward(polybin_ctx* ctx, const TIN* in, const TM* m1, const TM* m2, C<T
 // same band-limited function as on the data grid, sampled at fewer points.
 template <typename T>
 int run_shells(polybin_ctx* ctx, const C<T>* box, C<T>* u1, C<T>* u2, T* g, int ell, const InvGrid& ig) {
+    return run_shells_m<T>(ctx, box, u1, u2, g, ell, kLegendreM, ig);
+}
+
+template <typename T>
+int run_shells_m(polybin_ctx* ctx, const C<T>* box, C<T>* u1, C<T>* u2, T* g, int ell, int m, const InvGrid& ig) {
     const int N0 = ig.N[0], N1 = ig.N[1], N2 = ig.N[2];
     const int nb = ctx->nb;
     int rc = POLYBIN_OK;
@@ -164,6 +169,7 @@ int run_shells(polybin_ctx* ctx, const C<T>* box, C<T>* u1, C<T>* u2, T* g, int 
             b.it[i].rx = bb.rx; b.it[i].ry = bb.ry; b.it[i].rz = bb.rz;
             b.it[i].bin = i;
             b.it[i].ell = ell;
+            b.it[i].m = m;
             maxcols = std::max(maxcols, bb.ry.cnt * bb.rz.cnt);
         }
         dim3 grid((maxcols + TK - 1) / TK, nb, 1);
@@ -308,6 +314,8 @@ template int run_pkbin_dev<float>(polybin_ctx*, const float2*);
 template int run_pkbin_dev<double>(polybin_ctx*, const double2*);
 template int run_shells<float>(polybin_ctx*, const float2*, float2*, float2*, float*, int, const InvGrid&);
 template int run_shells<double>(polybin_ctx*, const double2*, double2*, double2*, double*, int, const InvGrid&);
+template int run_shells_m<float>(polybin_ctx*, const float2*, float2*, float2*, float*, int, int, const InvGrid&);
+template int run_shells_m<double>(polybin_ctx*, const double2*, double2*, double2*, double*, int, int, const InvGrid&);
 template int run_contract<float>(polybin_ctx*, const float*, int, const float*, int, double*, size_t, double*, long);
 template int run_contract<double>(polybin_ctx*, const double*, int, const double*, int, double*, size_t, double*, long);
 

@@ -10,6 +10,7 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "ylm.cuh"
 
 namespace pb {
 
@@ -755,11 +756,13 @@ __global__ void __launch_bounds__(256) k_col(ColBatch batch, FftPlan plan, const
 // each multiplied by Theta_b(|n|) (bin lookup on the integer |n|^2), an optional per-mode weight
 // (|n|^2-indexed table wtab, or the Legendre factor of the line of sight), and `scale`.
 // spec == nullptr means a unit spectrum (the t_b maps that normalise the bispectrum).
+constexpr int kLegendreM = 100;   // XInvItem::m of the global line of sight (weight L_ell(mu))
 struct XInvItem {
     void* out;            // C<T>* [n0][ry.cnt * rz.cnt]
     AxisRange rx, ry, rz; // bin bounding box
     int bin;
-    int ell;              // Legendre weight L_ell(mu), mu = n_z / |n| (0: none)
+    int ell;              // 0: no weight; else L_ell(mu), mu = n_z / |n| (m == kLegendreM) or Ybar_lm(n / |n|)
+    int m;
 };
 struct XInvBatch {
     XInvItem it[kMaxItems];
@@ -797,9 +800,12 @@ __global__ void __launch_bounds__(256) k_inv_x_filter(XInvBatch batch, const C<T
         const int s = fx * fx + fy * fy + fz * fz;
         if (s > smax || lut[s] != item.bin) continue;
         T wgt = scale;
-        if (item.ell) {
+        if (item.ell && item.m == kLegendreM) {
             const T mu2 = T(fz * fz) / T(s);
             wgt *= item.ell == 2 ? T(0.5) * (T(3) * mu2 - T(1)) : (T(35) * mu2 * mu2 - T(30) * mu2 + T(3)) / T(8);
+        } else if (item.ell) {
+            const T inv = T(1) / sqrt(T(s));
+            wgt *= ybar<T>(item.ell, item.m, T(fx) * inv, T(fy) * inv, T(fz) * inv);
         }
         C<T> v = mk<T>(wgt, T(0));
         if (spec) {

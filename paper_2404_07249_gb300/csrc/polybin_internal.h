@@ -90,6 +90,9 @@ int run_forward(polybin_ctx*, const TIN*, const TM*, const TM*, C<T>*, C<T>*, C<
 // Shell maps of all bins on grid `ig` (the data grid ctx->fg or the contraction grid ctx->cg), normalised with the
 // 1/N of the data grid's inverse DFT, so that maps on either grid sample the same band-limited function.
 template <typename T> int run_shells(polybin_ctx*, const C<T>*, C<T>*, C<T>*, T*, int ell, const InvGrid& ig);
+// The same with the weight Ybar_lm(k / |k|) of the local line of sight (m in [-ell, ell]; m = kLegendreM: L_ell(mu)).
+template <typename T>
+int run_shells_m(polybin_ctx*, const C<T>*, C<T>*, C<T>*, T*, int ell, int m, const InvGrid& ig);
 template <typename T> int run_pkbin(polybin_ctx*, const C<T>*, std::vector<double>&);
 // Contractions over `ncell` cells (maps of the data grid or of the contraction grid).
 template <typename T> int run_contract(polybin_ctx*, const T*, int, const T*, int, double*, size_t, double*, long ncell);
@@ -194,6 +197,8 @@ struct polybin_ctx {
     int tused = 0;        // slots recorded since the last read-back
     bool topen = false;   // a stage bracket is open (brackets do not nest)
 
+    // observer of the local line of sight, box coordinates centred on the origin (Mpc/h)
+    double observer[3] = {0.0, 0.0, 0.0};
     // the contraction kernel that ran last (polybin_contract_path values), -1 before the first contraction
     int last_path = -1;
     // device error flag of the kernels with bounded waits

@@ -251,6 +251,116 @@ __global__ void k_gemv(const double* __restrict__ M, const double* __restrict__ 
     y[i] = s;
 }
 
+// ---- local (Yamamoto) line of sight: real harmonics Ybar_lm of the cell direction and of the wave vector
+
+// Cell geometry of the data grid: spacing h, half box, observer (box coordinates centred on the origin).
+template <typename T>
+struct CellGeom {
+    int N[3];
+    T h[3], half_l, obs[3];
+};
+
+// out[i] = Ybar_lm(x_i) in[i] (times m1[i] m2[i] when given), x_i the direction of cell i from the observer.
+template <typename T, typename TIN, typename TM>
+__global__ void k_mul_ylm(const TIN* __restrict__ in, const TM* __restrict__ m1, const TM* __restrict__ m2,
+                          T* __restrict__ out, int ell, int m, CellGeom<T> cg) {
+    const long n = (long)cg.N[0] * cg.N[1] * cg.N[2];
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const long k = i % cg.N[2], r = i / cg.N[2];
+        const long j = r % cg.N[1], a = r / cg.N[1];
+        T x, y, z;
+        cell_direction<T>(a, j, k, cg.h, cg.half_l, cg.obs, x, y, z);
+        T v = ybar<T>(ell, m, x, y, z) * T(in[i]);
+        if (m1) v *= T(m1[i]);
+        if (m2) v *= T(m2[i]);
+        out[i] = v;
+    }
+}
+
+// Q[b][i] += fac Ybar_lm(x_i) q[b][i] for the nb maps (one harmonic evaluation a cell).
+template <typename T>
+__global__ void k_ylm_axpy(T* __restrict__ Q, const T* __restrict__ q, int nb, int ell, int m, T fac, CellGeom<T> cg) {
+    const long n = (long)cg.N[0] * cg.N[1] * cg.N[2];
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const long k = i % cg.N[2], r = i / cg.N[2];
+        const long j = r % cg.N[1], a = r / cg.N[1];
+        T x, y, z;
+        cell_direction<T>(a, j, k, cg.h, cg.half_l, cg.obs, x, y, z);
+        const T yv = fac * ybar<T>(ell, m, x, y, z);
+        for (int b = 0; b < nb; ++b) Q[(size_t)b * n + i] += yv * q[(size_t)b * n + i];
+    }
+}
+
+// Direction of box entry o (wave numbers gx.lo + ix, gy.lo + iy, iz); false at n = 0.
+__device__ __forceinline__ bool box_direction(long o, AxisRange gx, AxisRange gy, AxisRange gz, double& x, double& y,
+                                              double& z) {
+    const int iz = (int)(o % gz.cnt);
+    const long r = o / gz.cnt;
+    const int iy = (int)(r % gy.cnt), ix = (int)(r / gy.cnt);
+    const double fx = gx.lo + ix, fy = gy.lo + iy, fz = gz.lo + iz;
+    const double s = fx * fx + fy * fy + fz * fz;
+    if (s <= 0) return false;
+    const double inv = 1.0 / sqrt(s);
+    x = fx * inv; y = fy * inv; z = fz * inv;
+    return true;
+}
+
+// H[o] (= or +=) Ybar_lm(k_o) G[o] over the box (FP64 harmonic, working-precision product).
+template <typename T>
+__global__ void k_ylm_box_accum(const C<T>* __restrict__ G, C<T>* __restrict__ H, int ell, int m, int first,
+                                AxisRange gx, AxisRange gy, AxisRange gz) {
+    const long nbox = (long)gx.cnt * gy.cnt * gz.cnt;
+    for (long o = (long)blockIdx.x * blockDim.x + threadIdx.x; o < nbox; o += (long)gridDim.x * blockDim.x) {
+        double x, y, z;
+        const T yv = box_direction(o, gx, gy, gz, x, y, z) ? (T)ybar<double>(ell, m, x, y, z) : T(0);
+        const C<T> g = G[o];
+        const C<T> v = mk<T>(yv * g.x, yv * g.y);
+        H[o] = first ? v : add<T>(H[o], v);
+    }
+}
+
+// acc[q] (= or +=) Ybar_lm(k_q) box[offs[q]] over the binned modes (FP64 accumulation).
+template <typename T>
+__global__ void k_ylm_gather(const C<T>* __restrict__ box, const int* __restrict__ offs, long M, int ell, int m,
+                             int first, AxisRange gx, AxisRange gy, AxisRange gz, double2* __restrict__ acc) {
+    for (long q = (long)blockIdx.x * blockDim.x + threadIdx.x; q < M; q += (long)gridDim.x * blockDim.x) {
+        const long o = offs[q];
+        double x, y, z;
+        const double yv = box_direction(o, gx, gy, gz, x, y, z) ? ybar<double>(ell, m, x, y, z) : 0.0;
+        const C<T> g = box[o];
+        const double2 v = make_double2(yv * (double)g.x, yv * (double)g.y);
+        acc[q] = first ? v : make_double2(acc[q].x + v.x, acc[q].y + v.y);
+    }
+}
+
+// out[b][seg][l] = sum_{binned modes q of bin b} w_q Re(conj(X[offs[q]]) Y[l][q])  (w_q = 1 or 2: the half spectrum).
+template <typename T>
+__global__ void __launch_bounds__(256) k_cross_bin_local(const C<T>* __restrict__ X, const double2* __restrict__ Y,
+                                                         const int* __restrict__ offs, const double* __restrict__ wq,
+                                                         long M, const int* __restrict__ bin_start, int nell,
+                                                         int seg_len, double* __restrict__ partial) {
+    __shared__ double red[256 * 3];
+    const int b = blockIdx.x, seg = blockIdx.y;
+    const long beg = bin_start[b] + (long)seg * seg_len;
+    const long end = min((long)bin_start[b + 1], beg + seg_len);
+    double s[3] = {0.0, 0.0, 0.0};
+    for (long q = beg + threadIdx.x; q < end; q += blockDim.x) {
+        const C<T> x = X[offs[q]];
+        for (int l = 0; l < nell; ++l) {
+            const double2 y = Y[(long)l * M + q];
+            s[l] += wq[q] * ((double)x.x * y.x + (double)x.y * y.y);
+        }
+    }
+    for (int l = 0; l < 3; ++l) red[l * 256 + threadIdx.x] = s[l];
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int l = 0; l < 3; ++l) red[l * 256 + threadIdx.x] += red[l * 256 + threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < nell) partial[((long)b * gridDim.y + seg) * nell + threadIdx.x] = red[threadIdx.x * 256];
+}
+
 }  // namespace uw
 
 // ---------------------------------------------------------------------------------------------- state
@@ -276,12 +386,21 @@ struct UwState {
     double* dFp_inv = nullptr;
     double* dFb_inv = nullptr;
     bool have_p = false, have_b = false;
+    // local line of sight: compact sum_m Ybar_lm(k) FT[Ybar_lm u](k) per ell [3][M]; a box of the same sums; nb maps of
+    // one harmonic's inverse transforms; the Fisher matrix and its inverse
+    double2* ylc = nullptr;
+    void* hbox = nullptr;
+    void* g3 = nullptr;
+    std::vector<double> Fl, Fl_inv;
+    double* dFl_inv = nullptr;
+    bool have_l = false;
 };
 
 static void uw_free(UwState* u) {
     if (!u) return;
     void* ptrs[] = {u->g2, u->xmap, u->a[0], u->a[1], u->spec[0], u->spec[1], u->spec[2], u->spec[3], u->pairs, u->qbox,
-                    u->zc, u->yc, u->v1, u->v2, u->dF, u->dpart, u->dvec, u->dvec2, u->dinfo, u->dFp_inv, u->dFb_inv};
+                    u->zc, u->yc, u->v1, u->v2, u->dF, u->dpart, u->dvec, u->dvec2, u->dinfo, u->dFp_inv, u->dFb_inv,
+                    u->ylc, u->hbox, u->g3, u->dFl_inv};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete u;
@@ -462,6 +581,164 @@ static int pk_fisher_draw(polybin_ctx* ctx, const float* n, const float* w, unsi
     return POLYBIN_OK;
 }
 
+// ---------------------------------------------------------------------------------------------- local line of sight
+
+template <typename T>
+static uw::CellGeom<T> cell_geom(const polybin_ctx* ctx) {
+    uw::CellGeom<T> g;
+    for (int a = 0; a < 3; ++a) {
+        g.N[a] = ctx->N[a];
+        g.h[a] = T(ctx->L / ctx->N[a]);
+        g.obs[a] = T(ctx->observer[a]);
+    }
+    g.half_l = T(0.5 * ctx->L);
+    return g;
+}
+
+// Workspace of the local line of sight: compact harmonic sums [3][M], one box, nb data-grid maps (Fisher only).
+template <typename T>
+static int uw_alloc_local(polybin_ctx* ctx, bool fisher) {
+    UwState* u = static_cast<UwState*>(ctx->ext);
+    const long nbox = (long)ctx->gx.cnt * ctx->gy.cnt * ctx->gz.cnt;
+    if (!u->ylc) PB_CUDA_OK(cudaMalloc(&u->ylc, sizeof(double2) * 3 * std::max(ctx->nmodes, 1L)));
+    if (!u->hbox) PB_CUDA_OK(cudaMalloc(&u->hbox, sizeof(C<T>) * nbox));
+    if (fisher && !u->g3) PB_CUDA_OK(cudaMalloc(&u->g3, sizeof(T) * (size_t)ctx->nb * ctx->ncell));
+    return POLYBIN_OK;
+}
+
+// u->ylc[l] = sum_m Ybar_lm(k) FT[Ybar_lm v](k) on the binned modes, l = 0 .. lmax/2 (l = 0: FT[v]), for the field
+// v = in m1 m2 (multipliers optional); ubox receives FT[v] (the asymmetric derivative of Sec. 3.3.2 before Theta_b).
+template <typename T, typename TIN>
+static int local_asym(polybin_ctx* ctx, const TIN* in, const float* m1, const float* m2, C<T>* ubox) {
+    UwState* u = static_cast<UwState*>(ctx->ext);
+    Work& W = ctx->w;
+    const long M = ctx->nmodes, N = ctx->ncell;
+    const uw::CellGeom<T> cg = cell_geom<T>(ctx);
+    int rc;
+    if ((rc = run_forward<T, TIN, float>(ctx, in, m1, m2, (C<T>*)W.t1, (C<T>*)W.t2, ubox))) return rc;
+    uw::k_ylm_gather<T><<<grid1d(M), 256, 0, ctx->stream>>>(ubox, ctx->d_offs, M, 0, 0, 1, ctx->gx, ctx->gy, ctx->gz,
+                                                            u->ylc);
+    ctx->launches++;
+    C<T>* tmp = (C<T>*)u->spec[2];
+    for (int il = 1; il < ctx->nell; ++il) {
+        const int ell = 2 * il;
+        for (int m = -ell; m <= ell; ++m) {
+            uw::k_mul_ylm<T, TIN, float><<<grid1d(N), 256, 0, ctx->stream>>>(in, m1, m2, (T*)u->xmap, ell, m, cg);
+            ctx->launches++;
+            if ((rc = run_forward<T, T, float>(ctx, (const T*)u->xmap, (const float*)nullptr, (const float*)nullptr,
+                                               (C<T>*)W.t1, (C<T>*)W.t2, tmp)))
+                return rc;
+            uw::k_ylm_gather<T><<<grid1d(M), 256, 0, ctx->stream>>>(tmp, ctx->d_offs, M, ell, m, m == -ell ? 1 : 0,
+                                                                    ctx->gx, ctx->gy, ctx->gz, u->ylc + (size_t)il * M);
+            ctx->launches++;
+        }
+    }
+    PB_CUDA_OK(cudaGetLastError());
+    return POLYBIN_OK;
+}
+
+// out[l][b] = sum_{k in b} w_k Re(conj(X(k)) ylc[l](k)) over the full k-grid (host result).
+template <typename T>
+static int run_cross_local(polybin_ctx* ctx, const C<T>* X, std::vector<double>& out) {
+    UwState* u = static_cast<UwState*>(ctx->ext);
+    const int nb = ctx->nb, nell = ctx->nell;
+    uw::k_cross_bin_local<T><<<dim3(nb, ctx->pk_nseg, 1), 256, 0, ctx->stream>>>(
+        X, u->ylc, ctx->d_offs, ctx->d_coef, ctx->nmodes, ctx->d_bin_start, nell, ctx->pk_seg_len, u->dpart);
+    ctx->launches++;
+    PB_CUDA_OK(cudaGetLastError());
+    std::vector<double> part((size_t)nb * ctx->pk_nseg * nell);
+    PB_CUDA_OK(cudaMemcpyAsync(part.data(), u->dpart, part.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    PB_CUDA_OK(cudaStreamSynchronize(ctx->stream));
+    out.assign((size_t)nell * nb, 0.0);
+    for (int b = 0; b < nb; ++b)
+        for (int sg = 0; sg < ctx->pk_nseg; ++sg)
+            for (int l = 0; l < nell; ++l) out[(size_t)l * nb + b] += part[((size_t)b * ctx->pk_nseg + sg) * nell + l];
+    return POLYBIN_OK;
+}
+
+// Numerator with a local line of sight (Sec. 3.3.1, eq. pk-num-fft), pixel units:
+// p_num(l, b) = 1/2 (1/N) sum_{k in b} sum_m Ybar_lm(k) Re(conj(FT[Ybar_lm u]) FT[u]),  u = w d.
+template <typename T>
+static int pk_numerator_local_t(polybin_ctx* ctx, const float* d, const float* w, std::vector<double>& pnum) {
+    UwState* u = static_cast<UwState*>(ctx->ext);
+    int rc;
+    C<T>* U = (C<T>*)u->spec[0];
+    if ((rc = local_asym<T, float>(ctx, d, w, (const float*)nullptr, U))) return rc;
+    std::vector<double> num;
+    if ((rc = run_cross_local<T>(ctx, U, num))) return rc;
+    pnum.resize(num.size());
+    for (size_t i = 0; i < num.size(); ++i) pnum[i] = 0.5 * num[i] / (double)ctx->ncell;
+    return POLYBIN_OK;
+}
+
+// One Monte Carlo term of the P Fisher matrix with a local line of sight (Sec. 3.3.2, eqs. Q-alpha-local,
+// fish-from-Q; A = I), pixel units, host [na][na]:
+//   F[(l,b)][(l',b')] = 1/2 (1/N) Re sum_{k in b'} conj(FT[s Q_(l,b)[s a]]) sum_m Ybar_l'm(k) FT[Ybar_l'm a](k),
+//   Q_(l,b)[v] = 1/2 sum_m { Ybar_lm(x) IFT[Theta_b Ybar_lm FT[v]] + IFT[Theta_b Ybar_lm FT[Ybar_lm v]] },  s = w n
+// (for l = 0 both terms are IFT[Theta_b FT[v]]).  The second terms are summed over m in k-space (one set of inverse
+// transforms per l); the first take one set a harmonic, multiplied by Ybar_lm(x) and accumulated.
+template <typename T>
+static int pk_fisher_draw_local(polybin_ctx* ctx, const float* n, const float* w, unsigned long long seed, int r,
+                                std::vector<double>& F) {
+    UwState* u = static_cast<UwState*>(ctx->ext);
+    Work& W = ctx->w;
+    const long N = ctx->ncell;
+    const int nb = ctx->nb, nell = ctx->nell, na = nell * nb;
+    const uw::CellGeom<T> cg = cell_geom<T>(ctx);
+    int rc;
+    if ((rc = ensure_fine_inv<T>(ctx))) return rc;
+    T* a = (T*)u->a[0];
+    uw::k_draw<T><<<grid1d((N + 3) / 4), 256, 0, ctx->stream>>>(a, N, seed, (uint32_t)r, 2u);
+    ctx->launches++;
+    // asymmetric side: ylc[l'] from a
+    if ((rc = local_asym<T, T>(ctx, (const T*)a, (const float*)nullptr, (const float*)nullptr, (C<T>*)u->spec[0])))
+        return rc;
+    // SA = FT[s a]
+    C<T>* SA = (C<T>*)u->spec[1];
+    if ((rc = run_forward<T, T, float>(ctx, a, w, n, (C<T>*)W.t1, (C<T>*)W.t2, SA))) return rc;
+    F.assign((size_t)na * na, 0.0);
+    T* Q = (T*)u->g2;
+    T* q = (T*)u->g3;
+    C<T>* H = (C<T>*)u->hbox;
+    C<T>* X = (C<T>*)u->spec[3];
+    std::vector<double> cross;
+    for (int il = 0; il < nell; ++il) {
+        const int ell = 2 * il;
+        double fac = 1.0;
+        if (ell == 0) {
+            if ((rc = run_shells<T>(ctx, SA, (C<T>*)W.u1f, (C<T>*)W.u2f, Q, 0, ctx->fg))) return rc;
+        } else {
+            fac = 0.5;
+            for (int m = -ell; m <= ell; ++m) {
+                uw::k_mul_ylm<T, T, float><<<grid1d(N), 256, 0, ctx->stream>>>(a, w, n, (T*)u->xmap, ell, m, cg);
+                ctx->launches++;
+                if ((rc = run_forward<T, T, float>(ctx, (const T*)u->xmap, (const float*)nullptr, (const float*)nullptr,
+                                                   (C<T>*)W.t1, (C<T>*)W.t2, (C<T>*)u->spec[2])))
+                    return rc;
+                uw::k_ylm_box_accum<T><<<grid1d((long)ctx->gx.cnt * ctx->gy.cnt * ctx->gz.cnt), 256, 0, ctx->stream>>>(
+                    (const C<T>*)u->spec[2], H, ell, m, m == -ell ? 1 : 0, ctx->gx, ctx->gy, ctx->gz);
+                ctx->launches++;
+            }
+            if ((rc = run_shells<T>(ctx, H, (C<T>*)W.u1f, (C<T>*)W.u2f, Q, 0, ctx->fg))) return rc;
+            for (int m = -ell; m <= ell; ++m) {
+                if ((rc = run_shells_m<T>(ctx, SA, (C<T>*)W.u1f, (C<T>*)W.u2f, q, ell, m, ctx->fg))) return rc;
+                uw::k_ylm_axpy<T><<<grid1d(N), 256, 0, ctx->stream>>>(Q, q, nb, ell, m, T(1), cg);
+                ctx->launches++;
+            }
+        }
+        for (int b = 0; b < nb; ++b) {
+            if ((rc = run_forward<T, T, float>(ctx, Q + (size_t)b * N, w, n, (C<T>*)W.t1, (C<T>*)W.t2, X))) return rc;
+            if ((rc = run_cross_local<T>(ctx, X, cross))) return rc;
+            const int alpha = il * nb + b;
+            for (int jl = 0; jl < nell; ++jl)
+                for (int b2 = 0; b2 < nb; ++b2)
+                    F[(size_t)alpha * na + jl * nb + b2] = 0.5 * fac * cross[(size_t)jl * nb + b2] / (double)N;
+        }
+    }
+    PB_CUDA_OK(cudaGetLastError());
+    return POLYBIN_OK;
+}
+
 // ---------------------------------------------------------------------------------------------- B Fisher
 
 // Pair spectra P_xy(k) = FT[g_x g_y](k) (x <= y, lexicographic) on the box |n_i| <= m, of the shell maps of one box
@@ -604,6 +881,7 @@ static uint64_t setup_hash(const polybin_ctx* ctx, int which) {
     h = fnv1a(&ctx->lmax, sizeof(ctx->lmax), h);
     h = fnv1a(&which, sizeof(which), h);
     h = fnv1a(&ctx->prec, sizeof(ctx->prec), h);
+    if (which == 2) h = fnv1a(ctx->observer, sizeof(ctx->observer), h);
     return h;
 }
 
@@ -658,12 +936,14 @@ static int fisher_sum(polybin_ctx* ctx, const float* n, const float* w, unsigned
                       std::vector<double>& sum, double* per_draw) {
     UwState* u = static_cast<UwState*>(ctx->ext);
     int rc;
-    const int na = which == 0 ? ctx->nell * ctx->nb : (int)ctx->Nabc.size();
+    const int na = which != 1 ? ctx->nell * ctx->nb : (int)ctx->Nabc.size();
     if (sum.size() != (size_t)na * na) sum.assign((size_t)na * na, 0.0);
     std::vector<double> F;
     for (int r = r0; r < r1; ++r) {
         if (which == 0) {
             if ((rc = pk_fisher_draw<T>(ctx, n, w, seed, r, F))) return rc;
+        } else if (which == 2) {
+            if ((rc = pk_fisher_draw_local<T>(ctx, n, w, seed, r, F))) return rc;
         } else {
             if (!u->dF) {
                 cudaError_t e = cudaMalloc(&u->dF, sizeof(double) * (size_t)na * na);
@@ -681,14 +961,32 @@ static int fisher_sum(polybin_ctx* ctx, const float* n, const float* w, unsigned
     return POLYBIN_OK;
 }
 
+// Caches F and F^-1 (host copies, F^-1 on the device) of mode `which` in the context.
+static int store_fisher(polybin_ctx* ctx, int which, const std::vector<double>& F, const std::vector<double>& Finv) {
+    UwState* u = static_cast<UwState*>(ctx->ext);
+    const size_t na2 = F.size();
+    double** dinv = which == 0 ? &u->dFp_inv : (which == 1 ? &u->dFb_inv : &u->dFl_inv);
+    if (!*dinv) {
+        cudaError_t e = cudaMalloc(dinv, sizeof(double) * na2);
+        if (e != cudaSuccess) return fail_cuda(ctx, e, "cudaMalloc Finv", __FILE__, __LINE__);
+    }
+    PB_CUDA_OK(cudaMemcpyAsync(*dinv, Finv.data(), sizeof(double) * na2, cudaMemcpyHostToDevice, ctx->stream));
+    PB_CUDA_OK(cudaStreamSynchronize(ctx->stream));
+    if (which == 0) { u->Fp = F; u->Fp_inv = Finv; u->have_p = true; }
+    else if (which == 1) { u->Fb = F; u->Fb_inv = Finv; u->have_b = true; }
+    else { u->Fl = F; u->Fl_inv = Finv; u->have_l = true; }
+    return POLYBIN_OK;
+}
+
 template <typename T>
 static int fisher_t(polybin_ctx* ctx, const float* n, const float* w, int n_mc, unsigned long long seed, int which,
                     double* fisher_out, double* fisher_inv_out, const char* ckpt) {
     int rc;
     if (which == 1 && (rc = ensure_triplets(ctx))) return rc;
     if ((rc = uw_alloc<T>(ctx, which == 1))) return rc;
+    if (which == 2 && (rc = uw_alloc_local<T>(ctx, true))) return rc;
     UwState* u = static_cast<UwState*>(ctx->ext);
-    const int na = which == 0 ? ctx->nell * ctx->nb : (int)ctx->Nabc.size();
+    const int na = which != 1 ? ctx->nell * ctx->nb : (int)ctx->Nabc.size();
     std::vector<double> sum((size_t)na * na, 0.0);
     int64_t done = 0;
     CkptHeader h;
@@ -713,16 +1011,7 @@ static int fisher_t(polybin_ctx* ctx, const float* n, const float* w, int n_mc, 
     if ((rc = gpu_solve(ctx, F.data(), na, I.data(), na, Finv.data()))) return rc;
     if (fisher_out) std::memcpy(fisher_out, F.data(), sizeof(double) * F.size());
     if (fisher_inv_out) std::memcpy(fisher_inv_out, Finv.data(), sizeof(double) * Finv.size());
-    double** dinv = which == 0 ? &u->dFp_inv : &u->dFb_inv;
-    if (!*dinv) {
-        cudaError_t e = cudaMalloc(dinv, sizeof(double) * (size_t)na * na);
-        if (e != cudaSuccess) return fail_cuda(ctx, e, "cudaMalloc Finv", __FILE__, __LINE__);
-    }
-    PB_CUDA_OK(cudaMemcpyAsync(*dinv, Finv.data(), sizeof(double) * Finv.size(), cudaMemcpyHostToDevice, ctx->stream));
-    PB_CUDA_OK(cudaStreamSynchronize(ctx->stream));
-    if (which == 0) { u->Fp = F; u->Fp_inv = Finv; u->have_p = true; }
-    else { u->Fb = F; u->Fb_inv = Finv; u->have_b = true; }
-    return POLYBIN_OK;
+    return store_fisher(ctx, which, F, Finv);
 }
 
 // x = F^-1 v on the device (FP64).
@@ -863,7 +1152,7 @@ extern "C" int polybin_fisher(polybin_ctx* ctx, const float* n_dev, const float*
                               int which, double* fisher_out, double* fisher_inv_out, const char* checkpoint_path) {
     int rc = check_uw_args(ctx, n_dev, w_dev, "polybin_fisher");
     if (rc) return rc;
-    if (n_mc < 1 || (which != 0 && which != 1)) return fail(ctx, POLYBIN_EINVAL, "polybin_fisher: n_mc >= 1, which in {0, 1}");
+    if (n_mc < 1 || which < 0 || which > 2) return fail(ctx, POLYBIN_EINVAL, "polybin_fisher: n_mc >= 1, which in {0, 1, 2}");
     return ctx->prec == POLYBIN_FP64 ? fisher_t<double>(ctx, n_dev, w_dev, n_mc, seed, which, fisher_out, fisher_inv_out, checkpoint_path)
                                      : fisher_t<float>(ctx, n_dev, w_dev, n_mc, seed, which, fisher_out, fisher_inv_out, checkpoint_path);
 }
@@ -872,35 +1161,69 @@ extern "C" int polybin_fisher_draws(polybin_ctx* ctx, const float* n_dev, const 
                                     int which, int draw_begin, int draw_end, double* per_draw_out) {
     int rc = check_uw_args(ctx, n_dev, w_dev, "polybin_fisher_draws");
     if (rc) return rc;
-    if (!per_draw_out || draw_begin < 0 || draw_end < draw_begin || (which != 0 && which != 1))
+    if (!per_draw_out || draw_begin < 0 || draw_end < draw_begin || which < 0 || which > 2)
         return fail(ctx, POLYBIN_EINVAL, "polybin_fisher_draws: bad argument");
     if (which == 1 && (rc = ensure_triplets(ctx))) return rc;
     std::vector<double> sum;
     if (ctx->prec == POLYBIN_FP64) {
         if ((rc = uw_alloc<double>(ctx, which == 1))) return rc;
+        if (which == 2 && (rc = uw_alloc_local<double>(ctx, true))) return rc;
         return fisher_sum<double>(ctx, n_dev, w_dev, seed, which, draw_begin, draw_end, sum, per_draw_out);
     }
     if ((rc = uw_alloc<float>(ctx, which == 1))) return rc;
+    if (which == 2 && (rc = uw_alloc_local<float>(ctx, true))) return rc;
     return fisher_sum<float>(ctx, n_dev, w_dev, seed, which, draw_begin, draw_end, sum, per_draw_out);
 }
 
 extern "C" int polybin_set_fisher(polybin_ctx* ctx, int which, const double* fisher) {
-    if (!ctx || !fisher || (which != 0 && which != 1)) return fail(ctx, POLYBIN_EINVAL, "polybin_set_fisher: bad argument");
+    if (!ctx || !fisher || which < 0 || which > 2) return fail(ctx, POLYBIN_EINVAL, "polybin_set_fisher: bad argument");
     int rc;
     if (which == 1 && (rc = ensure_triplets(ctx))) return rc;
     if ((rc = ctx->prec == POLYBIN_FP64 ? uw_alloc<double>(ctx, false) : uw_alloc<float>(ctx, false))) return rc;
-    UwState* u = static_cast<UwState*>(ctx->ext);
-    const int na = which == 0 ? ctx->nell * ctx->nb : (int)ctx->Nabc.size();
+    const int na = which != 1 ? ctx->nell * ctx->nb : (int)ctx->Nabc.size();
     std::vector<double> F(fisher, fisher + (size_t)na * na), I((size_t)na * na, 0.0), Finv((size_t)na * na);
     for (int i = 0; i < na; ++i) I[(size_t)i * na + i] = 1.0;
     if ((rc = gpu_solve(ctx, F.data(), na, I.data(), na, Finv.data()))) return rc;
-    double** dinv = which == 0 ? &u->dFp_inv : &u->dFb_inv;
-    if (!*dinv) PB_CUDA_OK(cudaMalloc(dinv, sizeof(double) * (size_t)na * na));
-    PB_CUDA_OK(cudaMemcpyAsync(*dinv, Finv.data(), sizeof(double) * Finv.size(), cudaMemcpyHostToDevice, ctx->stream));
-    PB_CUDA_OK(cudaStreamSynchronize(ctx->stream));
-    if (which == 0) { u->Fp = F; u->Fp_inv = Finv; u->have_p = true; }
-    else { u->Fb = F; u->Fb_inv = Finv; u->have_b = true; }
+    return store_fisher(ctx, which, F, Finv);
+}
+
+extern "C" int polybin_set_observer(polybin_ctx* ctx, const double pos[3]) {
+    if (!ctx || !pos) return fail(ctx, POLYBIN_EINVAL, "polybin_set_observer: NULL argument");
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(pos[a])) return fail(ctx, POLYBIN_EINVAL, "polybin_set_observer: position must be finite");
+    for (int a = 0; a < 3; ++a) ctx->observer[a] = pos[a];
+    UwState* u = static_cast<UwState*>(ctx->ext);
+    if (u) u->have_l = false;   // the local Fisher matrix belongs to the previous observer
     return POLYBIN_OK;
+}
+
+// Unwindowed P_ell with a local line of sight: p_num of eq. pk-num-fft, p = F^-1 p_num with the local Fisher,
+// physical units p V / N.
+template <typename T>
+static int pk_unwindowed_local_t(polybin_ctx* ctx, const float* d, const float* w, double* pk_out, double* pnum_out) {
+    int rc;
+    if ((rc = uw_alloc<T>(ctx, false))) return rc;
+    if ((rc = uw_alloc_local<T>(ctx, false))) return rc;
+    UwState* u = static_cast<UwState*>(ctx->ext);
+    const int na = ctx->nell * ctx->nb;
+    std::vector<double> pnum;
+    if ((rc = pk_numerator_local_t<T>(ctx, d, w, pnum))) return rc;
+    if (pnum_out) std::memcpy(pnum_out, pnum.data(), sizeof(double) * na);
+    if (!pk_out) return POLYBIN_OK;
+    if (!u->have_l)
+        return fail(ctx, POLYBIN_ENOTREADY, "polybin_pk_unwindowed_local: run polybin_fisher(POLYBIN_FISHER_PK_LOCAL) first");
+    std::vector<double> x;
+    if ((rc = apply_inverse(ctx, u->dFl_inv, na, pnum, x))) return rc;
+    for (int i = 0; i < na; ++i) pk_out[i] = x[i] * ctx->vol / (double)ctx->ncell;
+    return POLYBIN_OK;
+}
+
+extern "C" int polybin_pk_unwindowed_local(polybin_ctx* ctx, const float* d_dev, const float* w_dev, double* pk_out,
+                                           double* pnum_out) {
+    int rc = check_uw_args(ctx, d_dev, w_dev, "polybin_pk_unwindowed_local");
+    if (rc) return rc;
+    return ctx->prec == POLYBIN_FP64 ? pk_unwindowed_local_t<double>(ctx, d_dev, w_dev, pk_out, pnum_out)
+                                     : pk_unwindowed_local_t<float>(ctx, d_dev, w_dev, pk_out, pnum_out);
 }
 
 extern "C" int polybin_pk_unwindowed(polybin_ctx* ctx, const float* d_dev, const float* w_dev, double* pk_out, double* pnum_out) {
