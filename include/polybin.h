@@ -133,7 +133,7 @@ int polybin_bk_pk_ideal(polybin_ctx* ctx, const float* delta, int batch, double*
  * power-spectrum Fisher draws.  Parameter index alpha: power spectrum (ell, b) ell-major, index
  * (ell / 2) * n_kbins + b; bispectrum the closed triplets in polybin_get_triplets order. */
 
-enum { POLYBIN_FISHER_PK = 0, POLYBIN_FISHER_BK = 1, POLYBIN_FISHER_PK_LOCAL = 2 };
+enum { POLYBIN_FISHER_PK = 0, POLYBIN_FISHER_BK = 1, POLYBIN_FISHER_PK_LOCAL = 2, POLYBIN_FISHER_PK_OPT = 3 };
 
 /* w = 1 / (n P_FKP + 1) (Sec. 2.4, eq. Sinv-fkp), evaluated in FP64 and stored as float32 (device arrays). */
 int polybin_fkp_weights(polybin_ctx* ctx, const float* n_dev, double p_fkp, float* w_dev);
@@ -196,6 +196,52 @@ int polybin_pk_unwindowed(polybin_ctx* ctx, const float* d_dev, const float* w_d
  * [n_mocks][N] or NULL when n_mocks = 0.  bnum_out, lin_out: host [n_triplets] or NULL. */
 int polybin_bk_unwindowed(polybin_ctx* ctx, const float* d_dev, const float* w_dev, const float* mocks_dev, int n_mocks,
                           double* bk_out, double* bnum_out, double* lin_out);
+
+/* ---- optimal weighting by preconditioned conjugate gradients ------------------------------------------------------
+ * Sec. 2.4, eq. cgd-operation-eqn and the transpose equation beside it; Sec. 3.3.3, eq. Sinv-optimal in the
+ * distant-observer limit.  Data model d = n delta + eps, C = P xi P^T + N with P = diag(n), N = diag(n2) (pixel window
+ * m = 1) and xi = IFT[P(k) FT[.]], P(k) = sum_ell P_ell(k) L_ell(mu) about the global line of sight.  On the cells
+ * with n_w > 0 (Phi = 1) S^-1 solves n_w IFT[P FT[Phi S^-1 v]] + (n2_w / n_w) Phi S^-1 v = v: with
+ * A = Phi (IFT[P FT[.]] + n2_w / n_w^2) Phi (symmetric positive definite there) and G = A^-1 on that subspace,
+ *     S^-1 v = G (v / n_w),    S^-T v = G (v) / n_w,
+ * zero where n_w = 0.  IFT[P FT[u]] is taken with the unnormalised forward DFT and the 1/N inverse (the exact
+ * discretisation of int dy int_k e^{ik(x-y)} P(k) u(y)): n_w, n2_w are densities and P_ell powers in matching units.
+ * G comes from conjugate gradients preconditioned with the ideal weighting of eq. Sinv-ideal (the exact inverse for a
+ * uniform density), M^-1 r = Phi IFT[FT[Phi r] / (P(k) + sigma)], sigma = mean of n2_w / n_w^2 over the cells with
+ * n_w > 0.  Each iteration costs two pruned forward and two pruned inverse transforms plus four map passes; dot
+ * products accumulate in FP64.  Not part of the paper's interface: the weighting is configured once per context. */
+
+/* The largest binned |n|^2 (integer wave numbers): fiducial tables may have up to smax + 1 entries. */
+int polybin_max_shell(polybin_ctx* ctx, int* smax);
+
+/* Configure the optimal weighting.  n_w_dev, n2_w_dev: float32 device arrays [N] (copied; n2_w_dev = NULL takes
+ * n2_w = n_w, the Poisson noise of a unit-weight catalogue).  pfid: host [nell_fid][n_s] FP64, pfid[l][s] the fiducial
+ * multipole ell = 2 l on the shell |n|^2 = s (|k| = k_F sqrt(s)), zero for s >= n_s; 1 <= nell_fid <= 3,
+ * 1 <= n_s <= smax + 1 (P vanishes beyond the binned range, so both Fourier operators act on the pruned box of
+ * binned wave numbers).  P(k, mu) + sigma must be > 0 on every box mode (POLYBIN_EINVAL otherwise).  The iteration
+ * stops when ||r|| <= tol ||b|| (tol > 0: one host read-back per iteration) or after max_iter iterations (tol = 0:
+ * exactly max_iter iterations, no read-back inside the loop).  Replaces any earlier configuration; a Fisher matrix of
+ * POLYBIN_FISHER_PK_OPT computed with another configuration is no longer used. */
+int polybin_set_optimal(polybin_ctx* ctx, const float* n_w_dev, const float* n2_w_dev, const double* pfid, int nell_fid,
+                        int n_s, int max_iter, double tol);
+
+/* out = S^-1 v (transpose = 0) or S^-T v (transpose = 1).  v_dev: float32 device [N]; out_dev: device [N] of the
+ * context's working type (double for POLYBIN_FP64, float otherwise), zero where n_w = 0.  iters_out, relres_out (may
+ * be NULL): iterations taken and the final ||r|| / ||b|| of the recursively updated residual.  POLYBIN_ENOTREADY
+ * without polybin_set_optimal; POLYBIN_ETOL if the iteration breaks down (a non-finite residual: the operator was not
+ * positive definite). */
+int polybin_sinv_optimal(polybin_ctx* ctx, const float* v_dev, int transpose, void* out_dev, int* iters_out,
+                         double* relres_out);
+
+/* which = POLYBIN_FISHER_PK_OPT in polybin_fisher / polybin_fisher_draws / polybin_set_fisher: the P Fisher matrix of
+ * eq. fish-from-Q with the optimal weighting, S^-1 P a = G (n a / n_w) and P^T S^-T u = n G (u) / n_w for the
+ * pointing density n = n_dev (w_dev is not used and may be NULL); 1 + n_alpha solves per draw.  alpha as for
+ * POLYBIN_FISHER_PK. */
+
+/* Unwindowed P_ell with the optimal weighting: p_num_alpha = 1/2 (1/N) sum_{k in b} L_ell |FT[S^-1 d]|^2, p = F^-1
+ * p_num with the POLYBIN_FISHER_PK_OPT Fisher matrix, pk_out = p V / N (host [n_alpha], may be NULL; POLYBIN_ENOTREADY
+ * if that Fisher matrix is missing or belongs to another configuration).  pnum_out: host [n_alpha] or NULL. */
+int polybin_pk_unwindowed_opt(polybin_ctx* ctx, const float* d_dev, double* pk_out, double* pnum_out);
 
 /* X = A^-1 B in FP64 on the GPU (dense LU with partial pivoting).  A: host [n][n], B, X: host [n][nrhs], row major.
  * POLYBIN_EINVAL if A is exactly singular. */

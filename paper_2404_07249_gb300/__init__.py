@@ -66,9 +66,15 @@ _SIGS = {
     "polybin_bk_ideal_multipoles": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                                    ctypes.c_void_p]),
     "polybin_contraction_grid": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "polybin_max_shell": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
+    "polybin_set_optimal": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double]),
+    "polybin_sinv_optimal": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                            ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
+    "polybin_pk_unwindowed_opt": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
 }
 
-FISHER_PK, FISHER_BK, FISHER_PK_LOCAL = 0, 1, 2
+FISHER_PK, FISHER_BK, FISHER_PK_LOCAL, FISHER_PK_OPT = 0, 1, 2, 3
 PATH_SIMT_FP64, PATH_SIMT_FP32, PATH_TENSOR_SPLIT_TF32X3 = 0, 1, 2
 
 STAGES = ("forward", "shells", "contract", "pk_bin")
@@ -268,20 +274,61 @@ class PolyBin:
         return out
 
     def fisher(self, n_dev, w_dev, n_mc: int, seed: int, which: int, checkpoint: str | None = None):
+        """Monte Carlo Fisher matrix and its inverse; w_dev may be None for FISHER_PK_OPT."""
         na = self.n_alpha(which)
         F = np.zeros((na, na))
         Finv = np.zeros((na, na))
         ck = checkpoint.encode() if checkpoint else None
-        self._check(self.lib.polybin_fisher(self.ctx, _ptr(_f32(n_dev)), _ptr(_f32(w_dev)), int(n_mc), int(seed),
-                                            int(which), _ptr(F), _ptr(Finv), ck), "polybin_fisher")
+        n32 = _f32(n_dev)
+        w32 = None if w_dev is None else _f32(w_dev)
+        self._check(self.lib.polybin_fisher(self.ctx, _ptr(n32), None if w32 is None else _ptr(w32), int(n_mc),
+                                            int(seed), int(which), _ptr(F), _ptr(Finv), ck), "polybin_fisher")
         return F, Finv
 
     def fisher_draws(self, n_dev, w_dev, seed: int, which: int, r0: int, r1: int):
         na = self.n_alpha(which)
         out = np.zeros((r1 - r0, na, na))
-        self._check(self.lib.polybin_fisher_draws(self.ctx, _ptr(_f32(n_dev)), _ptr(_f32(w_dev)), int(seed), int(which),
-                                                  int(r0), int(r1), _ptr(out)), "polybin_fisher_draws")
+        n32 = _f32(n_dev)
+        w32 = None if w_dev is None else _f32(w_dev)
+        self._check(self.lib.polybin_fisher_draws(self.ctx, _ptr(n32), None if w32 is None else _ptr(w32), int(seed),
+                                                  int(which), int(r0), int(r1), _ptr(out)), "polybin_fisher_draws")
         return out
+
+    # ---- optimal weighting (conjugate gradients)
+    def max_shell(self) -> int:
+        """Largest binned |n|^2: fiducial tables hold up to max_shell() + 1 shells."""
+        v = ctypes.c_int(0)
+        self._check(self.lib.polybin_max_shell(self.ctx, ctypes.byref(v)), "polybin_max_shell")
+        return v.value
+
+    def set_optimal(self, n_w_dev, pfid, n2_w_dev=None, max_iter: int = 10, tol: float = 0.0):
+        """Configure S^-1 = optimal weighting: pfid[l][s] the fiducial multipole 2 l on the shell |n|^2 = s."""
+        pf = np.ascontiguousarray(np.atleast_2d(pfid), dtype=np.float64)
+        nw = _f32(n_w_dev)
+        n2 = None if n2_w_dev is None else _f32(n2_w_dev)
+        self._check(self.lib.polybin_set_optimal(self.ctx, _ptr(nw), None if n2 is None else _ptr(n2), _ptr(pf),
+                                                 int(pf.shape[0]), int(pf.shape[1]), int(max_iter), float(tol)),
+                    "polybin_set_optimal")
+
+    def sinv_optimal(self, v_dev, transpose: bool = False):
+        """(S^-1 v or S^-T v as a device tensor of the working type, iterations, final relative residual)."""
+        import torch
+        v = _f32(v_dev)
+        out = torch.empty(tuple(self.grid), dtype=self._real_dtype(), device=v.device)
+        it = ctypes.c_int(0)
+        rel = ctypes.c_double(0.0)
+        self._check(self.lib.polybin_sinv_optimal(self.ctx, _ptr(v), int(bool(transpose)), _ptr(out), ctypes.byref(it),
+                                                  ctypes.byref(rel)), "polybin_sinv_optimal")
+        return out, it.value, rel.value
+
+    def pk_unwindowed_opt(self, d_dev, with_estimate: bool = True):
+        na = self.n_alpha(FISHER_PK_OPT)
+        p = np.zeros(na)
+        pnum = np.zeros(na)
+        d = _f32(d_dev)
+        self._check(self.lib.polybin_pk_unwindowed_opt(self.ctx, _ptr(d), _ptr(p) if with_estimate else None,
+                                                       _ptr(pnum)), "polybin_pk_unwindowed_opt")
+        return (p if with_estimate else None), pnum
 
     def set_fisher(self, which: int, F):
         F = np.ascontiguousarray(F, dtype=np.float64)

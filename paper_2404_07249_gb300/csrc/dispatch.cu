@@ -176,6 +176,7 @@ void destroy_extras(polybin_ctx* ctx) {
     free_simt(reinterpret_cast<SimtPlans*>(ctx->simt));
     ctx->simt = nullptr;
     destroy_unwindowed(ctx);
+    destroy_optimal(ctx);
     destroy_multi(ctx);
     destroy_tc(ctx);
     if (ctx->d_err) cudaFree(ctx->d_err);

@@ -124,6 +124,18 @@ template <typename T> int run_triplet_sums_ell(polybin_ctx*, const T* g, const T
 int run_bk_normalise(polybin_ctx*, const double* d_S, double* d_B, double fac = 1.0);
 // P_ell(b) from the P binning partials on the device (FP64): (2 ell + 1) (V / N^2) num / N_b.
 int run_pk_normalise(polybin_ctx*, double* d_P);
+// Inverse transform of a box spectrum (the box of wave numbers |n_i| <= m) to a real map on the data grid with the
+// 1/N of the inverse DFT and an optional pointwise multiplier on output; v1 [N0][By][Bz], v2 [N0][N1][Bz].
+template <typename T> int run_inverse_box(polybin_ctx*, const C<T>* box, C<T>* v1, C<T>* v2, T* out, const T* mulout);
+// Optimal weighting (optimal.cu): out = post (/ n_w) G[Phi pre v (/ n_w)] by preconditioned conjugate gradients, with
+// G the inverse of Phi (IFT[P FT[.]] + n2_w / n_w^2) Phi on the cells with n_w > 0.  pre = null, pre_div = 1 gives
+// S^-1 v; post_div = 1 gives S^-T v; pre = n gives S^-1 P v; post = n with post_div = 1 gives P^T S^-T v.
+template <typename T, typename TIN, typename TOUT>
+int opt_apply(polybin_ctx*, const TIN* v, const float* pre, int pre_div, const float* post, int post_div, TOUT* out);
+// Identity of the configured optimal weighting (0 if none) and the statistics of the last solve.
+uint64_t opt_hash(const polybin_ctx*);
+void opt_stats(const polybin_ctx*, int* iters, double* relres);
+void destroy_optimal(polybin_ctx*);
 void destroy_extras(polybin_ctx*);
 void destroy_unwindowed(polybin_ctx*);
 void destroy_multi(polybin_ctx*);
@@ -209,8 +221,9 @@ struct polybin_ctx {
     unsigned long long uid = 0;
     void* multi = nullptr;
 
-    // extension slots (unwindowed estimators)
+    // extension slots (unwindowed estimators; optimal weighting)
     void* ext = nullptr;
+    void* opt = nullptr;
 };
 
 namespace pb {

@@ -394,13 +394,18 @@ struct UwState {
     std::vector<double> Fl, Fl_inv;
     double* dFl_inv = nullptr;
     bool have_l = false;
+    // optimal weighting: the Fisher matrix, its inverse and the weighting it was computed with
+    std::vector<double> Fo, Fo_inv;
+    double* dFo_inv = nullptr;
+    bool have_o = false;
+    uint64_t o_hash = 0;
 };
 
 static void uw_free(UwState* u) {
     if (!u) return;
     void* ptrs[] = {u->g2, u->xmap, u->a[0], u->a[1], u->spec[0], u->spec[1], u->spec[2], u->spec[3], u->pairs, u->qbox,
                     u->zc, u->yc, u->v1, u->v2, u->dF, u->dpart, u->dvec, u->dvec2, u->dinfo, u->dFp_inv, u->dFb_inv,
-                    u->ylc, u->hbox, u->g3, u->dFl_inv};
+                    u->ylc, u->hbox, u->g3, u->dFl_inv, u->dFo_inv};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete u;
@@ -463,7 +468,7 @@ static unsigned grid1d(long n) { return (unsigned)std::min<long>((n + 255) / 256
 // Inverse transform of a box spectrum to a real map: x-pass, y-pass, z-pass (C2R) with the 1/N of the IFT,
 // and an optional pointwise multiplier on output.
 template <typename T>
-static int run_inverse_box(polybin_ctx* ctx, const C<T>* box, C<T>* v1, C<T>* v2, T* out, const T* mulout) {
+int run_inverse_box(polybin_ctx* ctx, const C<T>* box, C<T>* v1, C<T>* v2, T* out, const T* mulout) {
     const int N0 = ctx->N[0], N1 = ctx->N[1], N2 = ctx->N[2];
     const int By = ctx->gy.cnt, Bz = ctx->gz.cnt;
     const C<T>* tw0 = (const C<T>*)(sizeof(T) == 4 ? ctx->d_tw_f[0] : ctx->d_tw_d[0]);
@@ -572,6 +577,46 @@ static int pk_fisher_draw(polybin_ctx* ctx, const float* n, const float* w, unsi
         for (int b = 0; b < nb; ++b) {
             C<T>* X = (C<T>*)u->spec[2];
             if ((rc = run_forward<T, T, float>(ctx, q + (size_t)b * N, w, n, (C<T>*)W.t1, (C<T>*)W.t2, X))) return rc;
+            if ((rc = run_cross_bin<T>(ctx, X, A, u->dpart, cross))) return rc;
+            const int alpha = il * nb + b;
+            for (int jl = 0; jl < nell; ++jl)
+                for (int b2 = 0; b2 < nb; ++b2) F[(size_t)alpha * na + jl * nb + b2] = 0.5 * cross[(size_t)jl * nb + b2] / (double)N;
+        }
+    }
+    return POLYBIN_OK;
+}
+
+// One Monte Carlo term of the P Fisher matrix with the optimal weighting (eq. fish-from-Q, global line of sight):
+// F[(l,b)][(l',b')] = 1/2 (1/N) sum_k conj(FT[P^T S^-T IFT[Theta_b L_l FT[S^-1 P a]]]) Theta_b' L_l' FT[a], with
+// S^-1 P a = G(n a / n_w) and P^T S^-T u = n G(u) / n_w, each G a conjugate-gradient solve (1 + nell nb per draw).
+template <typename T>
+static int pk_fisher_draw_opt(polybin_ctx* ctx, const float* n, unsigned long long seed, int r, std::vector<double>& F) {
+    UwState* u = static_cast<UwState*>(ctx->ext);
+    Work& W = ctx->w;
+    const long N = ctx->ncell;
+    const int nb = ctx->nb, nell = ctx->nell, na = nell * nb;
+    int rc;
+    T* a = (T*)u->a[0];
+    T* sa = (T*)u->a[1];
+    uw::k_draw<T><<<grid1d((N + 3) / 4), 256, 0, ctx->stream>>>(a, N, seed, (uint32_t)r, 2u);
+    ctx->launches++;
+    C<T>* A = (C<T>*)u->spec[0];
+    C<T>* SA = (C<T>*)u->spec[1];
+    if ((rc = run_forward<T, T, float>(ctx, a, (const float*)nullptr, (const float*)nullptr, (C<T>*)W.t1, (C<T>*)W.t2, A))) return rc;
+    if ((rc = opt_apply<T, T, T>(ctx, a, n, 1, nullptr, 0, sa))) return rc;
+    if ((rc = run_forward<T, T, float>(ctx, sa, (const float*)nullptr, (const float*)nullptr, (C<T>*)W.t1, (C<T>*)W.t2, SA))) return rc;
+    F.assign((size_t)na * na, 0.0);
+    std::vector<double> cross;
+    T* q = (T*)u->g2;
+    T* xm = (T*)u->xmap;
+    for (int il = 0; il < nell; ++il) {
+        if ((rc = ensure_fine_inv<T>(ctx))) return rc;
+        if ((rc = run_shells<T>(ctx, SA, (C<T>*)W.u1f, (C<T>*)W.u2f, q, 2 * il, ctx->fg))) return rc;
+        for (int b = 0; b < nb; ++b) {
+            C<T>* X = (C<T>*)u->spec[2];
+            if ((rc = opt_apply<T, T, T>(ctx, q + (size_t)b * N, nullptr, 0, n, 1, xm))) return rc;
+            if ((rc = run_forward<T, T, float>(ctx, xm, (const float*)nullptr, (const float*)nullptr, (C<T>*)W.t1, (C<T>*)W.t2, X)))
+                return rc;
             if ((rc = run_cross_bin<T>(ctx, X, A, u->dpart, cross))) return rc;
             const int alpha = il * nb + b;
             for (int jl = 0; jl < nell; ++jl)
@@ -882,13 +927,17 @@ static uint64_t setup_hash(const polybin_ctx* ctx, int which) {
     h = fnv1a(&which, sizeof(which), h);
     h = fnv1a(&ctx->prec, sizeof(ctx->prec), h);
     if (which == 2) h = fnv1a(ctx->observer, sizeof(ctx->observer), h);
+    if (which == 3) {
+        const uint64_t o = opt_hash(ctx);
+        h = fnv1a(&o, sizeof(o), h);
+    }
     return h;
 }
 
 static int mask_hash(polybin_ctx* ctx, const float* n, const float* w, uint64_t* out) {
-    std::vector<float> hn(ctx->ncell), hw(ctx->ncell);
+    std::vector<float> hn(ctx->ncell), hw(w ? ctx->ncell : 0);
     PB_CUDA_OK(cudaMemcpyAsync(hn.data(), n, sizeof(float) * ctx->ncell, cudaMemcpyDeviceToHost, ctx->stream));
-    PB_CUDA_OK(cudaMemcpyAsync(hw.data(), w, sizeof(float) * ctx->ncell, cudaMemcpyDeviceToHost, ctx->stream));
+    if (w) PB_CUDA_OK(cudaMemcpyAsync(hw.data(), w, sizeof(float) * ctx->ncell, cudaMemcpyDeviceToHost, ctx->stream));
     PB_CUDA_OK(cudaStreamSynchronize(ctx->stream));
     *out = fnv1a(hw.data(), sizeof(float) * hw.size(), fnv1a(hn.data(), sizeof(float) * hn.size()));
     return POLYBIN_OK;
@@ -944,6 +993,8 @@ static int fisher_sum(polybin_ctx* ctx, const float* n, const float* w, unsigned
             if ((rc = pk_fisher_draw<T>(ctx, n, w, seed, r, F))) return rc;
         } else if (which == 2) {
             if ((rc = pk_fisher_draw_local<T>(ctx, n, w, seed, r, F))) return rc;
+        } else if (which == 3) {
+            if ((rc = pk_fisher_draw_opt<T>(ctx, n, seed, r, F))) return rc;
         } else {
             if (!u->dF) {
                 cudaError_t e = cudaMalloc(&u->dF, sizeof(double) * (size_t)na * na);
@@ -965,7 +1016,7 @@ static int fisher_sum(polybin_ctx* ctx, const float* n, const float* w, unsigned
 static int store_fisher(polybin_ctx* ctx, int which, const std::vector<double>& F, const std::vector<double>& Finv) {
     UwState* u = static_cast<UwState*>(ctx->ext);
     const size_t na2 = F.size();
-    double** dinv = which == 0 ? &u->dFp_inv : (which == 1 ? &u->dFb_inv : &u->dFl_inv);
+    double** dinv = which == 0 ? &u->dFp_inv : (which == 1 ? &u->dFb_inv : (which == 2 ? &u->dFl_inv : &u->dFo_inv));
     if (!*dinv) {
         cudaError_t e = cudaMalloc(dinv, sizeof(double) * na2);
         if (e != cudaSuccess) return fail_cuda(ctx, e, "cudaMalloc Finv", __FILE__, __LINE__);
@@ -974,7 +1025,8 @@ static int store_fisher(polybin_ctx* ctx, int which, const std::vector<double>& 
     PB_CUDA_OK(cudaStreamSynchronize(ctx->stream));
     if (which == 0) { u->Fp = F; u->Fp_inv = Finv; u->have_p = true; }
     else if (which == 1) { u->Fb = F; u->Fb_inv = Finv; u->have_b = true; }
-    else { u->Fl = F; u->Fl_inv = Finv; u->have_l = true; }
+    else if (which == 2) { u->Fl = F; u->Fl_inv = Finv; u->have_l = true; }
+    else { u->Fo = F; u->Fo_inv = Finv; u->have_o = true; u->o_hash = opt_hash(ctx); }
     return POLYBIN_OK;
 }
 
@@ -985,7 +1037,8 @@ static int fisher_t(polybin_ctx* ctx, const float* n, const float* w, int n_mc, 
     if (which == 1 && (rc = ensure_triplets(ctx))) return rc;
     if ((rc = uw_alloc<T>(ctx, which == 1))) return rc;
     if (which == 2 && (rc = uw_alloc_local<T>(ctx, true))) return rc;
-    UwState* u = static_cast<UwState*>(ctx->ext);
+    if (which == 3 && !opt_hash(ctx))
+        return fail(ctx, POLYBIN_ENOTREADY, "polybin_fisher(POLYBIN_FISHER_PK_OPT): call polybin_set_optimal first");
     const int na = which != 1 ? ctx->nell * ctx->nb : (int)ctx->Nabc.size();
     std::vector<double> sum((size_t)na * na, 0.0);
     int64_t done = 0;
@@ -1113,6 +1166,38 @@ static int bk_unwindowed_t(polybin_ctx* ctx, const float* d, const float* w, con
     return POLYBIN_OK;
 }
 
+template int run_inverse_box<float>(polybin_ctx*, const float2*, float2*, float2*, float*, const float*);
+template int run_inverse_box<double>(polybin_ctx*, const double2*, double2*, double2*, double*, const double*);
+
+// Unwindowed P_ell with the optimal weighting: p_num of eq. pk-num-fft with u = S^-1 d = G(d / n_w), p = F^-1 p_num
+// with the Fisher matrix of the same weighting, physical units p V / N.
+template <typename T>
+static int pk_unwindowed_opt_t(polybin_ctx* ctx, const float* d, double* pk_out, double* pnum_out) {
+    int rc;
+    if ((rc = uw_alloc<T>(ctx, false))) return rc;
+    UwState* u = static_cast<UwState*>(ctx->ext);
+    Work& W = ctx->w;
+    const int na = ctx->nell * ctx->nb;
+    T* xm = (T*)u->xmap;
+    if ((rc = opt_apply<T, float, T>(ctx, d, nullptr, 1, nullptr, 0, xm))) return rc;
+    if ((rc = run_forward<T, T, float>(ctx, xm, (const float*)nullptr, (const float*)nullptr, (C<T>*)W.t1, (C<T>*)W.t2,
+                                       (C<T>*)W.box)))
+        return rc;
+    std::vector<double> num;
+    if ((rc = run_pkbin<T>(ctx, (const C<T>*)W.box, num))) return rc;
+    std::vector<double> pnum(na);
+    for (int i = 0; i < na; ++i) pnum[i] = 0.5 * num[i] / (double)ctx->ncell;
+    if (pnum_out) std::memcpy(pnum_out, pnum.data(), sizeof(double) * na);
+    if (!pk_out) return POLYBIN_OK;
+    if (!u->have_o) return fail(ctx, POLYBIN_ENOTREADY, "polybin_pk_unwindowed_opt: run polybin_fisher(POLYBIN_FISHER_PK_OPT) first");
+    if (u->o_hash != opt_hash(ctx))
+        return fail(ctx, POLYBIN_ENOTREADY, "polybin_pk_unwindowed_opt: the optimal weighting changed since its Fisher matrix was computed");
+    std::vector<double> x;
+    if ((rc = apply_inverse(ctx, u->dFo_inv, na, pnum, x))) return rc;
+    for (int i = 0; i < na; ++i) pk_out[i] = x[i] * ctx->vol / (double)ctx->ncell;
+    return POLYBIN_OK;
+}
+
 }  // namespace pb
 
 using namespace pb;
@@ -1148,22 +1233,31 @@ static int check_uw_args(polybin_ctx* ctx, const float* a, const float* b, const
     return POLYBIN_OK;
 }
 
+// The optimal weighting (which = 3) takes no weight map: w may be NULL.
+static int check_fisher_args(polybin_ctx* ctx, const float* n, const float* w, int which, const char* what) {
+    if (which == 3 && !w) return check_uw_args(ctx, n, n, what);
+    return check_uw_args(ctx, n, w, what);
+}
+
 extern "C" int polybin_fisher(polybin_ctx* ctx, const float* n_dev, const float* w_dev, int n_mc, unsigned long long seed,
                               int which, double* fisher_out, double* fisher_inv_out, const char* checkpoint_path) {
-    int rc = check_uw_args(ctx, n_dev, w_dev, "polybin_fisher");
+    int rc = check_fisher_args(ctx, n_dev, w_dev, which, "polybin_fisher");
     if (rc) return rc;
-    if (n_mc < 1 || which < 0 || which > 2) return fail(ctx, POLYBIN_EINVAL, "polybin_fisher: n_mc >= 1, which in {0, 1, 2}");
+    if (n_mc < 1 || which < 0 || which > 3) return fail(ctx, POLYBIN_EINVAL, "polybin_fisher: n_mc >= 1, which in {0, 1, 2, 3}");
+    if (which == 3) w_dev = nullptr;
     return ctx->prec == POLYBIN_FP64 ? fisher_t<double>(ctx, n_dev, w_dev, n_mc, seed, which, fisher_out, fisher_inv_out, checkpoint_path)
                                      : fisher_t<float>(ctx, n_dev, w_dev, n_mc, seed, which, fisher_out, fisher_inv_out, checkpoint_path);
 }
 
 extern "C" int polybin_fisher_draws(polybin_ctx* ctx, const float* n_dev, const float* w_dev, unsigned long long seed,
                                     int which, int draw_begin, int draw_end, double* per_draw_out) {
-    int rc = check_uw_args(ctx, n_dev, w_dev, "polybin_fisher_draws");
+    int rc = check_fisher_args(ctx, n_dev, w_dev, which, "polybin_fisher_draws");
     if (rc) return rc;
-    if (!per_draw_out || draw_begin < 0 || draw_end < draw_begin || which < 0 || which > 2)
+    if (!per_draw_out || draw_begin < 0 || draw_end < draw_begin || which < 0 || which > 3)
         return fail(ctx, POLYBIN_EINVAL, "polybin_fisher_draws: bad argument");
     if (which == 1 && (rc = ensure_triplets(ctx))) return rc;
+    if (which == 3 && !opt_hash(ctx))
+        return fail(ctx, POLYBIN_ENOTREADY, "polybin_fisher_draws(POLYBIN_FISHER_PK_OPT): call polybin_set_optimal first");
     std::vector<double> sum;
     if (ctx->prec == POLYBIN_FP64) {
         if ((rc = uw_alloc<double>(ctx, which == 1))) return rc;
@@ -1176,7 +1270,9 @@ extern "C" int polybin_fisher_draws(polybin_ctx* ctx, const float* n_dev, const 
 }
 
 extern "C" int polybin_set_fisher(polybin_ctx* ctx, int which, const double* fisher) {
-    if (!ctx || !fisher || which < 0 || which > 2) return fail(ctx, POLYBIN_EINVAL, "polybin_set_fisher: bad argument");
+    if (!ctx || !fisher || which < 0 || which > 3) return fail(ctx, POLYBIN_EINVAL, "polybin_set_fisher: bad argument");
+    if (which == 3 && !opt_hash(ctx))
+        return fail(ctx, POLYBIN_ENOTREADY, "polybin_set_fisher(POLYBIN_FISHER_PK_OPT): call polybin_set_optimal first");
     int rc;
     if (which == 1 && (rc = ensure_triplets(ctx))) return rc;
     if ((rc = ctx->prec == POLYBIN_FP64 ? uw_alloc<double>(ctx, false) : uw_alloc<float>(ctx, false))) return rc;
@@ -1224,6 +1320,13 @@ extern "C" int polybin_pk_unwindowed_local(polybin_ctx* ctx, const float* d_dev,
     if (rc) return rc;
     return ctx->prec == POLYBIN_FP64 ? pk_unwindowed_local_t<double>(ctx, d_dev, w_dev, pk_out, pnum_out)
                                      : pk_unwindowed_local_t<float>(ctx, d_dev, w_dev, pk_out, pnum_out);
+}
+
+extern "C" int polybin_pk_unwindowed_opt(polybin_ctx* ctx, const float* d_dev, double* pk_out, double* pnum_out) {
+    int rc = check_uw_args(ctx, d_dev, d_dev, "polybin_pk_unwindowed_opt");
+    if (rc) return rc;
+    return ctx->prec == POLYBIN_FP64 ? pk_unwindowed_opt_t<double>(ctx, d_dev, pk_out, pnum_out)
+                                     : pk_unwindowed_opt_t<float>(ctx, d_dev, pk_out, pnum_out);
 }
 
 extern "C" int polybin_pk_unwindowed(polybin_ctx* ctx, const float* d_dev, const float* w_dev, double* pk_out, double* pnum_out) {
