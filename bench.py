@@ -311,6 +311,38 @@ def other_workloads(pkg, synth, stream, dev) -> dict:
     pbb.close()
     out["masked256_split"] = {"pk_fisher_s_per_draw": tfp, "bk_fisher_s_per_draw_pair": tfb, "n_triplets": nt,
                               "pk_unwindowed_s": tpu, "bk_unwindowed_s_with_2_mocks": tbu}
+    out["masked256_optimal_fp32"] = optimal_workload(pkg, synth, stream, dev)
+    return out
+
+
+def optimal_workload(pkg, synth, stream, dev, fisher: bool = True) -> dict:
+    """Optimal weighting S^-1 on the masked 256^3 workload (global line of sight, fiducial = the field's own power
+    law, n2 = n): conjugate gradients with 10 iterations as in the paper's optimal-weight test (Sec. 6.1.2), and to a
+    relative residual of 1e-5; one P Fisher draw (1 + n_alpha solves) and the unwindowed estimate."""
+    import torch
+    w = synth.WORKLOADS[5]
+    n = synth.survey_mask(w.grid, (w.box,) * 3, 5000).astype(np.float32)
+    nd = torch.from_numpy(n).to(dev)
+    d = torch.from_numpy((n * synth.workload_field(5, 0)).astype(np.float32)).to(dev)
+    pb = pkg.PolyBin(w.grid, w.box, w.pk_edges, lmax=4, prec="fp32", stream=stream.cuda_stream)
+    kf = 2.0 * np.pi / w.box
+    pfid = synth.power_law(kf * np.sqrt(np.arange(pb.max_shell() + 1, dtype=np.float64)))[None, :]
+    out = {"grid": list(w.grid), "n_alpha": pb.n_alpha(pkg.FISHER_PK_OPT)}
+    pb.set_optimal(nd, pfid, None, max_iter=10, tol=0.0)
+    res = pb.sinv_optimal(d)
+    t10 = _time(lambda: pb.sinv_optimal(d), 5)
+    out.update({"solve_ms_10_iterations": 1e3 * t10, "ms_per_iteration": 1e3 * t10 / 10,
+                "relres_after_10": res[2]})
+    pb.set_optimal(nd, pfid, None, max_iter=200, tol=1e-5)
+    res = pb.sinv_optimal(d)
+    t5 = _time(lambda: pb.sinv_optimal(d), 3)
+    out.update({"iterations_to_1e-5": res[1], "solve_ms_to_1e-5": 1e3 * t5})
+    if fisher:
+        pb.set_optimal(nd, pfid, None, max_iter=10, tol=0.0)
+        out["pk_fisher_s_per_draw"] = _time(lambda: pb.fisher_draws(nd, None, 1, pkg.FISHER_PK_OPT, 0, 1), 1)
+        pb.fisher(nd, None, 1, 1, pkg.FISHER_PK_OPT)
+        out["pk_unwindowed_s"] = _time(lambda: pb.pk_unwindowed_opt(d), 3)
+    pb.close()
     return out
 
 
@@ -326,6 +358,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", type=int, nargs=3, default=None,
                     help="profiling only: run the workload's field model, box and bins on another grid")
+    ap.add_argument("--optimal-only", action="store_true",
+                    help="profiling only: time the optimal-weighting solves on the masked 256^3 workload and exit")
     ap.add_argument("--no-other-workloads", action="store_true",
                     help="skip the other workloads (64^3 FP64, 256^3, batched uneven grids, masked 256^3)")
     args = ap.parse_args()
@@ -350,6 +384,12 @@ def main():
     def barrier():
         if world > 1:
             dist.barrier()
+
+    if args.optimal_only:
+        out = optimal_workload(pkg, synth, torch.cuda.current_stream(dev), dev, fisher=False)
+        if rank == 0:
+            print(json.dumps({"workload": "masked256_optimal_fp32", **out}), flush=True)
+        return
 
     w, edges = _workload(args.config)
     grid, box = (tuple(args.grid) if args.grid else w.grid), w.box

@@ -36,6 +36,27 @@ constexpr int kMaxBlocks = 152 * 8;
 // device scalar slots
 enum { kBB = 0, kPQ = 1, kRR = 2, kRZ0 = 3, kRZ1 = 4, kDsum = 5, kDcnt = 6, kSlots = 8 };
 
+// Per-thread accumulator of a dot product: FP64 for FP64 maps; for FP32 maps compensated (Kahan) FP32 sums, which keep
+// the per-thread error at the FP32 rounding of one term while staying off the FP64 pipe (a small fraction of the FP32
+// rate on this part: an FP64 multiply-add plus two conversions per element made these kernels arithmetic-bound).
+template <typename T>
+struct Acc {
+    double s = 0.0;
+    __device__ __forceinline__ void add(T x) { s += (double)x; }
+    __device__ __forceinline__ double get() const { return s; }
+};
+template <>
+struct Acc<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float y = x - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double get() const { return (double)s - (double)c; }
+};
+
 __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
@@ -111,7 +132,7 @@ __global__ void __launch_bounds__(kThreads) k_init(const TIN* __restrict__ v, co
                                                    const float* __restrict__ nw, const T* __restrict__ Dm,
                                                    T* __restrict__ r, T* __restrict__ x, long N, double* part, double* sc,
                                                    unsigned* counter) {
-    double v2[1] = {0.0};
+    Acc<T> acc;
     for (long i = (long)blockIdx.x * kThreads + threadIdx.x; i < N; i += (long)gridDim.x * kThreads) {
         T ri = T(0);
         if (Dm[i] >= T(0)) {
@@ -121,8 +142,9 @@ __global__ void __launch_bounds__(kThreads) k_init(const TIN* __restrict__ v, co
         }
         r[i] = ri;
         x[i] = T(0);
-        v2[0] += (double)ri * (double)ri;
+        acc.add(ri * ri);
     }
+    const double v2[1] = {acc.get()};
     const int slot[1] = {kBB};
     reduce_to<1>(v2, part, sc, slot, counter);
 }
@@ -143,14 +165,15 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) k_op_post(const T* __restrict__ y, const T* __restrict__ p,
                                                       const T* __restrict__ Dm, T* __restrict__ q, long N,
                                                       double* part, double* sc, unsigned* counter) {
-    double v[1] = {0.0};
+    Acc<T> acc;
     for (long i = (long)blockIdx.x * kThreads + threadIdx.x; i < N; i += (long)gridDim.x * kThreads) {
         const T d = Dm[i];
         const T pi = p[i];
         const T qi = d >= T(0) ? y[i] + d * pi : T(0);
         q[i] = qi;
-        v[0] += (double)pi * (double)qi;
+        acc.add(pi * qi);
     }
+    const double v[1] = {acc.get()};
     const int slot[1] = {kPQ};
     reduce_to<1>(v, part, sc, slot, counter);
 }
@@ -162,13 +185,14 @@ __global__ void __launch_bounds__(kThreads) k_update(T* __restrict__ x, T* __res
                                                      double* sc, unsigned* counter) {
     const double pq = sc[kPQ];
     const T alpha = pq != 0.0 ? T(sc[rz_slot] / pq) : T(0);   // p = 0 only once r = 0 exactly
-    double v[1] = {0.0};
+    Acc<T> acc;
     for (long i = (long)blockIdx.x * kThreads + threadIdx.x; i < N; i += (long)gridDim.x * kThreads) {
         x[i] += alpha * p[i];
         const T ri = r[i] - alpha * q[i];
         r[i] = ri;
-        v[0] += (double)ri * (double)ri;
+        acc.add(ri * ri);
     }
+    const double v[1] = {acc.get()};
     const int slot[1] = {kRR};
     reduce_to<1>(v, part, sc, slot, counter);
 }
@@ -179,13 +203,14 @@ __global__ void __launch_bounds__(kThreads) k_prec_post(const T* __restrict__ y,
                                                         const T* __restrict__ Dm, T inv_sigma, T* __restrict__ z,
                                                         long N, int rz_slot, double* part, double* sc,
                                                         unsigned* counter) {
-    double v[1] = {0.0};
+    Acc<T> acc;
     for (long i = (long)blockIdx.x * kThreads + threadIdx.x; i < N; i += (long)gridDim.x * kThreads) {
         const T ri = r[i];
         const T zi = Dm[i] >= T(0) ? ri * inv_sigma + y[i] : T(0);
         z[i] = zi;
-        v[0] += (double)ri * (double)zi;
+        acc.add(ri * zi);
     }
+    const double v[1] = {acc.get()};
     const int slot[1] = {rz_slot};
     reduce_to<1>(v, part, sc, slot, counter);
 }
@@ -237,12 +262,25 @@ struct OptState {
     double* part = nullptr;          // block partials [2][kMaxBlocks]
     unsigned* counter = nullptr;
     double* hsc = nullptr;           // pinned host copy of the scalars
+    // the two halves of an iteration with the r.z slots of parity 0 and 1, captured once per configuration:
+    // half[par][0] = q = A p and the x, r update; half[par][1] = z = M^-1 r and the new direction
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t half[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    long half_launches[2] = {0, 0};
     int last_iters = 0;
     double last_relres = 0.0;
 };
 
+static void opt_drop_graphs(OptState* s) {
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+            if (s->half[a][b]) { cudaGraphExecDestroy(s->half[a][b]); s->half[a][b] = nullptr; }
+}
+
 static void opt_free(OptState* s) {
     if (!s) return;
+    opt_drop_graphs(s);
+    if (s->cap) cudaStreamDestroy(s->cap);
     void* ptrs[] = {s->nw, s->Dm, s->wk, s->wm, s->map[0], s->map[1], s->map[2], s->map[3], s->map[4], s->map[5],
                     s->box, s->f1, s->f2, s->sc, s->part, s->counter};
     for (void* p : ptrs)
@@ -273,6 +311,7 @@ static int opt_configure_t(polybin_ctx* ctx, const float* nw, const float* n2w, 
         s->elem = sizeof(T);
     }
     s->ready = false;
+    opt_drop_graphs(s);   // the captured iterations carry 1 / sigma by value
     const long N = ctx->ncell;
     const long nbox = (long)ctx->gx.cnt * ctx->gy.cnt * ctx->gz.cnt;
     auto need = [&](void** p, size_t bytes) -> int {
@@ -386,21 +425,87 @@ static int opt_precondition(polybin_ctx* ctx, OptState* s, int slot) {
     return opt_launched(ctx, "k_prec_post");
 }
 
+// First half of iteration `par`: q = A p (pruned forward, times P on the box, pruned inverse, + D p on the mask),
+// p.q, then x += alpha p, r -= alpha q with alpha = r.z / p.q (r.z in slot kRZ0 + par).
+template <typename T>
+static int opt_half_op(polybin_ctx* ctx, OptState* s, int par) {
+    const long N = ctx->ncell;
+    const long nbox = (long)ctx->gx.cnt * ctx->gy.cnt * ctx->gz.cnt;
+    T* x = (T*)s->map[0];
+    T* r = (T*)s->map[1];
+    T* p = (T*)s->map[3];
+    T* q = (T*)s->map[4];
+    T* y = (T*)s->map[5];
+    C<T>* box = (C<T>*)s->box;
+    const unsigned nbk = opt_blocks(N);
+    int rc;
+    if ((rc = run_forward<T, T, T>(ctx, p, (const T*)nullptr, (const T*)nullptr, (C<T>*)s->f1, (C<T>*)s->f2, box)))
+        return rc;
+    opt::k_box_mul<T><<<opt_blocks(nbox), opt::kThreads, 0, ctx->stream>>>(box, (const T*)s->wk, nbox);
+    if ((rc = opt_launched(ctx, "k_box_mul"))) return rc;
+    if ((rc = run_inverse_box<T>(ctx, box, (C<T>*)s->f2, (C<T>*)s->f1, y, nullptr))) return rc;
+    opt::k_op_post<T><<<nbk, opt::kThreads, 0, ctx->stream>>>(y, p, (const T*)s->Dm, q, N, s->part, s->sc, s->counter);
+    if ((rc = opt_launched(ctx, "k_op_post"))) return rc;
+    opt::k_update<T><<<nbk, opt::kThreads, 0, ctx->stream>>>(x, r, p, q, N, opt::kRZ0 + par, s->part, s->sc, s->counter);
+    return opt_launched(ctx, "k_update");
+}
+
+// Second half of iteration `par`: z = M^-1 r with r.z into slot kRZ0 + (1 - par), p = z + beta p.
+template <typename T>
+static int opt_half_prec(polybin_ctx* ctx, OptState* s, int par) {
+    const int cur = opt::kRZ0 + par, nxt = opt::kRZ0 + (1 - par);
+    int rc;
+    if ((rc = opt_precondition<T>(ctx, s, nxt))) return rc;
+    opt::k_dir<T><<<opt_blocks(ctx->ncell), opt::kThreads, 0, ctx->stream>>>((T*)s->map[3], (const T*)s->map[2],
+                                                                               ctx->ncell, 0, nxt, cur, s->sc);
+    return opt_launched(ctx, "k_dir");
+}
+
+// Captures the four iteration halves into CUDA graphs (private capture stream; the graphs are launched on the
+// context's stream).  They refer only to the configuration's own buffers, so they stay valid until it is replaced.
+template <typename T>
+static int opt_capture(polybin_ctx* ctx, OptState* s) {
+    if (s->half[1][1]) return POLYBIN_OK;
+    if (!s->cap) PB_CUDA_OK(cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking));
+    for (int par = 0; par < 2; ++par)
+        for (int h = 0; h < 2; ++h) {
+            cudaGraph_t graph = nullptr;
+            cudaError_t e = cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) { cudaGetLastError(); opt_drop_graphs(s); return fail_cuda(ctx, e, "cudaStreamBeginCapture", __FILE__, __LINE__); }
+            cudaStream_t saved = ctx->stream;
+            ctx->stream = s->cap;
+            ctx->capturing = true;
+            const long l0 = ctx->launches;
+            int rc = h == 0 ? opt_half_op<T>(ctx, s, par) : opt_half_prec<T>(ctx, s, par);
+            s->half_launches[h] = ctx->launches - l0;
+            ctx->launches = l0;
+            ctx->capturing = false;
+            ctx->stream = saved;
+            e = cudaStreamEndCapture(s->cap, &graph);
+            if (rc || e != cudaSuccess) {
+                cudaGetLastError();
+                if (graph) cudaGraphDestroy(graph);
+                opt_drop_graphs(s);
+                return rc ? rc : fail_cuda(ctx, e, "cudaStreamEndCapture", __FILE__, __LINE__);
+            }
+            e = cudaGraphInstantiate(&s->half[par][h], graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) { s->half[par][h] = nullptr; opt_drop_graphs(s); return fail_cuda(ctx, e, "cudaGraphInstantiate", __FILE__, __LINE__); }
+        }
+    return POLYBIN_OK;
+}
+
 template <typename T, typename TIN, typename TOUT>
 int opt_apply(polybin_ctx* ctx, const TIN* v, const float* pre, int pre_div, const float* post, int post_div, TOUT* out) {
     OptState* s = static_cast<OptState*>(ctx->opt);
     if (!s || !s->ready) return fail(ctx, POLYBIN_ENOTREADY, "optimal weighting: call polybin_set_optimal first");
     if (s->elem != sizeof(T)) return fail(ctx, POLYBIN_EINVAL, "optimal weighting: configured in another precision");
     const long N = ctx->ncell;
-    const long nbox = (long)ctx->gx.cnt * ctx->gy.cnt * ctx->gz.cnt;
     T* x = (T*)s->map[0];
     T* r = (T*)s->map[1];
     T* z = (T*)s->map[2];
     T* p = (T*)s->map[3];
-    T* q = (T*)s->map[4];
-    T* y = (T*)s->map[5];
     const T* Dm = (const T*)s->Dm;
-    C<T>* box = (C<T>*)s->box;
     const unsigned nbk = opt_blocks(N);
     int rc;
     opt::k_init<T, TIN><<<nbk, opt::kThreads, 0, ctx->stream>>>(v, pre, pre_div, s->nw, Dm, r, x, N, s->part, s->sc,
@@ -415,18 +520,17 @@ int opt_apply(polybin_ctx* ctx, const TIN* v, const float* pre, int pre_div, con
         if ((rc = opt_precondition<T>(ctx, s, opt::kRZ0))) return rc;
         opt::k_dir<T><<<nbk, opt::kThreads, 0, ctx->stream>>>(p, z, N, 1, opt::kRZ0, opt::kRZ0, s->sc);
         if ((rc = opt_launched(ctx, "k_dir"))) return rc;
+        const bool graphs = !ctx->capturing && opt_capture<T>(ctx, s) == POLYBIN_OK;
+        if (!graphs) cudaGetLastError();
+        auto half = [&](int par, int h) -> int {
+            if (!graphs) return h == 0 ? opt_half_op<T>(ctx, s, par) : opt_half_prec<T>(ctx, s, par);
+            cudaError_t e = cudaGraphLaunch(s->half[par][h], ctx->stream);
+            if (e != cudaSuccess) return fail_cuda(ctx, e, "cudaGraphLaunch", __FILE__, __LINE__);
+            ctx->launches += s->half_launches[h];
+            return POLYBIN_OK;
+        };
         while (it < s->max_iter) {
-            const int cur = opt::kRZ0 + (it & 1), nxt = opt::kRZ0 + ((it + 1) & 1);
-            // q = A p
-            if ((rc = run_forward<T, T, T>(ctx, p, (const T*)nullptr, (const T*)nullptr, (C<T>*)s->f1, (C<T>*)s->f2, box)))
-                return rc;
-            opt::k_box_mul<T><<<opt_blocks(nbox), opt::kThreads, 0, ctx->stream>>>(box, (const T*)s->wk, nbox);
-            if ((rc = opt_launched(ctx, "k_box_mul"))) return rc;
-            if ((rc = run_inverse_box<T>(ctx, box, (C<T>*)s->f2, (C<T>*)s->f1, y, nullptr))) return rc;
-            opt::k_op_post<T><<<nbk, opt::kThreads, 0, ctx->stream>>>(y, p, Dm, q, N, s->part, s->sc, s->counter);
-            if ((rc = opt_launched(ctx, "k_op_post"))) return rc;
-            opt::k_update<T><<<nbk, opt::kThreads, 0, ctx->stream>>>(x, r, p, q, N, cur, s->part, s->sc, s->counter);
-            if ((rc = opt_launched(ctx, "k_update"))) return rc;
+            if ((rc = half(it & 1, 0))) return rc;
             ++it;
             if (it == s->max_iter) break;
             if (s->tol > 0.0) {
@@ -437,9 +541,7 @@ int opt_apply(polybin_ctx* ctx, const TIN* v, const float* pre, int pre_div, con
                     return fail(ctx, POLYBIN_ETOL, "optimal weighting: conjugate gradients broke down (operator not positive definite?)");
                 if (rel <= s->tol) break;
             }
-            if ((rc = opt_precondition<T>(ctx, s, nxt))) return rc;
-            opt::k_dir<T><<<nbk, opt::kThreads, 0, ctx->stream>>>(p, z, N, 0, nxt, cur, s->sc);
-            if ((rc = opt_launched(ctx, "k_dir"))) return rc;
+            if ((rc = half((it - 1) & 1, 1))) return rc;
         }
     }
     opt::k_final<T, TOUT><<<nbk, opt::kThreads, 0, ctx->stream>>>(x, post, post_div, s->nw, Dm, out, N);
