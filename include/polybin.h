@@ -183,10 +183,11 @@ int polybin_set_observer(polybin_ctx* ctx, const double pos[3]);
 int polybin_pk_unwindowed_local(polybin_ctx* ctx, const float* d_dev, const float* w_dev, double* pk_out,
                                 double* pnum_out);
 
-/* Unwindowed P_ell (Sec. 3.2, eq. pk-estimator-def; no bias term in this data model):
- * p_num_alpha = 1/2 (1/N) sum_{k in b} L_ell |FT[w d]|^2 (pixel units), p = F^-1 p_num, pk_out = p V / N
- * (host [n_alpha]; needs polybin_fisher(POLYBIN_FISHER_PK) or polybin_set_fisher first, may be NULL).
- * pnum_out: host [n_alpha] or NULL. */
+/* Unwindowed P_ell (Sec. 3.2, eq. pk-estimator-def):
+ * p_num_alpha = 1/2 (1/N) sum_{k in b} L_ell |FT[w d]|^2 (pixel units), p = F^-1 (p_num - p_bias), pk_out = p V / N
+ * (host [n_alpha]; needs polybin_fisher(POLYBIN_FISHER_PK) or polybin_set_fisher first, may be NULL).  p_bias is the
+ * shot-noise bias last computed by polybin_pk_bias for POLYBIN_FISHER_PK (zero if none).  pnum_out: host [n_alpha] or
+ * NULL (the numerator without the bias). */
 int polybin_pk_unwindowed(polybin_ctx* ctx, const float* d_dev, const float* w_dev, double* pk_out, double* pnum_out);
 
 /* Unwindowed bispectrum (Sec. 4.2, eq. bk-estimator-def, with the numerator of eq. b-numerator-practical):
@@ -239,9 +240,21 @@ int polybin_sinv_optimal(polybin_ctx* ctx, const float* v_dev, int transpose, vo
  * POLYBIN_FISHER_PK. */
 
 /* Unwindowed P_ell with the optimal weighting: p_num_alpha = 1/2 (1/N) sum_{k in b} L_ell |FT[S^-1 d]|^2, p = F^-1
- * p_num with the POLYBIN_FISHER_PK_OPT Fisher matrix, pk_out = p V / N (host [n_alpha], may be NULL; POLYBIN_ENOTREADY
+ * (p_num - p_bias) with the POLYBIN_FISHER_PK_OPT Fisher matrix and bias (polybin_pk_bias), pk_out = p V / N (host [n_alpha], may be NULL; POLYBIN_ENOTREADY
  * if that Fisher matrix is missing or belongs to another configuration).  pnum_out: host [n_alpha] or NULL. */
 int polybin_pk_unwindowed_opt(polybin_ctx* ctx, const float* d_dev, double* pk_out, double* pnum_out);
+
+/* ---- Poisson shot noise of the P numerator ----------------------------------------------------------------------
+ * Data model d = n delta + eps with <eps eps^T> = diag(n2 / V_cell) (eq. two-point-noise, m = 1; n2 the density of the
+ * doubly-weighted sample, n2 = n for unit weights).  p_bias_alpha = 1/2 <(S^-1 N a) . Q^asym_alpha[S^-1 a]>_a (Sec.
+ * 3.3.2, first line of eq. fish-from-Q, A = I, global line of sight), averaged over the Monte Carlo maps r = 0 ..
+ * n_mc-1 of stream 3: one Monte Carlo term is 1/2 (1/N) sum_{k in b} L_ell Re conj(FT[S^-1 N a]) FT[S^-1 a] (pixel
+ * units, as p_num).  which = POLYBIN_FISHER_PK: S^-1 = w (w_dev); which = POLYBIN_FISHER_PK_OPT: the optimal weighting
+ * of polybin_set_optimal (w_dev unused; two solves per map).  The result is cached for that mode and subtracted by
+ * polybin_pk_unwindowed / polybin_pk_unwindowed_opt until replaced; n_mc = 0 clears it (n2_dev may then be NULL).
+ * bias_out: host [n_alpha] or NULL. */
+int polybin_pk_bias(polybin_ctx* ctx, const float* n2_dev, const float* w_dev, int which, int n_mc,
+                    unsigned long long seed, double* bias_out);
 
 /* X = A^-1 B in FP64 on the GPU (dense LU with partial pivoting).  A: host [n][n], B, X: host [n][nrhs], row major.
  * POLYBIN_EINVAL if A is exactly singular. */

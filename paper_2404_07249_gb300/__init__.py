@@ -72,6 +72,8 @@ _SIGS = {
     "polybin_sinv_optimal": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                             ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
     "polybin_pk_unwindowed_opt": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "polybin_pk_bias": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_ulonglong, ctypes.c_void_p]),
 }
 
 FISHER_PK, FISHER_BK, FISHER_PK_LOCAL, FISHER_PK_OPT = 0, 1, 2, 3
@@ -292,6 +294,15 @@ class PolyBin:
         w32 = None if w_dev is None else _f32(w_dev)
         self._check(self.lib.polybin_fisher_draws(self.ctx, _ptr(n32), None if w32 is None else _ptr(w32), int(seed),
                                                   int(which), int(r0), int(r1), _ptr(out)), "polybin_fisher_draws")
+        return out
+
+    def pk_bias(self, n2_dev, w_dev=None, which: int = FISHER_PK, n_mc: int = 1, seed: int = 0):
+        """Shot-noise bias of the P numerator (pixel units, cached and subtracted by the estimates; n_mc = 0 clears)."""
+        out = np.zeros(self.n_alpha(which))
+        n2 = None if n2_dev is None else _f32(n2_dev)
+        w = None if w_dev is None else _f32(w_dev)
+        self._check(self.lib.polybin_pk_bias(self.ctx, None if n2 is None else _ptr(n2), None if w is None else _ptr(w),
+                                             int(which), int(n_mc), int(seed), _ptr(out)), "polybin_pk_bias")
         return out
 
     # ---- optimal weighting (conjugate gradients)

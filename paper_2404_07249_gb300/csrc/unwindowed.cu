@@ -399,6 +399,9 @@ struct UwState {
     double* dFo_inv = nullptr;
     bool have_o = false;
     uint64_t o_hash = 0;
+    // shot-noise bias of the P numerator per mode (POLYBIN_FISHER_PK, POLYBIN_FISHER_PK_OPT), subtracted by the
+    // estimates while present
+    std::vector<double> pbias[4];
 };
 
 static void uw_free(UwState* u) {
@@ -623,6 +626,49 @@ static int pk_fisher_draw_opt(polybin_ctx* ctx, const float* n, unsigned long lo
                 for (int b2 = 0; b2 < nb; ++b2) F[(size_t)alpha * na + jl * nb + b2] = 0.5 * cross[(size_t)jl * nb + b2] / (double)N;
         }
     }
+    return POLYBIN_OK;
+}
+
+// Shot-noise bias of the P numerator (first line of eq. fish-from-Q, A = I, global line of sight), averaged over
+// draws r = 0..n_mc-1 of stream 3, host [nell][nb]:
+//     p_bias[(l,b)] = 1/2 (1/N) sum_{k in b} L_l Re conj(FT[S^-1 N a]) FT[S^-1 a],   N = diag(n2 / V_cell),
+// with S^-1 = w (which = POLYBIN_FISHER_PK) or the optimal weighting (POLYBIN_FISHER_PK_OPT; two solves per draw).
+template <typename T>
+static int pk_bias_t(polybin_ctx* ctx, const float* n2, const float* w, int which, int n_mc, unsigned long long seed,
+                     std::vector<double>& out) {
+    int rc;
+    if ((rc = uw_alloc<T>(ctx, false))) return rc;
+    UwState* u = static_cast<UwState*>(ctx->ext);
+    Work& W = ctx->w;
+    const long N = ctx->ncell;
+    const int na = ctx->nell * ctx->nb;
+    const double inv_vcell = (double)N / ctx->vol;
+    T* a = (T*)u->a[0];
+    T* sa = (T*)u->a[1];
+    T* xm = (T*)u->xmap;
+    C<T>* X = (C<T>*)u->spec[0];
+    C<T>* Y = (C<T>*)u->spec[1];
+    out.assign(na, 0.0);
+    std::vector<double> cross;
+    for (int r = 0; r < n_mc; ++r) {
+        uw::k_draw<T><<<grid1d((N + 3) / 4), 256, 0, ctx->stream>>>(a, N, seed, (uint32_t)r, 3u);
+        ctx->launches++;
+        PB_CUDA_OK(cudaGetLastError());
+        if (which == 0) {
+            if ((rc = run_forward<T, T, float>(ctx, a, w, n2, (C<T>*)W.t1, (C<T>*)W.t2, X))) return rc;
+            if ((rc = run_forward<T, T, float>(ctx, a, w, (const float*)nullptr, (C<T>*)W.t1, (C<T>*)W.t2, Y))) return rc;
+        } else {
+            if ((rc = opt_apply<T, T, T>(ctx, a, n2, 1, nullptr, 0, xm))) return rc;
+            if ((rc = opt_apply<T, T, T>(ctx, a, nullptr, 1, nullptr, 0, sa))) return rc;
+            if ((rc = run_forward<T, T, float>(ctx, xm, (const float*)nullptr, (const float*)nullptr, (C<T>*)W.t1, (C<T>*)W.t2, X)))
+                return rc;
+            if ((rc = run_forward<T, T, float>(ctx, sa, (const float*)nullptr, (const float*)nullptr, (C<T>*)W.t1, (C<T>*)W.t2, Y)))
+                return rc;
+        }
+        if ((rc = run_cross_bin<T>(ctx, X, Y, u->dpart, cross))) return rc;
+        for (int i = 0; i < na; ++i) out[i] += 0.5 * cross[i] / (double)N * inv_vcell;
+    }
+    for (int i = 0; i < na; ++i) out[i] /= (double)n_mc;
     return POLYBIN_OK;
 }
 
@@ -1104,6 +1150,8 @@ static int pk_unwindowed_t(polybin_ctx* ctx, const float* d, const float* w, dou
     if (pnum_out) std::memcpy(pnum_out, pnum.data(), sizeof(double) * na);
     if (!pk_out) return POLYBIN_OK;
     if (!u->have_p) return fail(ctx, POLYBIN_ENOTREADY, "polybin_pk_unwindowed: run polybin_fisher(POLYBIN_FISHER_PK) first");
+    if (!u->pbias[0].empty())
+        for (int i = 0; i < na; ++i) pnum[i] -= u->pbias[0][i];
     std::vector<double> x;
     if ((rc = apply_inverse(ctx, u->dFp_inv, na, pnum, x))) return rc;
     for (int i = 0; i < na; ++i) pk_out[i] = x[i] * ctx->vol / (double)ctx->ncell;
@@ -1192,6 +1240,8 @@ static int pk_unwindowed_opt_t(polybin_ctx* ctx, const float* d, double* pk_out,
     if (!u->have_o) return fail(ctx, POLYBIN_ENOTREADY, "polybin_pk_unwindowed_opt: run polybin_fisher(POLYBIN_FISHER_PK_OPT) first");
     if (u->o_hash != opt_hash(ctx))
         return fail(ctx, POLYBIN_ENOTREADY, "polybin_pk_unwindowed_opt: the optimal weighting changed since its Fisher matrix was computed");
+    if (!u->pbias[3].empty())
+        for (int i = 0; i < na; ++i) pnum[i] -= u->pbias[3][i];
     std::vector<double> x;
     if ((rc = apply_inverse(ctx, u->dFo_inv, na, pnum, x))) return rc;
     for (int i = 0; i < na; ++i) pk_out[i] = x[i] * ctx->vol / (double)ctx->ncell;
@@ -1320,6 +1370,28 @@ extern "C" int polybin_pk_unwindowed_local(polybin_ctx* ctx, const float* d_dev,
     if (rc) return rc;
     return ctx->prec == POLYBIN_FP64 ? pk_unwindowed_local_t<double>(ctx, d_dev, w_dev, pk_out, pnum_out)
                                      : pk_unwindowed_local_t<float>(ctx, d_dev, w_dev, pk_out, pnum_out);
+}
+
+extern "C" int polybin_pk_bias(polybin_ctx* ctx, const float* n2_dev, const float* w_dev, int which, int n_mc,
+                               unsigned long long seed, double* bias_out) {
+    if (!ctx || (which != 0 && which != 3) || n_mc < 0) return fail(ctx, POLYBIN_EINVAL, "polybin_pk_bias: which in {0, 3}, n_mc >= 0");
+    int rc;
+    if ((rc = ctx->prec == POLYBIN_FP64 ? uw_alloc<double>(ctx, false) : uw_alloc<float>(ctx, false))) return rc;
+    UwState* u = static_cast<UwState*>(ctx->ext);
+    if (n_mc == 0) {
+        u->pbias[which].clear();
+        return POLYBIN_OK;
+    }
+    if ((rc = check_uw_args(ctx, n2_dev, which == 0 ? w_dev : n2_dev, "polybin_pk_bias"))) return rc;
+    if (which == 3 && !opt_hash(ctx))
+        return fail(ctx, POLYBIN_ENOTREADY, "polybin_pk_bias(POLYBIN_FISHER_PK_OPT): call polybin_set_optimal first");
+    std::vector<double> b;
+    if ((rc = ctx->prec == POLYBIN_FP64 ? pk_bias_t<double>(ctx, n2_dev, w_dev, which, n_mc, seed, b)
+                                        : pk_bias_t<float>(ctx, n2_dev, w_dev, which, n_mc, seed, b)))
+        return rc;
+    u->pbias[which] = b;
+    if (bias_out) std::memcpy(bias_out, b.data(), sizeof(double) * b.size());
+    return POLYBIN_OK;
 }
 
 extern "C" int polybin_pk_unwindowed_opt(polybin_ctx* ctx, const float* d_dev, double* pk_out, double* pnum_out) {
