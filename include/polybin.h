@@ -256,6 +256,26 @@ int polybin_pk_unwindowed_opt(polybin_ctx* ctx, const float* d_dev, double* pk_o
 int polybin_pk_bias(polybin_ctx* ctx, const float* n2_dev, const float* w_dev, int which, int n_mc,
                     unsigned long long seed, double* bias_out);
 
+/* ---- Poisson shot noise of the B numerator ----------------------------------------------------------------------
+ * Sec. 4.3.3 (eq. three-point-noise and the Monte Carlo form after it), FKP weighting S^-1 = w, ell = 0, global line
+ * of sight.  The noise is split as N_ijk = -2 N3_ijk + (d_i N2_jk + 2 perms), N3[u, v] = n3 u v / V_cell^2 and
+ * N2 u = d2 u / V_cell (n3: the three-point noise density; d2: the doubly-weighted data minus randoms; n3 = n and
+ * d2 = d for unit weights), and
+ *     b_bias = -1/3 <beta[w N3[a1, a2], w a1, w a2]> + 1/2 <beta[w N2 a1, w a1, w d]>
+ * over the Monte Carlo pairs r = 0 .. n_mc-1 of streams 4 and 5, beta of eq. beta-def (six assignments of the maps to
+ * the bins, 1 / Delta), in the units of b_num.  Each pair costs six forward transforms, six sets of shell maps and
+ * six contractions of 2 n_kbins by n_kbins maps (n_kbins <= 32).  Fields are float32 device arrays [N].
+ * bias_out: host [n_triplets]. */
+int polybin_bk_bias(polybin_ctx* ctx, const float* n3_dev, const float* d2_dev, const float* d_dev, const float* w_dev,
+                    int n_mc, unsigned long long seed, double* bias_out);
+
+/* polybin_bk_unwindowed with the shot noise removed: b = F^-1 (b_num - b_bias), b_bias of polybin_bk_bias for this d
+ * (the bias depends on the data through its second term, so it is computed with the estimate).  bk_out, bnum_out
+ * (without the bias), bias_out: host [n_triplets] or NULL. */
+int polybin_bk_unwindowed_shot(polybin_ctx* ctx, const float* d_dev, const float* w_dev, const float* mocks_dev,
+                               int n_mocks, const float* n3_dev, const float* d2_dev, int n_mc, unsigned long long seed,
+                               double* bk_out, double* bnum_out, double* bias_out);
+
 /* X = A^-1 B in FP64 on the GPU (dense LU with partial pivoting).  A: host [n][n], B, X: host [n][nrhs], row major.
  * POLYBIN_EINVAL if A is exactly singular. */
 int polybin_solve(polybin_ctx* ctx, const double* A, int n, const double* B, int nrhs, double* X);

@@ -72,6 +72,12 @@ _SIGS = {
     "polybin_sinv_optimal": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                             ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
     "polybin_pk_unwindowed_opt": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "polybin_bk_bias": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_int, ctypes.c_ulonglong, ctypes.c_void_p]),
+    "polybin_bk_unwindowed_shot": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                  ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                                  ctypes.c_ulonglong, ctypes.c_void_p, ctypes.c_void_p,
+                                                  ctypes.c_void_p]),
     "polybin_pk_bias": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                        ctypes.c_ulonglong, ctypes.c_void_p]),
 }
@@ -304,6 +310,27 @@ class PolyBin:
         self._check(self.lib.polybin_pk_bias(self.ctx, None if n2 is None else _ptr(n2), None if w is None else _ptr(w),
                                              int(which), int(n_mc), int(seed), _ptr(out)), "polybin_pk_bias")
         return out
+
+    def bk_bias(self, n3_dev, d2_dev, d_dev, w_dev, n_mc: int = 1, seed: int = 0):
+        """Shot-noise bias of the B numerator (units of b_num), FKP weighting."""
+        out = np.zeros(self.num_triplets())
+        args = [_f32(x) for x in (n3_dev, d2_dev, d_dev, w_dev)]
+        self._check(self.lib.polybin_bk_bias(self.ctx, *[_ptr(x) for x in args], int(n_mc), int(seed), _ptr(out)),
+                    "polybin_bk_bias")
+        return out
+
+    def bk_unwindowed_shot(self, d_dev, w_dev, n3_dev, d2_dev, mocks_dev=None, n_mc: int = 1, seed: int = 0):
+        """(b = F^-1 (b_num - b_bias) in physical units, b_num, b_bias)."""
+        nt = self.num_triplets()
+        b, bnum, bias = np.zeros(nt), np.zeros(nt), np.zeros(nt)
+        args = [_f32(x) for x in (d_dev, w_dev, n3_dev, d2_dev)]
+        nm = 0 if mocks_dev is None else int(mocks_dev.shape[0])
+        mk = None if mocks_dev is None else _f32(mocks_dev)
+        self._check(self.lib.polybin_bk_unwindowed_shot(self.ctx, _ptr(args[0]), _ptr(args[1]),
+                                                        None if mk is None else _ptr(mk), nm, _ptr(args[2]),
+                                                        _ptr(args[3]), int(n_mc), int(seed), _ptr(b), _ptr(bnum),
+                                                        _ptr(bias)), "polybin_bk_unwindowed_shot")
+        return b, bnum, bias
 
     # ---- optimal weighting (conjugate gradients)
     def max_shell(self) -> int:

@@ -361,6 +361,17 @@ __global__ void __launch_bounds__(256) k_cross_bin_local(const C<T>* __restrict_
     if (threadIdx.x < nell) partial[((long)b * gridDim.y + seg) * nell + threadIdx.x] = red[threadIdx.x * 256];
 }
 
+// out = scale a (b) m: the noise-weighted products N3[a1, a2] = n3 a1 a2 / V^2 and N2 a = d2 a / V.
+template <typename T>
+__global__ void k_noise_map(T* __restrict__ out, const T* __restrict__ a, const T* __restrict__ b,
+                            const float* __restrict__ m, T scale, long N) {
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) {
+        T v = a[i] * T(m[i]) * scale;
+        if (b) v *= b[i];
+        out[i] = v;
+    }
+}
+
 }  // namespace uw
 
 // ---------------------------------------------------------------------------------------------- state
@@ -402,13 +413,19 @@ struct UwState {
     // shot-noise bias of the P numerator per mode (POLYBIN_FISHER_PK, POLYBIN_FISHER_PK_OPT), subtracted by the
     // estimates while present
     std::vector<double> pbias[4];
+    // bispectrum shot noise: shell maps of X, Y, Z, X on the contraction grid [4][nb][cn], contraction partials and
+    // output for 2 nb maps
+    void* bmaps = nullptr;
+    double* bpart = nullptr;
+    double* bout = nullptr;
+    size_t bpart_cap = 0;
 };
 
 static void uw_free(UwState* u) {
     if (!u) return;
     void* ptrs[] = {u->g2, u->xmap, u->a[0], u->a[1], u->spec[0], u->spec[1], u->spec[2], u->spec[3], u->pairs, u->qbox,
                     u->zc, u->yc, u->v1, u->v2, u->dF, u->dpart, u->dvec, u->dvec2, u->dinfo, u->dFp_inv, u->dFb_inv,
-                    u->ylc, u->hbox, u->g3, u->dFl_inv, u->dFo_inv};
+                    u->ylc, u->hbox, u->g3, u->dFl_inv, u->dFo_inv, u->bmaps, u->bpart, u->bout};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete u;
@@ -669,6 +686,110 @@ static int pk_bias_t(polybin_ctx* ctx, const float* n2, const float* w, int whic
         for (int i = 0; i < na; ++i) out[i] += 0.5 * cross[i] / (double)N * inv_vcell;
     }
     for (int i = 0; i < na; ++i) out[i] /= (double)n_mc;
+    return POLYBIN_OK;
+}
+
+// Delta beta[X, Y, Z] for every closed triplet (eq. beta-def, ell = 0): the sum over the six assignments of (X, Y, Z)
+// to the bins of sum_x g_a g_b g_c, from three contractions of 2 nb maps by nb maps on the contraction grid with the
+// shell maps laid out as [X][Y][Z][X]:  [X, Y] x Z,  [Z, X] x Y,  [Y, Z] x X.  Adds fac * (that) / Delta to acc.
+template <typename T>
+static int beta_sym_add(polybin_ctx* ctx, double fac, std::vector<double>& acc) {
+    UwState* u = static_cast<UwState*>(ctx->ext);
+    const int nb = ctx->nb, n2 = 2 * nb, np2 = n2 * (n2 + 1) / 2;
+    const int nt = (int)ctx->Nabc.size();
+    const long cn = ctx->cg.ncell;
+    const T* G = (const T*)u->bmaps;
+    const T* gX = G;
+    const T* gY = G + (size_t)nb * cn;
+    const T* gZ = G + (size_t)2 * nb * cn;
+    std::vector<double> M[3];
+    const T* first[3] = {gX, gZ, gY};     // [X, Y], [Z, X], [Y, Z]
+    const T* third[3] = {gZ, gY, gX};
+    int rc;
+    for (int c = 0; c < 3; ++c) {
+        if ((rc = run_contract_any<T>(ctx, first[c], n2, third[c], nb, u->bpart, u->bpart_cap, u->bout, cn))) return rc;
+        M[c].resize((size_t)np2 * nb);
+        PB_CUDA_OK(cudaMemcpyAsync(M[c].data(), u->bout, sizeof(double) * M[c].size(), cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    PB_CUDA_OK(cudaStreamSynchronize(ctx->stream));
+    const double rho = ctx->cg_ratio;
+    for (int t = 0; t < nt; ++t) {
+        const int a = ctx->trip[3 * t], b = ctx->trip[3 * t + 1], c = ctx->trip[3 * t + 2];
+        const size_t p_ab = (size_t)pair_index(n2, a, nb + b), p_ba = (size_t)pair_index(n2, b, nb + a);
+        double v = 0.0;
+        for (int k = 0; k < 3; ++k) v += M[k][p_ab * nb + c] + M[k][p_ba * nb + c];
+        const double dl = (a == b && b == c) ? 6.0 : ((a == b || b == c) ? 2.0 : 1.0);
+        acc[t] += fac * rho * v / dl;
+    }
+    return POLYBIN_OK;
+}
+
+// Shell maps of FT[w m] into slot `slot` of the [X][Y][Z][X] layout (slot 0 is copied to slot 3).
+template <typename T, typename TIN>
+static int bias_shells(polybin_ctx* ctx, const TIN* m, const float* w, int slot) {
+    UwState* u = static_cast<UwState*>(ctx->ext);
+    Work& W = ctx->w;
+    const int nb = ctx->nb;
+    const long cn = ctx->cg.ncell;
+    T* G = (T*)u->bmaps + (size_t)slot * nb * cn;
+    int rc;
+    if ((rc = run_forward<T, TIN, float>(ctx, m, w, (const float*)nullptr, (C<T>*)W.t1, (C<T>*)W.t2, (C<T>*)W.box))) return rc;
+    if ((rc = run_shells<T>(ctx, (const C<T>*)W.box, (C<T>*)W.u1, (C<T>*)W.u2, G, 0, ctx->cg))) return rc;
+    if (slot == 0)
+        PB_CUDA_OK(cudaMemcpyAsync((T*)u->bmaps + (size_t)3 * nb * cn, G, sizeof(T) * (size_t)nb * cn,
+                                   cudaMemcpyDeviceToDevice, ctx->stream));
+    return POLYBIN_OK;
+}
+
+// Shot-noise bias of the B numerator (Sec. 4.3.3; FKP weighting S^-1 = w, ell = 0, global line of sight), averaged
+// over the pairs r = 0..n_mc-1 of streams 4 and 5, host [nt] in the units of b_num:
+//     b_bias = -1/3 <beta[w N3[a1, a2], w a1, w a2]> + 1/2 <beta[w N2 a1, w a1, w d]>,
+// N3[a1, a2] = n3 a1 a2 / V_cell^2, N2 a = d2 a / V_cell.
+template <typename T>
+static int bk_bias_t(polybin_ctx* ctx, const float* n3, const float* d2, const float* d, const float* w, int n_mc,
+                     unsigned long long seed, std::vector<double>& out) {
+    int rc;
+    if ((rc = ensure_triplets(ctx))) return rc;
+    if ((rc = uw_alloc<T>(ctx, false))) return rc;
+    UwState* u = static_cast<UwState*>(ctx->ext);
+    const int nb = ctx->nb, nt = (int)ctx->Nabc.size();
+    if (2 * nb > 64) return fail(ctx, POLYBIN_EINVAL, "polybin_bk_bias: at most 32 k-bins");
+    const long N = ctx->ncell, cn = ctx->cg.ncell;
+    if (!u->bmaps) {
+        const ContractGeom G = contract_geom(2 * nb, nb, cn);
+        u->bpart_cap = (size_t)G.ncb * G.npairs * G.nh;
+        cudaError_t e = cudaMalloc(&u->bmaps, sizeof(T) * (size_t)4 * nb * cn);
+        if (e == cudaSuccess) e = cudaMalloc((void**)&u->bpart, sizeof(double) * u->bpart_cap);
+        if (e == cudaSuccess) e = cudaMalloc((void**)&u->bout, sizeof(double) * (size_t)nb * (2 * nb + 1) * nb);
+        if (e != cudaSuccess) return fail_cuda(ctx, e, "bispectrum bias workspace", __FILE__, __LINE__);
+    }
+    if ((rc = ensure_fine_inv<T>(ctx))) return rc;
+    T* a1 = (T*)u->a[0];
+    T* a2 = (T*)u->a[1];
+    T* xm = (T*)u->xmap;
+    const T iv = T((double)N / ctx->vol);
+    out.assign(nt, 0.0);
+    for (int r = 0; r < n_mc; ++r) {
+        uw::k_draw<T><<<grid1d((N + 3) / 4), 256, 0, ctx->stream>>>(a1, N, seed, (uint32_t)r, 4u);
+        uw::k_draw<T><<<grid1d((N + 3) / 4), 256, 0, ctx->stream>>>(a2, N, seed, (uint32_t)r, 5u);
+        ctx->launches += 2;
+        // -1/3 beta[w n3 a1 a2 / V^2, w a1, w a2]
+        uw::k_noise_map<T><<<grid1d(N), 256, 0, ctx->stream>>>(xm, a1, a2, n3, iv * iv, N);
+        ctx->launches++;
+        PB_CUDA_OK(cudaGetLastError());
+        if ((rc = bias_shells<T, T>(ctx, xm, w, 0))) return rc;
+        if ((rc = bias_shells<T, T>(ctx, a1, w, 1))) return rc;
+        if ((rc = bias_shells<T, T>(ctx, a2, w, 2))) return rc;
+        if ((rc = beta_sym_add<T>(ctx, -1.0 / 3.0, out))) return rc;
+        // +1/2 beta[w d2 a1 / V, w a1, w d]   (slot 1 still holds w a1)
+        uw::k_noise_map<T><<<grid1d(N), 256, 0, ctx->stream>>>(xm, a1, (const T*)nullptr, d2, iv, N);
+        ctx->launches++;
+        PB_CUDA_OK(cudaGetLastError());
+        if ((rc = bias_shells<T, T>(ctx, xm, w, 0))) return rc;
+        if ((rc = bias_shells<T, float>(ctx, d, w, 2))) return rc;
+        if ((rc = beta_sym_add<T>(ctx, 0.5, out))) return rc;
+    }
+    for (int t = 0; t < nt; ++t) out[t] /= (double)n_mc;
     return POLYBIN_OK;
 }
 
@@ -1160,7 +1281,7 @@ static int pk_unwindowed_t(polybin_ctx* ctx, const float* d, const float* w, dou
 
 template <typename T>
 static int bk_unwindowed_t(polybin_ctx* ctx, const float* d, const float* w, const float* mocks, int n_mocks,
-                           double* bk_out, double* bnum_out, double* lin_out) {
+                           double* bk_out, double* bnum_out, double* lin_out, const double* bias = nullptr) {
     int rc;
     if ((rc = ensure_triplets(ctx))) return rc;
     if ((rc = uw_alloc<T>(ctx, false))) return rc;
@@ -1207,6 +1328,8 @@ static int bk_unwindowed_t(polybin_ctx* ctx, const float* d, const float* w, con
     if (lin_out) std::memcpy(lin_out, lin.data(), sizeof(double) * nt);
     if (!bk_out) return POLYBIN_OK;
     if (!u->have_b) return fail(ctx, POLYBIN_ENOTREADY, "polybin_bk_unwindowed: run polybin_fisher(POLYBIN_FISHER_BK) first");
+    if (bias)
+        for (int t = 0; t < nt; ++t) bnum[t] -= bias[t];
     std::vector<double> x;
     if ((rc = apply_inverse(ctx, u->dFb_inv, nt, bnum, x))) return rc;
     const double v2 = (ctx->vol / (double)N) * (ctx->vol / (double)N);
@@ -1416,6 +1539,37 @@ extern "C" int polybin_bk_unwindowed(polybin_ctx* ctx, const float* d_dev, const
         return fail(ctx, POLYBIN_EINVAL, "polybin_bk_unwindowed: mocks must be device memory when n_mocks > 0");
     return ctx->prec == POLYBIN_FP64 ? bk_unwindowed_t<double>(ctx, d_dev, w_dev, mocks_dev, n_mocks, bk_out, bnum_out, lin_out)
                                      : bk_unwindowed_t<float>(ctx, d_dev, w_dev, mocks_dev, n_mocks, bk_out, bnum_out, lin_out);
+}
+
+extern "C" int polybin_bk_bias(polybin_ctx* ctx, const float* n3_dev, const float* d2_dev, const float* d_dev,
+                               const float* w_dev, int n_mc, unsigned long long seed, double* bias_out) {
+    int rc = check_uw_args(ctx, n3_dev, d2_dev, "polybin_bk_bias");
+    if (rc || (rc = check_uw_args(ctx, d_dev, w_dev, "polybin_bk_bias"))) return rc;
+    if (n_mc < 1 || !bias_out) return fail(ctx, POLYBIN_EINVAL, "polybin_bk_bias: n_mc >= 1 and bias_out required");
+    std::vector<double> b;
+    if ((rc = ctx->prec == POLYBIN_FP64 ? bk_bias_t<double>(ctx, n3_dev, d2_dev, d_dev, w_dev, n_mc, seed, b)
+                                        : bk_bias_t<float>(ctx, n3_dev, d2_dev, d_dev, w_dev, n_mc, seed, b)))
+        return rc;
+    std::memcpy(bias_out, b.data(), sizeof(double) * b.size());
+    return POLYBIN_OK;
+}
+
+extern "C" int polybin_bk_unwindowed_shot(polybin_ctx* ctx, const float* d_dev, const float* w_dev, const float* mocks_dev,
+                                          int n_mocks, const float* n3_dev, const float* d2_dev, int n_mc,
+                                          unsigned long long seed, double* bk_out, double* bnum_out, double* bias_out) {
+    int rc = check_uw_args(ctx, d_dev, w_dev, "polybin_bk_unwindowed_shot");
+    if (rc || (rc = check_uw_args(ctx, n3_dev, d2_dev, "polybin_bk_unwindowed_shot"))) return rc;
+    if (n_mocks < 0 || (n_mocks > 0 && (!mocks_dev || !is_device_ptr(mocks_dev))) || n_mc < 1)
+        return fail(ctx, POLYBIN_EINVAL, "polybin_bk_unwindowed_shot: bad mocks or n_mc < 1");
+    if ((rc = ensure_triplets(ctx))) return rc;
+    std::vector<double> b;
+    if ((rc = ctx->prec == POLYBIN_FP64 ? bk_bias_t<double>(ctx, n3_dev, d2_dev, d_dev, w_dev, n_mc, seed, b)
+                                        : bk_bias_t<float>(ctx, n3_dev, d2_dev, d_dev, w_dev, n_mc, seed, b)))
+        return rc;
+    if (bias_out) std::memcpy(bias_out, b.data(), sizeof(double) * b.size());
+    return ctx->prec == POLYBIN_FP64
+               ? bk_unwindowed_t<double>(ctx, d_dev, w_dev, mocks_dev, n_mocks, bk_out, bnum_out, nullptr, b.data())
+               : bk_unwindowed_t<float>(ctx, d_dev, w_dev, mocks_dev, n_mocks, bk_out, bnum_out, nullptr, b.data());
 }
 
 extern "C" int polybin_solve(polybin_ctx* ctx, const double* A, int n, const double* B, int nrhs, double* X) {

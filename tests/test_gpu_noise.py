@@ -93,3 +93,27 @@ def test_pk_bias_optimal(pkg, fields):
     ref = noise.pk_bias(n2, vcell, sinv, bins, mu2, nb, ells, 21, 2, unwindowed.draw, 3, np.float32).ravel()
     assert np.max(np.abs(got - ref)) < 1e-4 * np.max(np.abs(ref))
     pb.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "split"])
+def test_bk_bias_and_estimate(pkg, fields, prec):
+    """B shot noise: same Monte Carlo pairs (streams 4, 5) as the oracle, within 2e-5 of the largest |value| (FP32 maps
+    and sums of six assignments with cancelling signs), and the estimate F^-1 (b_num - b_bias)."""
+    n, n2, w, _, _ = fields
+    edges = binning.kf_of(BOX) * np.array([1.0, 3.0, 5.0, 7.0])
+    nb = len(edges) - 1
+    vcell = BOX ** 3 / n.size
+    d = (np.random.Generator(np.random.PCG64(4)).poisson(n.astype(np.float64) * vcell) / vcell - n).astype(np.float32)
+    pb = pkg.PolyBin(GRID, BOX, edges, prec=prec)
+    trip = [tuple(t) for t in pb.triplets()[0].tolist()]
+    got = pb.bk_bias(_dev(n), _dev(d), _dev(d), _dev(w), n_mc=2, seed=17)
+    bins = binning.bin_grid(GRID, BOX, edges)
+    ref = noise.bk_bias(d, n, d, vcell, lambda v: w.astype(np.float64) * v, bins, nb, trip, 17, 2, unwindowed.draw,
+                        (4, 5), np.float32)
+    assert np.max(np.abs(got - ref)) < 2e-5 * np.max(np.abs(ref)), np.max(np.abs(got - ref)) / np.max(np.abs(ref))
+    F, _ = pb.fisher(_dev(n), _dev(w), 1, 2, pkg.FISHER_BK)
+    b, bnum, bias = pb.bk_unwindowed_shot(_dev(d), _dev(w), _dev(n), _dev(d), n_mc=2, seed=17)
+    assert np.array_equal(bias, got)
+    want = unwindowed.solve(F, bnum - bias) * (BOX ** 3 / n.size) ** 2
+    assert np.max(np.abs(b - want)) < 1e-9 * np.max(np.abs(want))
+    pb.close()
