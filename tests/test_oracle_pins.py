@@ -346,3 +346,48 @@ def test_bispectrum_quadrupole_of_transverse_modes():
     assert scale > 0
     assert np.max(np.abs(B2 - 5 * (-0.5) * B0)) <= 1e-12 * scale
     assert np.max(np.abs(B4 - 9 * 0.375 * B0)) <= 1e-12 * scale
+
+
+def test_unwindowed_bk_matches_ideal_on_injected_bispectrum_mocks():
+    """Sec. 6.2 validation design: mocks with an injected bispectrum; the unwindowed estimator on the masked mocks
+    (eq. bk-estimator-def: FKP weight, Monte Carlo Fisher of eq. bk-fish-def, the zero-mean linear term dropped)
+    agrees with the ideal estimator on the same unmasked mocks, whereas the windowed estimate (the ideal estimator on
+    the masked mocks, rescaled by mean n^3) is distorted by the mask.
+    Mocks: g a Gaussian field with a flat spectrum on the binned band and none outside, delta = g + f Theta[g^2] with
+    Theta the band filter, so that the bispectrum is 6 f P^2 on every binned triangle (plus an O(f^3) term, 4 % here)
+    and no mode outside the bins carries power that the mask could couple into them (the paper's validation likewise
+    sets the spectrum to zero outside the range of interest).  500 mocks, 500 Fisher pairs: the mean difference lies
+    within 4 standard errors on every triplet; the signal and the windowed distortion are detected at > 10."""
+    n = 16
+    grid = (n, n, n)
+    box = 400.0
+    kf = binning.kf_of(box)
+    edges = kf * np.array([1.0, 2.5, 4.0, 5.5])
+    nb = 3
+    bins = binning.bin_grid(grid, box, edges)
+    trip = binning.triplets(nb)
+    geom = synth.SurveyGeometry(r_min=0.1 * box, r_max=0.48 * box, n_holes=2, hole_radius=0.07 * box, n0=3.0e-4,
+                                r0=0.3 * box, s2=0.05 * box * box)
+    nmask = synth.survey_mask(grid, (box,) * 3, 5, geom)
+    w = unwindowed.fkp_weight(nmask, 1.0e4)
+    F = unwindowed.bk_fisher(nmask, w, bins, nb, trip, seed=11, n_mc=500)
+    scale = (box ** 3 / nmask.size) ** 2
+    band = bins >= 0
+    n3 = np.mean(nmask ** 3)
+    ide, unw, win = [], [], []
+    for i in range(500):
+        g = synth.gaussian_field(grid, (box,) * 3, 300 + i, pk=lambda k: np.ones_like(k), kmin=edges[0], kmax=edges[-1])
+        g = g / g.std()
+        dl = g + 0.3 * np.fft.ifftn(np.where(band, np.fft.fftn(g * g), 0.0)).real
+        ide.append(ideal.bk_ideal(dl, box, edges)["B"])
+        bn = unwindowed.bk_numerator(nmask * dl, w, [], bins, nb, trip)["b_num"]
+        unw.append(unwindowed.solve(F, bn) * scale)
+        win.append(ideal.bk_ideal(nmask * dl, box, edges)["B"] / n3)
+    ide, unw, win = np.array(ide), np.array(unw), np.array(win)
+
+    def z(x):
+        return x.mean(0) / (x.std(0, ddof=1) / math.sqrt(len(x)))
+
+    assert np.max(np.abs(z(unw - ide))) < 4.0, z(unw - ide)
+    assert np.min(z(ide)) > 10.0
+    assert np.max(np.abs(z(win - ide))) > 10.0
