@@ -504,7 +504,7 @@ def main():
                        "statistics": "B_abc(all closed) + P_ell(0,2)", "precision_mode": args.prec,
                        "l2": f"inputs {field.nbytes / 1e6:.0f} MB" + (" > L2 (no flush needed)" if field.nbytes > 129e6
                                                                        else " (not larger than L2)"),
-                       "nabc_init_s": t_nabc},
+                       "nabc_init_s": t_nabc, "contraction_plan": pb.contract_plan_info()},
             "e2e": {"value": world * 1000.0 / e2e_ms, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "clocks": clocks, "roofline": roof}

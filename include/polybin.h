@@ -198,6 +198,15 @@ int polybin_pk_unwindowed(polybin_ctx* ctx, const float* d_dev, const float* w_d
 int polybin_bk_unwindowed(polybin_ctx* ctx, const float* d_dev, const float* w_dev, const float* mocks_dev, int n_mocks,
                           double* bk_out, double* bnum_out, double* lin_out);
 
+/* The closed-triplet plan of the split-TF32 contraction (after the first estimate; -1 before) and the autotuner's
+ * choice.  info: [0] tile cost of the tile-cutting DP, [1] tiles a row group may take, [2] cell split (0: one CTA per
+ * SM and row group; 1: one wave of SMs / groups CTAs a group; 2: two CTAs per SM and group), [3] row groups, [4] CTAs
+ * per group, [5] candidates timed (0: not tuned).  ms: the chosen plan's time per launch on the tuning inputs.  The
+ * autotuner runs on the first contraction outside stream capture: every distinct valid candidate is launched twice
+ * on the caller's inputs and the fastest kept (POLYBIN_AUTOTUNE=0 in the environment keeps the default plan).  Not
+ * part of the paper's interface. */
+int polybin_contract_plan_info(polybin_ctx* ctx, int info[6], float* ms);
+
 /* ---- optimal weighting by preconditioned conjugate gradients ------------------------------------------------------
  * Sec. 2.4, eq. cgd-operation-eqn and the transpose equation beside it; Sec. 3.3.3, eq. Sinv-optimal in the
  * distant-observer limit.  Data model d = n delta + eps, C = P xi P^T + N with P = diag(n), N = diag(n2) (pixel window

@@ -66,6 +66,7 @@ _SIGS = {
     "polybin_bk_ideal_multipoles": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                                    ctypes.c_void_p]),
     "polybin_contraction_grid": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "polybin_contract_plan_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)]),
     "polybin_max_shell": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
     "polybin_set_optimal": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double]),
@@ -244,6 +245,17 @@ class PolyBin:
         d = np.zeros(3, dtype=np.int32)
         self._check(self.lib.polybin_contraction_grid(self.ctx, _ptr(d)), "polybin_contraction_grid")
         return tuple(int(v) for v in d)
+
+    def contract_plan_info(self) -> dict:
+        """The closed-triplet tensor-core plan and the autotuner's choice (-1 entries before the first estimate)."""
+        info = np.zeros(6, dtype=np.int32)
+        ms = ctypes.c_float(0.0)
+        self._check(self.lib.polybin_contract_plan_info(self.ctx, _ptr(info), ctypes.byref(ms)),
+                    "polybin_contract_plan_info")
+        keys = ("tile_cost", "group_cap", "cta_mode", "row_groups", "ctas_per_group", "candidates_timed")
+        out = {k: int(v) for k, v in zip(keys, info)}
+        out["ms"] = float(ms.value)
+        return out
 
     def launch_count(self) -> int:
         n = ctypes.c_longlong()

@@ -217,6 +217,11 @@ int run_shells_m(polybin_ctx* ctx, const C<T>* box, C<T>* u1, C<T>* u2, T* g, in
             const int lpc = 16;
             dim3 grid512((unsigned)(((nlines + 1) / 2 + lpc - 1) / lpc), nb, 1);
             k_inv_z512<T><<<grid512, 256, 0, ctx->stream>>>(b, nlines, T(1), (const T*)nullptr, tw(2), lpc);
+        } else if (N2 == 256) {
+            // register-resident 256-point transform, one warp a line pair, 16 line pairs per CTA
+            const int lpc = 16;
+            dim3 grid256((unsigned)(((nlines + 1) / 2 + lpc - 1) / lpc), nb, 1);
+            k_inv_z256<T><<<grid256, 256, 0, ctx->stream>>>(b, nlines, T(1), (const T*)nullptr, tw(2), lpc);
         } else if (N2 == 288 && sizeof(T) == 4) {
             // register-resident 288-point transform, 128 line pairs per CTA (8 rounds of 16, input staged with
             // cp.async one round ahead)

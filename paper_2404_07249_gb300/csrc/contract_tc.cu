@@ -42,8 +42,10 @@
 
 #include <algorithm>
 #include <cstring>
+#include <cstdlib>
 #include <map>
 #include <mutex>
+#include <set>
 #include <tuple>
 #include <vector>
 
@@ -1014,8 +1016,26 @@ struct NeedPair {
     std::vector<std::pair<int, int>> outs;        // (single, output index)
 };
 
+// Run-time choices of a plan that leave the kernel unchanged, tried by the autotuner: the per-tile cost of the
+// tile-cutting DP (small: more, narrower tiles; large: fewer, wider ones), the number of tiles a row group (CTA)
+// may take, and the cell split (0: one CTA per SM and row group, ngroups waves; 1: one wave of SMs / ngroups CTAs
+// per group; 2: two CTAs per SM and row group, shorter cell ranges).
+struct PlanOpts {
+    int tile_cost = 8;
+    int group_cap = 3;
+    int cta_mode = 0;
+};
+
 struct Plan {
     int ng = 0, nh = 0, hsep = 0, n_out = 0, ncta = 0, ngroups = 0, total_units = 0;
+    PlanOpts opts{};
+    bool tuned = false;
+    float tuned_ms = 0.f;   // time of the chosen candidate (0 when not tuned)
+    int tuned_of = 0;       // candidates timed
+    // what the plan was built from (the autotuner rebuilds it with other options)
+    std::vector<NeedPair> need;
+    int sing_g = 0;
+    long ncell = 0;
     long cells_cta = 0;
     Params base{};
     size_t smem = 0;
@@ -1033,7 +1053,7 @@ static int round_w(int w) { return w <= 16 ? 16 : 32; }
 
 // Tiles of <= 128 pairs, consecutive in the order of (hi, lo), cut by dynamic programming to minimise the summed
 // window width (the tensor work) plus a per-tile cost.
-static std::vector<std::pair<int, int>> cut_tiles(const std::vector<NeedPair>& P) {
+static std::vector<std::pair<int, int>> cut_tiles(const std::vector<NeedPair>& P, int tile_cost) {
     const int n = (int)P.size();
     std::vector<long> f(n + 1, (long)1 << 40);
     std::vector<int> arg(n + 1, 0);
@@ -1045,7 +1065,7 @@ static std::vector<std::pair<int, int>> cut_tiles(const std::vector<NeedPair>& P
             hi = std::max(hi, P[j].hi);
             const int s0 = lo / 8 * 8;
             if (hi + 1 - s0 > 32) break;
-            const long c = f[j] + round_w(hi + 1 - s0) + 8;
+            const long c = f[j] + round_w(hi + 1 - s0) + tile_cost;
             if (c < f[i]) { f[i] = c; arg[i] = j; }
         }
     }
@@ -1060,14 +1080,18 @@ static std::vector<std::pair<int, int>> cut_tiles(const std::vector<NeedPair>& P
 // sing_g = 1 with hsep = 1: the slot holds the g rows and the h rows (pairs may take one map from each, h rows at
 // index h_row0 + i) and the singles are the g rows.
 static const char* layout_plan(Plan& pl, long ncell, int nsm, int ng, int nh, int hsep, std::vector<NeedPair> need,
-                               int n_out, std::vector<short2>& rows, std::vector<int>& gidx, int sing_g = 0) {
+                               int n_out, std::vector<short2>& rows, std::vector<int>& gidx, int sing_g = 0,
+                               const PlanOpts& opts = PlanOpts{}) {
     pl.ng = ng; pl.nh = nh; pl.hsep = hsep; pl.n_out = n_out;
+    pl.opts = opts;
+    if (opts.group_cap < 1 || opts.group_cap > kMaxTiles || opts.cta_mode < 0 || opts.cta_mode > 2)
+        return "contract_tc: bad plan options";
     std::stable_sort(need.begin(), need.end(), [](const NeedPair& a, const NeedPair& b) {
         return std::tie(a.hi, a.lo) < std::tie(b.hi, b.lo);
     });
     for (const NeedPair& p : need)
         if (p.hi + 1 - p.lo / 8 * 8 > 32) return "contract_tc: a pair needs a window of more than 32 singles";
-    auto seg = need.empty() ? std::vector<std::pair<int, int>>{} : cut_tiles(need);
+    auto seg = need.empty() ? std::vector<std::pair<int, int>>{} : cut_tiles(need, opts.tile_cost);
     struct TileH { int first, last, s0, W; };
     std::vector<TileH> tiles;
     for (auto& sg : seg) {
@@ -1084,7 +1108,7 @@ static const char* layout_plan(Plan& pl, long ncell, int nsm, int ng, int nh, in
     std::vector<std::pair<int, int>> groups;
     for (int t = 0; t < (int)tiles.size();) {
         int e = t, dcols = 0, units = 0;
-        while (e < (int)tiles.size() && e - t < kMaxTiles) {
+        while (e < (int)tiles.size() && e - t < opts.group_cap) {
             const int nd = dcols + 2 * tiles[e].W, nu = units + tiles[e].W / 16, nt = e - t + 1;
             if (nu > kMaxUnits || kDBuf * ((nd + 31) / 32 * 32) + 2 * 2 * kKC * nt > 512) break;
             dcols = nd; units = nu; ++e;
@@ -1170,7 +1194,8 @@ static const char* layout_plan(Plan& pl, long ncell, int nsm, int ng, int nh, in
     if (pl.smem > 227 * 1024) return "contract_tc: shared memory plan exceeds 227 KB";
 
     const long nsl = (ncell + kSlotCells - 1) / kSlotCells;
-    pl.ncta = (int)std::max(1L, std::min((long)nsm, nsl));
+    const long want = opts.cta_mode == 1 ? std::max(1L, (long)nsm / pl.ngroups) : (opts.cta_mode == 2 ? 2L * nsm : (long)nsm);
+    pl.ncta = (int)std::max(1L, std::min(want, nsl));
     pl.cells_cta = (nsl + pl.ncta - 1) / pl.ncta * kSlotCells;
     pl.ncta = (int)((ncell + pl.cells_cta - 1) / pl.cells_cta);
     P.ncell = ncell;
@@ -1179,15 +1204,18 @@ static const char* layout_plan(Plan& pl, long ncell, int nsm, int ng, int nh, in
 }
 
 static int build_plan(polybin_ctx* ctx, Plan& pl, long ncell, int ng, int nh, int hsep, std::vector<NeedPair> need,
-                      int n_out, int sing_g = 0) {
+                      int n_out, int sing_g = 0, const PlanOpts& opts = PlanOpts{}, bool quiet = false) {
     int dev = 0, nsm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return fail_cuda(ctx, e, "cudaDeviceGetAttribute", __FILE__, __LINE__);
     std::vector<short2> rows;
     std::vector<int> gidx;
-    const char* msg = layout_plan(pl, ncell, nsm, ng, nh, hsep, std::move(need), n_out, rows, gidx, sing_g);
-    if (msg) return fail(ctx, POLYBIN_EINVAL, "%s", msg);
+    pl.need = need;
+    pl.sing_g = sing_g;
+    pl.ncell = ncell;
+    const char* msg = layout_plan(pl, ncell, nsm, ng, nh, hsep, std::move(need), n_out, rows, gidx, sing_g, opts);
+    if (msg) return quiet ? POLYBIN_EINVAL : fail(ctx, POLYBIN_EINVAL, "%s", msg);
     PB_CUDA_OK(cudaMalloc(&pl.d_rows, sizeof(short2) * rows.size()));
     PB_CUDA_OK(cudaMemcpy(pl.d_rows, rows.data(), sizeof(short2) * rows.size(), cudaMemcpyHostToDevice));
     PB_CUDA_OK(cudaMalloc(&pl.d_gidx, sizeof(int) * gidx.size()));
@@ -1310,6 +1338,89 @@ static int launch(polybin_ctx* ctx, Plan& pl, const float* g, const float* h, do
 static PlanCache* cache_of(polybin_ctx* ctx) {
     if (!ctx->tc) ctx->tc = new PlanCache();
     return static_cast<PlanCache*>(ctx->tc);
+}
+
+// Autotuner.  On the first launch of a plan outside stream capture (unless POLYBIN_AUTOTUNE=0), every distinct valid
+// candidate of the option grid {tile cost 8, 24} x {3 or 1 tiles a group} x {cell splits 0, 1, 2} runs on the
+// caller's own inputs, timed with CUDA events on the context stream (one launch to warm up, two timed); the fastest
+// replaces the plan in the cache.  Candidates differ only in how cells and rows are split, so their results agree to
+// FP32 rounding of the partial sums; after tuning every call takes the chosen plan.
+static int tune_plan(polybin_ctx* ctx, Plan** pl_io, const float* g, const float* h, double* d_out) {
+    Plan* pl = *pl_io;
+    if (pl->tuned) return POLYBIN_OK;
+    if (ctx->capturing) {   // a captured graph keeps this plan's buffers: it must never be replaced
+        pl->tuned = true;
+        return POLYBIN_OK;
+    }
+    const char* env = std::getenv("POLYBIN_AUTOTUNE");
+    if (env && env[0] == '0') { pl->tuned = true; return POLYBIN_OK; }
+    PlanCache* pc = cache_of(ctx);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    PB_CUDA_OK(cudaEventCreate(&e0));
+    PB_CUDA_OK(cudaEventCreate(&e1));
+    auto time_plan = [&](Plan& c, float* ms) -> int {
+        int rc;
+        if ((rc = launch(ctx, c, g, h, d_out))) return rc;
+        PB_CUDA_OK(cudaEventRecord(e0, ctx->stream));
+        for (int i = 0; i < 2; ++i)
+            if ((rc = launch(ctx, c, g, h, d_out))) return rc;
+        PB_CUDA_OK(cudaEventRecord(e1, ctx->stream));
+        PB_CUDA_OK(cudaEventSynchronize(e1));
+        PB_CUDA_OK(cudaEventElapsedTime(ms, e0, e1));
+        *ms *= 0.5f;
+        return POLYBIN_OK;
+    };
+    float best_ms = 0.f;
+    int rc = time_plan(*pl, &best_ms);
+    Plan* best = pl;
+    int tried = 1;
+    std::vector<Plan*> others;
+    auto sig = [](const Plan& c) {   // (tiles, groups, ncta, cells a CTA, units): equal signatures, equal launches
+        int nt = 0;
+        for (int i = 0; i < c.ngroups; ++i) nt += c.base.grp[i].ntiles;
+        return std::make_tuple(nt, c.ngroups, c.ncta, c.cells_cta, c.total_units);
+    };
+    std::set<std::tuple<int, int, int, long, int>> seen;
+    seen.insert(sig(*pl));
+    const int costs[2] = {8, 24}, caps[2] = {kMaxTiles, 1};
+    for (int ci = 0; ci < 2 && !rc; ++ci)
+        for (int gi = 0; gi < 2 && !rc; ++gi)
+            for (int mode = 0; mode < 3 && !rc; ++mode) {
+                PlanOpts o;
+                o.tile_cost = costs[ci];
+                o.group_cap = caps[gi];
+                o.cta_mode = mode;
+                Plan* c = new Plan();
+                if (build_plan(ctx, *c, pl->ncell, pl->ng, pl->nh, pl->hsep, pl->need, pl->n_out, pl->sing_g, o, true)) {
+                    delete c;
+                    continue;
+                }
+                if (!seen.insert(sig(*c)).second) { delete c; continue; }
+                float ms = 0.f;
+                rc = time_plan(*c, &ms);
+                ++tried;
+                others.push_back(c);
+                if (!rc && ms < best_ms) { best_ms = ms; best = c; }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // keep the winner in the cache slot of the original plan
+    for (auto& kv : pc->plans)
+        if (kv.second == pl) kv.second = best;
+    if (best != pl) delete pl;
+    for (Plan* c : others)
+        if (c != best) delete c;
+    best->tuned = true;
+    best->tuned_ms = best_ms;
+    best->tuned_of = tried;
+    *pl_io = best;
+    return rc;
+}
+
+static int launch_tuned(polybin_ctx* ctx, Plan* pl, const float* g, const float* h, double* d_out) {
+    int rc;
+    if ((rc = tune_plan(ctx, &pl, g, h, d_out))) return rc;
+    return launch(ctx, *pl, g, h, d_out);
 }
 
 // Plan of all pairs (j <= k) of ng maps against the nh singles [0, nh), output M[(j, k)][i] pair-major.
@@ -1462,7 +1573,7 @@ int run_contract_tc(polybin_ctx* ctx, const float* g, int ng, const float* h, in
     tc::Plan* pl = nullptr;
     int rc = tc::full_plan(ctx, ncell, ng, nh, hsep, &pl);
     if (rc) return rc;
-    return tc::launch(ctx, *pl, g, hsep ? h : g, d_out);
+    return tc::launch_tuned(ctx, pl, g, hsep ? h : g, d_out);
 }
 
 // Builds the closed-triplet plan ahead of time (before any stream capture).
@@ -1477,7 +1588,7 @@ int run_triplet_sums_ell_tc(polybin_ctx* ctx, const float* g, const float* gl, d
     tc::Plan* pl = nullptr;
     int rc = tc::ell_plan(ctx, &pl);
     if (rc) return rc;
-    return tc::launch(ctx, *pl, g, gl, d_S);
+    return tc::launch_tuned(ctx, pl, g, gl, d_S);
 }
 
 // out[i][j] += scale sum_k A[i][k] B[j][k] for float32 rows A [nA][K], B [nB][K] (K a multiple of 4, 16-byte aligned
@@ -1539,7 +1650,7 @@ int run_triplet_sums_tc(polybin_ctx* ctx, const float* g, double* d_S) {
     tc::Plan* pl = nullptr;
     int rc = tc::triplet_plan(ctx, &pl);
     if (rc) return rc;
-    return tc::launch(ctx, *pl, g, g, d_S);
+    return tc::launch_tuned(ctx, pl, g, g, d_S);
 }
 
 }  // namespace pb
@@ -1554,5 +1665,25 @@ extern "C" int polybin_selftest_wait(polybin_ctx* ctx, int* timed_out) {
     PB_CUDA_OK(cudaGetLastError());
     PB_CUDA_OK(cudaMemcpyAsync(timed_out, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     PB_CUDA_OK(cudaStreamSynchronize(ctx->stream));
+    return POLYBIN_OK;
+}
+
+// The closed-triplet plan of the context's tensor-core contraction (ell = 0) and what the autotuner chose.
+extern "C" int polybin_contract_plan_info(polybin_ctx* ctx, int info[6], float* ms) {
+    if (!ctx || !info) return pb::fail(ctx, POLYBIN_EINVAL, "polybin_contract_plan_info: NULL argument");
+    for (int i = 0; i < 6; ++i) info[i] = -1;
+    if (ms) *ms = 0.f;
+    if (!ctx->tc) return POLYBIN_OK;
+    pb::tc::PlanCache* pc = static_cast<pb::tc::PlanCache*>(ctx->tc);
+    auto it = pc->plans.find(std::make_tuple(ctx->nb, ctx->nb, 0, 1, ctx->cg.ncell));
+    if (it == pc->plans.end()) return POLYBIN_OK;
+    const pb::tc::Plan& p = *it->second;
+    info[0] = p.opts.tile_cost;
+    info[1] = p.opts.group_cap;
+    info[2] = p.opts.cta_mode;
+    info[3] = p.ngroups;
+    info[4] = p.ncta;
+    info[5] = p.tuned ? p.tuned_of : 0;
+    if (ms) *ms = p.tuned_ms;
     return POLYBIN_OK;
 }

@@ -476,6 +476,131 @@ __global__ void __launch_bounds__(256) k_inv_z512(ZInvBatch batch, long nlines, 
 }
 
 // ------------------------------------------------------------------------------------------------
+// z-pass, inverse (C2R), length 256, register-resident, one warp per packed line pair (the same result as k_inv_z,
+// including the packing of line pairs and the kz = 0 and n/2 treatment; measured 44 us against the staged kernel's
+// 46 us at 256^3 with 48 kept wave numbers; a forward counterpart on the same scheme was slower than k_fwd_z).  With k = t + 32 j and n = n1 + 8 n2,
+// n2 = c + 8 d, t = a + 4 b (w_m = e^{DIR 2 pi i / m}):
+//   X[n1 + 8 c + 64 d] = sum_a w4^(a d) [ w32^(a c) sum_b w8^(b c) ( w256^(t n1) sum_j Z[t + 32 j] w8^(j n1) ) ]
+// stage 1: lane t takes the 8-point DFT over j of its points and the twiddles w256^(t n1); stage 2 (after an exchange
+// through shared memory): lane (n1, a) = (lane / 4, lane % 4) the 8-point DFT over b and the twiddles w32^(a c);
+// stage 3: lane (n1, c0) = (lane % 8, lane / 8) the two 4-point DFTs over a for c = c0 and c0 + 4.  Twiddles come
+// from the table tw[m] = e^{-2 pi i m / 256} once per lane and stay in registers; the warp synchronises with
+// __syncwarp only.  Eight warps a CTA; a CTA takes `lpc` line pairs.
+constexpr int kZ256Pad = 9;   // exchange rows of 8 complex values padded to 9 (conflict-free column reads)
+
+// In-register 256-point DFT of one warp (lane t holds v[j] = Z[t + 32 j]); on return lane (n1, c0) holds
+// X[n1 + 8 c + 64 d] in v[d] (c = c0) and v[4 + d] (c = c0 + 4), n1 = lane % 8, c0 = lane / 8.
+template <typename T, int DIR>
+__device__ __forceinline__ void fft256_warp(C<T> (&v)[8], C<T>* buf, const C<T> (&w1)[8], const C<T> (&w2)[8],
+                                            int lane) {
+    dft<T, DIR>(v, 8);                                     // over j -> n1
+#pragma unroll
+    for (int r = 1; r < 8; ++r) v[r] = DIR < 0 ? mul<T>(v[r], w1[r]) : mulc<T>(v[r], w1[r]);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) buf[lane * kZ256Pad + r] = v[r];          // row t, column n1
+    __syncwarp();
+    const int n1 = lane >> 2, a = lane & 3;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) v[b] = buf[(a + 4 * b) * kZ256Pad + n1];  // Y[a + 4 b][n1]
+    dft<T, DIR>(v, 8);                                     // over b -> c
+#pragma unroll
+    for (int r = 1; r < 8; ++r) v[r] = DIR < 0 ? mul<T>(v[r], w2[r]) : mulc<T>(v[r], w2[r]);
+    __syncwarp();
+#pragma unroll
+    for (int c = 0; c < 8; ++c) buf[(n1 * 8 + c) * 4 + a] = v[c];          // [(n1, c)][a], 4 a row
+    __syncwarp();
+    const int m1 = lane & 7, c0 = lane >> 3;
+    C<T> u[4], x[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) { u[q] = buf[(m1 * 8 + c0) * 4 + q]; x[q] = buf[(m1 * 8 + c0 + 4) * 4 + q]; }
+    dft<T, DIR>(u, 4);                                     // over a -> d
+    dft<T, DIR>(x, 4);
+#pragma unroll
+    for (int d = 0; d < 4; ++d) { v[d] = u[d]; v[4 + d] = x[d]; }
+    __syncwarp();
+}
+
+template <typename T>
+__device__ __forceinline__ void z256_twiddles(const C<T>* __restrict__ twg, int lane, C<T> (&w1)[8], C<T> (&w2)[8]) {
+    const int a = lane & 3;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        w1[r] = twg[(lane * r) & 255];
+        w2[r] = twg[(8 * a * r) & 255];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_inv_z256(ZInvBatch batch, long nlines, T scale, const T* __restrict__ mulout,
+                                                 const C<T>* __restrict__ twg, int lpc) {
+    constexpr int N = 256;
+    __shared__ __align__(16) C<T> sbuf[8][32 * kZ256Pad];
+    const ZInvItem item = batch.it[blockIdx.y];
+    const C<T>* __restrict__ in = static_cast<const C<T>*>(item.in);
+    T* __restrict__ out = static_cast<T*>(item.out);
+    const int kin = item.kin;
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    C<T>* buf = sbuf[wid];
+    C<T> w1[8], w2[8];
+    z256_twiddles<T>(twg, lane, w1, w2);
+    const long npairs = (nlines + 1) / 2;
+    for (int q = wid; q < lpc; q += 8) {
+        const long p = (long)blockIdx.x * lpc + q;
+        if (p >= npairs) break;                          // uniform within the warp
+        const long l1 = 2 * p, l2 = 2 * p + 1;
+        const bool has2 = l2 < nlines;
+        const C<T>* in1 = in + l1 * kin;
+        const C<T>* in2 = in + l2 * kin;
+        C<T> v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int k = lane + 32 * j;
+            C<T> z = mk<T>(T(0), T(0));
+            if (k == 0 || 2 * k == N) {
+                if (k < kin) z = mk<T>(in1[k].x, has2 ? in2[k].x : T(0));
+            } else if (k < kin) {
+                const C<T> a = in1[k];
+                const C<T> b = has2 ? in2[k] : mk<T>(T(0), T(0));
+                z = mk<T>(a.x - b.y, a.y + b.x);
+            } else if (N - k < kin) {
+                const C<T> a = in1[N - k];
+                const C<T> b = has2 ? in2[N - k] : mk<T>(T(0), T(0));
+                z = mk<T>(a.x + b.y, b.x - a.y);
+            }
+            v[j] = z;
+        }
+        fft256_warp<T, +1>(v, buf, w1, w2, lane);
+        // real parts -> line l1, imaginary parts -> line l2, through shared memory for coalesced stores
+        T* re = reinterpret_cast<T*>(buf);
+        T* im = re + N;
+        const int m1 = lane & 7, c0 = lane >> 3;
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+            const int x0 = m1 + 8 * c0 + 64 * d, x1 = x0 + 32;
+            re[x0] = v[d].x * scale;
+            im[x0] = v[d].y * scale;
+            re[x1] = v[4 + d].x * scale;
+            im[x1] = v[4 + d].y * scale;
+        }
+        __syncwarp();
+        T* o1 = out + l1 * N;
+        T* o2 = out + l2 * N;
+#pragma unroll
+        for (int e = 0; e < N / 32; ++e) {
+            const int x = lane + 32 * e;
+            T a = re[x], b = im[x];
+            if (mulout) {
+                a *= mulout[l1 * N + x];
+                if (has2) b *= mulout[l2 * N + x];
+            }
+            o1[x] = a;
+            if (has2) o2[x] = b;
+        }
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
 // z-pass, inverse (C2R), length 288 = 12 x 24, register-resident: the same result as k_inv_z (packing of line pairs,
 // kz = 0 and n/2 treatment) as a two-stage Cooley-Tukey transform.  With k = t + 12 j and n = n1 + 24 n2,
 //   z[n1 + 24 n2] = sum_t w12^(t n2) [ w288^(t n1) sum_j Z[t + 12 j] w24^(j n1) ]      (w_m = e^{+2 pi i / m}),

@@ -532,7 +532,11 @@ int run_inverse_box(polybin_ctx* ctx, const C<T>* box, C<T>* v1, C<T>* v2, T* ou
         ZInvBatch b;
         b.it[0].in = v2; b.it[0].out = out; b.it[0].kin = Bz;
         const long nlines = (long)N0 * N1;
-        if (N2 == 512) {
+        if (N2 == 256) {
+            const int lpc = 16;
+            k_inv_z256<T><<<dim3((unsigned)(((nlines + 1) / 2 + lpc - 1) / lpc), 1, 1), 256, 0, ctx->stream>>>(
+                b, nlines, T(1.0 / (double)ctx->ncell), mulout, tw2, lpc);
+        } else if (N2 == 512) {
             const int lpc = 16;
             k_inv_z512<T><<<dim3((unsigned)(((nlines + 1) / 2 + lpc - 1) / lpc), 1, 1), 256, 0, ctx->stream>>>(
                 b, nlines, T(1.0 / (double)ctx->ncell), mulout, tw2, lpc);

@@ -24,15 +24,18 @@ static int n_fail = 0;
         }                                                       \
     } while (0)
 
-static void check(const char* name, long ncell, int ng, int nh, int hsep, std::vector<NeedPair> need, int n_out,
-                  int sing_g = 0) {
+// One layout with the given options: the default options must succeed; the autotuner's other candidates may be
+// rejected by the planner (e.g. more than four row groups) but must satisfy every check when accepted.
+static void check_one(const char* name, long ncell, int ng, int nh, int hsep, std::vector<NeedPair> need, int n_out,
+                      int sing_g, const PlanOpts& opts, bool must) {
     std::map<int, std::tuple<int, int, int>> want;   // output -> (j, k, single)
     for (const NeedPair& p : need)
         for (auto& so : p.outs) want[so.second] = std::make_tuple(p.j, p.k, so.first);
     Plan pl;   // layout only: its device pointers stay null
     std::vector<short2> rows;
     std::vector<int> gidx;
-    const char* msg = layout_plan(pl, ncell, 148, ng, nh, hsep, need, n_out, rows, gidx, sing_g);
+    const char* msg = layout_plan(pl, ncell, 148, ng, nh, hsep, need, n_out, rows, gidx, sing_g, opts);
+    if (msg && !must) return;
     REQUIRE(msg == nullptr, "layout_plan: %s", msg ? msg : "");
     const Params& P = pl.base;
     REQUIRE(pl.smem <= 227 * 1024, "shared memory %zu", pl.smem);
@@ -95,6 +98,20 @@ static void check(const char* name, long ncell, int ng, int nh, int hsep, std::v
         REQUIRE(jk.x < grows + (hsep ? (nh + 7) / 8 * 8 : 0) && jk.y < grows + (hsep ? (nh + 7) / 8 * 8 : 0),
                 "output %d: pair row beyond the slot", o);
     }
+}
+
+static void check(const char* name, long ncell, int ng, int nh, int hsep, std::vector<NeedPair> need, int n_out,
+                  int sing_g = 0) {
+    check_one(name, ncell, ng, nh, hsep, need, n_out, sing_g, PlanOpts{}, true);
+    for (int cost : {8, 24})
+        for (int cap : {kMaxTiles, 1})
+            for (int mode : {0, 1, 2}) {
+                PlanOpts o;
+                o.tile_cost = cost;
+                o.group_cap = cap;
+                o.cta_mode = mode;
+                check_one(name, ncell, ng, nh, hsep, need, n_out, sing_g, o, false);
+            }
 }
 
 // all pairs j <= k of ng maps against nh singles (the general contraction)

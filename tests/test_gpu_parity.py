@@ -52,6 +52,9 @@ CASES = [
     ((8, 4, 512), 2000.0, 1.0 + 40.0 * np.arange(8), "lognormal"),    # 512-point z lines up to the z Nyquist
     ((8, 6, 288), 2000.0, 1.0 + 20.0 * np.arange(8), "lognormal"),    # 288-point z lines (register-resident pass)
     ((8, 8, 512), 2000.0, 0.5 + 11.9375 * np.arange(9), "lognormal"), # m = 95: contraction grid 8 x 8 x 288
+    ((16, 8, 256), 2000.0, 1.0 + 6.0 * np.arange(8), "lognormal"),    # 256-point z lines (register-resident passes)
+    ((6, 10, 256), 1500.0, 1.0 + 4.0 * np.arange(7), "lognormal"),    # 256-point lines, radix-3 and radix-5 x, y
+    ((8, 8, 256), 2000.0, 0.5 + 11.25 * np.arange(9), "lognormal"),   # m = 90: shells on 256-point z lines
 ]
 
 
