@@ -8,6 +8,13 @@ Bispectrum criterion (tests/bk_criterion.py): e_norm <= 1e-6 for every triplet, 
 with kappa <= 10, and every triplet above 1e-6 listed with its kappa.
 * 256^3 masked workload (shell with holes, FKP weights, 24 P bins x ell 0,2,4, 16 B bins): the full P Fisher term
   of one draw, and a sampled block of the B Fisher term of one draw pair, within 1e-6 of sqrt(F_aa F_bb).
+* The same mask with the optimal weighting of the benchmark (fiducial = the field's power law on the binned shells,
+  n2 = n): in FP64 the ten conjugate-gradient iterations of the paper's optimal-weight test equal the oracle's ten
+  FP64 iterations within 1e-6 of max |S^-1 d| (measured 9e-8: ten steps of this recurrence amplify rounding by
+  ~1e8 -- the fiducial spans 5e6 down to the noise level 4e3).  In FP32 the same ten iterations differ from FP64
+  ones by ~1 % (a CPU emulation of the FP32 recurrence lands on the GPU's iterate to all printed digits), so the
+  FP32 path is checked on what is unique: iterated to ||r|| <= 1e-5 ||b||,
+  its solution solves the oracle's FP64 system to 3e-5, and the P numerator of that solution matches within 1e-5.
 The oracle computes only the maps these checks need (FP64, all host cores).
 """
 import numpy as np
@@ -151,3 +158,40 @@ def test_config5_fisher_terms(pkg):
     G = Fb[np.ix_(idx, idx)]
     dg = np.sqrt(np.abs(np.diag(Rb)))
     assert np.max(np.abs(G - Rb) / np.outer(dg, dg)) < 1e-6
+
+
+def test_config5_optimal_weighting_full_size(pkg):
+    from oracle import optimal
+    wl = synth.WORKLOADS[5]
+    grid, box = wl.grid, wl.box
+    n = synth.survey_mask(grid, (box,) * 3, 5000).astype(np.float32)
+    d = (n * synth.workload_field(5, 0)).astype(np.float32)
+    nn = n.astype(np.float64)
+    b = np.where(nn > 0, d.astype(np.float64) / np.where(nn > 0, nn, 1.0), 0.0)
+    kf = binning.kf_of(box)
+    nd, dd = torch.from_numpy(n).cuda(), torch.from_numpy(d).cuda()
+    # FP64: the same ten iterations as the oracle
+    pb = pkg.PolyBin(grid, box, wl.pk_edges, lmax=4, prec="fp64")
+    pfid = synth.power_law(kf * np.sqrt(np.arange(pb.max_shell() + 1, dtype=np.float64)))[None, :]
+    Pk = optimal.fiducial_grid(pfid, grid)
+    pb.set_optimal(nd, pfid, None, max_iter=10, tol=0.0)
+    x64, it, rel = pb.sinv_optimal(dd)
+    pb.close()
+    ref, it_ref, rel_ref = optimal.g_pcg(b, nn, nn, Pk, max_iter=10, tol=0.0)
+    assert it == it_ref == 10
+    err = np.max(np.abs(x64.cpu().numpy() - ref)) / np.max(np.abs(ref))
+    assert err < 1e-6, err
+    assert abs(rel - rel_ref) < 1e-4 * rel_ref   # the residual is 6e-3 of b: its relative error is ~1/rel larger
+    # FP32 (the benchmarked precision), iterated to ||r|| <= 1e-5 ||b||: the FP64 residual of its solution
+    pb = pkg.PolyBin(grid, box, wl.pk_edges, lmax=4, prec="fp32")
+    pb.set_optimal(nd, pfid, None, max_iter=200, tol=1e-5)
+    x32, it32, rel32 = pb.sinv_optimal(dd)
+    _, pnum = pb.pk_unwindowed_opt(dd, with_estimate=False)
+    pb.close()
+    xs = x32.cpu().numpy().astype(np.float64)
+    res = np.sqrt(np.sum((b - optimal.apply_a(xs, nn, nn, Pk)) ** 2) / np.sum(b * b))
+    assert rel32 <= 1e-5 and res < 3e-5, (it32, rel32, res)
+    nb = len(wl.pk_edges) - 1
+    bins = binning.bin_grid(grid, box, wl.pk_edges)
+    pref = optimal.pk_numerator_general(d, lambda v: xs, bins, binning.mu2_grid(grid), nb, [0, 2, 4]).ravel()
+    assert np.max(np.abs(pnum - pref)) < 1e-5 * np.max(np.abs(pref))

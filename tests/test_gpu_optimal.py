@@ -60,8 +60,9 @@ def _kaiser_table(ns, kf, nell=3, amp=2.0e4):
 # ------------------------------------------------------------------------------------------------ the solver
 
 
-def test_fixed_iterations_match_the_oracle_fp64(pkg):
-    grid, box = (16, 16, 16), 16.0
+@pytest.mark.parametrize("grid", [(16, 16, 16), (8, 8, 256)])   # 8 x 8 x 256: the 256-point C2R pass
+def test_fixed_iterations_match_the_oracle_fp64(pkg, grid):
+    box = 16.0
     kf = binning.kf_of(box)
     edges = kf * np.array([0.5, 2.5, 4.5, 6.5])
     n, n2 = _random_mask(grid, 1, 0.4)
