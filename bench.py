@@ -37,8 +37,8 @@ UNIT = "estimates/s"
 # workload's bins, field model and box on a 320^3 data grid, whose contraction grid (288^3) is the 512^3 workload's:
 # the contraction launch is the same (the same 30 maps of 288^3 cells).
 CAPTURED_TRAFFIC = {
-    ("26e64de9d9ac80a10c998e59800f90c7f9ff51f7483631f93ad3917397310211", "lognormal_kaiser512", "split"):
-        2866895616 + 3286016,
+    ("373cb97f2b0fe1b34501ac5024d188a48b5596215a4dff1f9db08c34f6f532d9", "lognormal_kaiser512", "split"):
+        2866815744 + 3194112,
 }
 
 
@@ -301,6 +301,8 @@ def other_workloads(pkg, synth, stream, dev) -> dict:
     tfp = _time(lambda: pbp.fisher_draws(nd, wd, 1, 0, 0, 1), 1)
     pbp.fisher(nd, wd, 2, 1, 0)
     tpu = _time(lambda: pbp.pk_unwindowed(dG, wd), 3)
+    tpb = _time(lambda: pbp.pk_bias(nd, wd, pkg.FISHER_PK, n_mc=1, seed=3), 3)   # n2 = n (unit weights)
+    pbp.pk_bias(None, None, pkg.FISHER_PK, n_mc=0)
     pbp.close()
     pbb = pkg.PolyBin(w.grid, w.box, w.bk_edges, prec="split", stream=stream.cuda_stream)
     nt = pbb.num_triplets()
@@ -308,9 +310,11 @@ def other_workloads(pkg, synth, stream, dev) -> dict:
     mocks = torch.stack([torch.from_numpy((n * synth.workload_field(5, 1 + i)).astype(np.float32)) for i in range(2)]).to(dev)
     pbb.fisher(nd, wd, 1, 1, 1)
     tbu = _time(lambda: pbb.bk_unwindowed(dG, wd, mocks), 1)
+    tbb = _time(lambda: pbb.bk_bias(nd, dG, dG, wd, n_mc=1, seed=3), 1)         # n3 = n, d2 = d (unit weights)
     pbb.close()
     out["masked256_split"] = {"pk_fisher_s_per_draw": tfp, "bk_fisher_s_per_draw_pair": tfb, "n_triplets": nt,
-                              "pk_unwindowed_s": tpu, "bk_unwindowed_s_with_2_mocks": tbu}
+                              "pk_unwindowed_s": tpu, "bk_unwindowed_s_with_2_mocks": tbu,
+                              "pk_shot_noise_s_per_draw": tpb, "bk_shot_noise_s_per_pair": tbb}
     out["masked256_optimal_fp32"] = optimal_workload(pkg, synth, stream, dev)
     return out
 
