@@ -119,7 +119,9 @@ int polybin_pk_discrete(polybin_ctx* ctx, const float* delta, int batch, double*
 int polybin_mode_counts(const polybin_ctx* ctx, double* counts);
 
 /* Both statistics of the same fields from one forward transform: bk_out as polybin_bk_ideal, pk_out as
- * polybin_pk (continuous normalisation).  Either output may be NULL to skip that statistic. */
+ * polybin_pk (continuous normalisation).  Either output may be NULL to skip that statistic.  With host memory and
+ * batch > 1 the fields are staged through two device buffers on a copy stream, the copy of field f + 1 overlapping
+ * the transforms of field f (pinned memory overlaps; pageable memory is copied synchronously by the driver). */
 int polybin_bk_pk_ideal(polybin_ctx* ctx, const float* delta, int batch, double* bk_out, double* pk_out);
 
 /* ---- masked ("unwindowed") estimators, global line of sight ------------------------------------------------

@@ -543,6 +543,65 @@ template int alloc_work<float>(polybin_ctx*, Work&);
 template int alloc_work<double>(polybin_ctx*, Work&);
 
 // Host or device input -> device pointer (host data copied into the context's staging buffer).
+// Batched input staging.  For host memory and more than one field, field f is copied on the context's copy stream
+// into buffer f % 2 while the context stream transforms field f - 1; the context stream waits for the copy, and the
+// next copy into a buffer waits until the forward transform that read it has run.  (Pageable memory works too, but
+// the driver then copies synchronously and nothing overlaps: pass pinned memory.)
+struct InputStager {
+    polybin_ctx* ctx;
+    const float* base;
+    int batch;
+    bool on = false;
+    int init() {
+        cudaPointerAttributes at;
+        cudaError_t e = cudaPointerGetAttributes(&at, base);
+        if (e != cudaSuccess) { cudaGetLastError(); at.type = cudaMemoryTypeUnregistered; }
+        on = batch > 1 && !ctx->capturing && at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged;
+        if (!on) return POLYBIN_OK;
+        const size_t n = (size_t)ctx->ncell;
+        if (n > ctx->stage_cap) {
+            for (int i = 0; i < 2; ++i) {
+                if (ctx->d_stage[i]) cudaFree(ctx->d_stage[i]);
+                ctx->d_stage[i] = nullptr;
+            }
+            ctx->stage_cap = 0;
+            for (int i = 0; i < 2; ++i) PB_CUDA_OK(cudaMalloc(&ctx->d_stage[i], sizeof(float) * n));
+            ctx->stage_cap = n;
+        }
+        if (!ctx->cstream) PB_CUDA_OK(cudaStreamCreateWithFlags(&ctx->cstream, cudaStreamNonBlocking));
+        for (int i = 0; i < 2; ++i) {
+            if (!ctx->ev_copied[i]) PB_CUDA_OK(cudaEventCreateWithFlags(&ctx->ev_copied[i], cudaEventDisableTiming));
+            if (!ctx->ev_used[i]) PB_CUDA_OK(cudaEventCreateWithFlags(&ctx->ev_used[i], cudaEventDisableTiming));
+        }
+        // the copy stream starts after the work already queued on the context stream
+        PB_CUDA_OK(cudaEventRecord(ctx->ev_used[0], ctx->stream));
+        PB_CUDA_OK(cudaEventRecord(ctx->ev_used[1], ctx->stream));
+        return copy(0);
+    }
+    int copy(int f) {
+        const int s = f & 1;
+        PB_CUDA_OK(cudaStreamWaitEvent(ctx->cstream, ctx->ev_used[s], 0));
+        PB_CUDA_OK(cudaMemcpyAsync(ctx->d_stage[s], base + (size_t)f * ctx->ncell, sizeof(float) * ctx->ncell,
+                                   cudaMemcpyHostToDevice, ctx->cstream));
+        PB_CUDA_OK(cudaEventRecord(ctx->ev_copied[s], ctx->cstream));
+        return POLYBIN_OK;
+    }
+    // the device pointer of field f (issuing the copy of field f + 1 first)
+    int get(int f, const float** out) {
+        if (!on) return resolve_input(ctx, base + (size_t)f * ctx->ncell, ctx->ncell, out);
+        int rc;
+        if (f + 1 < batch && (rc = copy(f + 1))) return rc;
+        PB_CUDA_OK(cudaStreamWaitEvent(ctx->stream, ctx->ev_copied[f & 1], 0));
+        *out = ctx->d_stage[f & 1];
+        return POLYBIN_OK;
+    }
+    // field f's buffer has been read (after its forward transform)
+    int done(int f) {
+        if (on) PB_CUDA_OK(cudaEventRecord(ctx->ev_used[f & 1], ctx->stream));
+        return POLYBIN_OK;
+    }
+};
+
 int resolve_input(polybin_ctx* ctx, const float* p, size_t count, const float** out) {
     cudaPointerAttributes at;
     cudaError_t e = cudaPointerGetAttributes(&at, p);
@@ -703,13 +762,19 @@ extern "C" int polybin_init(polybin_ctx** out, const int grid[3], const double b
 extern "C" void polybin_destroy(polybin_ctx* ctx) {
     if (!ctx) return;
     free_work(ctx->w);
+    if (ctx->cstream) cudaStreamSynchronize(ctx->cstream);
     void* ptrs[] = {ctx->d_lut, ctx->d_pairs, ctx->d_offs, ctx->d_coef, ctx->d_bin_start, ctx->d_pkpart, ctx->d_in,
-                    ctx->d_pkout, ctx->d_counts,
+                    ctx->d_stage[0], ctx->d_stage[1], ctx->d_pkout, ctx->d_counts,
                     ctx->d_tw_f[0], ctx->d_tw_f[1], ctx->d_tw_f[2], ctx->d_tw_d[0], ctx->d_tw_d[1], ctx->d_tw_d[2],
                     ctx->d_ctw[0], ctx->d_ctw[1], ctx->d_ctw[2], ctx->d_ctw[3], ctx->d_ctw[4], ctx->d_ctw[5]};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     destroy_extras(ctx);
+    for (int i = 0; i < 2; ++i) {
+        if (ctx->ev_copied[i]) cudaEventDestroy(ctx->ev_copied[i]);
+        if (ctx->ev_used[i]) cudaEventDestroy(ctx->ev_used[i]);
+    }
+    if (ctx->cstream) cudaStreamDestroy(ctx->cstream);
     if (ctx->tev[0]) {
         harvest_stage_times(ctx);
         for (cudaEvent_t ev : ctx->tev) cudaEventDestroy(ev);
@@ -747,11 +812,14 @@ static int bk_pk_t(polybin_ctx* ctx, const float* delta, int batch, double* bk_o
     int rc;
     const int nb = ctx->nb, nell = ctx->nell;
     const size_t nt = ctx->Nabc.size();
+    InputStager st{ctx, delta, batch};
+    if ((rc = st.init())) return rc;
     for (int f = 0; f < batch; ++f) {
         const float* in;
-        if ((rc = resolve_input(ctx, delta + (size_t)f * ctx->ncell, ctx->ncell, &in))) return rc;
+        if ((rc = st.get(f, &in))) return rc;
         Work& w = ctx->w;
         if ((rc = run_forward<T, float, float>(ctx, in, (const float*)nullptr, (const float*)nullptr, (C<T>*)w.t1, (C<T>*)w.t2, (C<T>*)w.box))) return rc;
+        if ((rc = st.done(f))) return rc;
         if (pk_out) {
             if ((rc = run_pkbin_dev<T>(ctx, (const C<T>*)w.box))) return rc;
             if ((rc = run_pk_normalise(ctx, ctx->d_pkout))) return rc;

@@ -172,6 +172,12 @@ struct polybin_ctx {
     pb::Work w;
     float* d_in = nullptr;
     size_t in_cap = 0;
+    // batched host input: two device buffers filled on a copy stream, the copy of field f + 1 overlapping the
+    // transforms of field f
+    float* d_stage[2] = {nullptr, nullptr};
+    size_t stage_cap = 0;
+    cudaStream_t cstream = nullptr;
+    cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr};
 
     // P_ell binning
     long nmodes = 0;
