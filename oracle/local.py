@@ -157,3 +157,35 @@ def pk_fisher_local(n, w, bins, nb, ells, xhat, khat, seed: int, n_mc: int, draw
     for r in range(n_mc):
         F = F + pk_fisher_draw_local(draw(n.shape, seed, r, stream, dtype), n, w, bins, nb, ells, xhat, khat)
     return F / n_mc
+
+
+def bk_ideal_multipoles_local(delta, box: float, edges, lmax: int, xhat, khat) -> dict:
+    """Ideal bispectrum multipoles with a local line of sight (Sec. 4.3.1, eq. g-ell-def and its spherical-harmonic
+    expansion; normalised as the global ones, Sec. 4.4.1):
+
+        g_{c,ell}[u] = IFT[Theta_c sum_m Ybar_lm(k) FT[Ybar_lm(x) u]],   S^ell_abc = sum_x g_a g_b g_{c,ell},
+        B_ell(a, b, c) = (2 ell + 1) (V^2 / N^3) S^ell_abc / T_abc,
+
+    the line of sight x / |x| from the observer at each cell (xhat), the conjugates of eq. g-ell-def dropped as for
+    the global line of sight (for real fields and even ell they reflect every map of a sum at once).  Returns the
+    triplets, B[ell index][triplet] and S."""
+    from .ideal import closed_triplets, forward, shell_maps, triple_sums, unit_maps
+    delta = np.asarray(delta, dtype=np.float64)
+    grid = delta.shape
+    ncell = int(np.prod(grid))
+    vol = float(box) ** 3
+    nb = len(edges) - 1
+    ells = list(range(0, lmax + 1, 2))
+    bins = binning.bin_grid(grid, box, edges)
+    G = shell_maps(forward(delta), bins, nb).reshape(nb, -1)
+    T = triple_sums(unit_maps(bins, nb))
+    trip = closed_triplets(T, ncell)
+    Tv = np.array([T[a, b, c] for a, b, c in trip])
+    H = _asym_spectra(delta, [e for e in ells if e > 0], xhat, khat)
+    S = np.zeros((len(ells), len(trip)))
+    for il, ell in enumerate(ells):
+        GL = G if ell == 0 else shell_maps(H[ell], bins, nb).reshape(nb, -1)
+        for t, (a, b, c) in enumerate(trip):
+            S[il, t] = np.dot(G[a] * G[b], GL[c])
+    B = np.array([(2 * ell + 1) * (vol * vol / float(ncell) ** 3) * S[il] / Tv for il, ell in enumerate(ells)])
+    return {"triplets": trip, "ells": ells, "S": S, "T": Tv, "B": B, "H": H}

@@ -102,3 +102,41 @@ def test_fisher_draw_equals_dense_matrix_product():
             want[i, j] = 0.5 * left @ (mats[be][1] @ av)
     scale = np.sqrt(np.abs(np.outer(np.diag(want), np.diag(want)))) + 1e-300
     assert np.max(np.abs(F - want) / scale) < 1e-10
+
+
+def test_bk_local_multipole_pins():
+    """Local-line-of-sight bispectrum multipoles (oracle local.bk_ideal_multipoles_local):
+    * the harmonic spectrum sum_m Ybar_lm(k) FT[Ybar_lm delta](k) equals the definition inside eq. g-ell-def,
+      sum_x e^{-ik.x} L_ell(k.x) delta(x) (explicit exponentials, no harmonics);
+    * S^ell_abc equals the brute-force sum over closed triangles of D(k1) D(k2) H_ell(k3) (C, no FFT shells);
+    * with the observer far away along z every cell sees the global line of sight: the global multipoles."""
+    from oracle import brute, ideal
+    grid, box = (8, 8, 8), 400.0
+    kf = binning.kf_of(box)
+    edges = kf * np.array([1.0, 2.0, 3.0, 4.0])
+    obs = (31.0, -17.0, 45.0)
+    f = synth.lognormal_field(grid, (box,) * 3, 21, kaiser_beta=0.5)
+    xhat = local.position_units(grid, box, obs)
+    khat = local.mode_units(grid)
+    res = local.bk_ideal_multipoles_local(f, box, edges, 4, xhat, khat)
+    xs = xhat.reshape(-1, 3)
+    fl = f.ravel()
+    pos = np.stack(np.meshgrid(*[np.arange(g) for g in grid], indexing="ij"), axis=-1).reshape(-1, 3)
+    fr = [binning.int_freqs(g) for g in grid]
+    for ell in (2, 4):
+        H = res["H"][ell]
+        for idx in [(1, 0, 0), (0, 2, 1), (3, 7, 2), (6, 1, 4), (2, 2, 2)]:
+            nv = np.array([fr[a][idx[a]] for a in range(3)], dtype=np.float64)
+            kh = nv / np.linalg.norm(nv)
+            mu = xs @ kh
+            want = np.sum(np.exp(-2j * np.pi * (pos @ (nv / np.array(grid)))) * binning.legendre(ell, mu * mu) * fl)
+            assert abs(H[idx] - want) <= 1e-11 * np.max(np.abs(fl)) * fl.size
+        D = ideal.forward(f)
+        _, sdd = brute.brute_bk(D, grid, kf, edges, D2=D, D3=H)
+        il = res["ells"].index(ell)
+        want = np.array([sdd[t] for t in res["triplets"]]) / f.size ** 2
+        assert np.max(np.abs(res["S"][il] - want)) <= 1e-10 * np.max(np.abs(want))
+    far = local.position_units(grid, box, (0.0, 0.0, -1.0e10))
+    loc = local.bk_ideal_multipoles_local(f, box, edges, 4, far, khat)["B"]
+    glob = ideal.bk_ideal_multipoles(f, box, edges, 4)["B"]
+    assert np.max(np.abs(loc - glob)) <= 1e-6 * np.max(np.abs(glob))
