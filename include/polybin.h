@@ -95,6 +95,14 @@ int polybin_bk_ideal(polybin_ctx* ctx, const float* delta, int batch, double* bk
  * set of contraction-grid maps (allocated on the first call with lmax_b > 0). */
 int polybin_bk_ideal_multipoles(polybin_ctx* ctx, const float* delta, int batch, int lmax_b, double* bk_out);
 
+/* The same multipoles with a local line of sight (Sec. 4.3.1, eq. g-ell-def and its expansion in normalised real
+ * spherical harmonics): g_{c,ell} = IFT[Theta_c sum_m Ybar_lm(k) FT[Ybar_lm(x) delta]], the direction x / |x| from
+ * the observer of polybin_set_observer at every cell (cell centres as for the local P estimator), 2 ell + 1 forward
+ * transforms per ell > 0 and field; normalised as polybin_bk_ideal_multipoles.  Same arguments and layout.  Not part
+ * of the paper's printed estimator set (its ideal estimator, eq. ideal-bk, takes a global line of sight); the local
+ * maps are those its unwindowed estimators use. */
+int polybin_bk_ideal_multipoles_local(polybin_ctx* ctx, const float* delta, int batch, int lmax_b, double* bk_out);
+
 /* Ideal bispectra of n_fields fields on possibly different grids (e.g. a batch of 96^3, 128^3 and 160^3
  * realisations).  ctxs[i] is the context of field i (fields on one grid share a context; all contexts must use
  * one stream, that of ctxs[0]); fields[i]: device float32 [N0][N1][N2] of ctxs[i]; bk_out[i]: host

@@ -66,6 +66,8 @@ _SIGS = {
     "polybin_bk_ideal_multipoles": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                                    ctypes.c_void_p]),
     "polybin_contraction_grid": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "polybin_bk_ideal_multipoles_local": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                                         ctypes.c_void_p]),
     "polybin_contract_plan_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)]),
     "polybin_max_shell": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
     "polybin_set_optimal": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -197,6 +199,15 @@ class PolyBin:
         out = np.zeros((batch, lmax_b // 2 + 1, self.num_triplets()), dtype=np.float64)
         self._check(self.lib.polybin_bk_ideal_multipoles(self.ctx, _ptr(delta), batch, int(lmax_b), _ptr(out)),
                     "polybin_bk_ideal_multipoles")
+        return out
+
+    def bk_multipoles_local(self, delta, lmax_b: int = 2) -> np.ndarray:
+        """B_ell with the local line of sight of set_observer: array [batch][lmax_b / 2 + 1][n_triplets]."""
+        delta = _f32(delta)
+        batch = delta.shape[0] if delta.ndim == 4 else 1
+        out = np.zeros((batch, lmax_b // 2 + 1, self.num_triplets()), dtype=np.float64)
+        self._check(self.lib.polybin_bk_ideal_multipoles_local(self.ctx, _ptr(delta), batch, int(lmax_b), _ptr(out)),
+                    "polybin_bk_ideal_multipoles_local")
         return out
 
     # ---- power spectrum

@@ -1341,6 +1341,62 @@ static int bk_unwindowed_t(polybin_ctx* ctx, const float* d, const float* w, con
     return POLYBIN_OK;
 }
 
+// Ideal bispectrum multipoles with a local line of sight (Sec. 4.3.1, eq. g-ell-def with its Ybar_lm expansion):
+// H_ell = sum_m Ybar_lm(k) FT[Ybar_lm(x) u] on the box (2 ell + 1 forward transforms of the harmonic-weighted field),
+// g_{c,ell} = IFT[Theta_c H_ell] on the contraction grid beside the ell = 0 maps g, S^ell = sum_x g_a g_b g_{c,ell}
+// and B_ell = (2 ell + 1)(V^2 / N^3) S^ell / T_abc on the device (the normalisation of the global multipoles).
+template <typename T>
+static int bk_multipoles_local_t(polybin_ctx* ctx, const float* delta, int batch, int lmax_b, double* bk_out) {
+    int rc;
+    if ((rc = ensure_triplets(ctx))) return rc;
+    if ((rc = uw_alloc<T>(ctx, false))) return rc;
+    if ((rc = uw_alloc_local<T>(ctx, false))) return rc;
+    UwState* u = static_cast<UwState*>(ctx->ext);
+    Work& w = ctx->w;
+    const size_t nt = ctx->Nabc.size();
+    const int nl = lmax_b / 2 + 1;
+    const long N = ctx->ncell, nbox = (long)ctx->gx.cnt * ctx->gy.cnt * ctx->gz.cnt;
+    if (lmax_b > 0 && !w.g2) PB_CUDA_OK(cudaMalloc(&w.g2, sizeof(T) * (size_t)ctx->nb * ctx->cg.ncell));
+    const uw::CellGeom<T> geom = cell_geom<T>(ctx);
+    C<T>* H = (C<T>*)u->hbox;
+    C<T>* tmp = (C<T>*)u->spec[2];
+    for (int f = 0; f < batch; ++f) {
+        const float* in;
+        if ((rc = resolve_input(ctx, delta + (size_t)f * N, N, &in))) return rc;
+        if ((rc = run_forward<T, float, float>(ctx, in, (const float*)nullptr, (const float*)nullptr, (C<T>*)w.t1,
+                                               (C<T>*)w.t2, (C<T>*)w.box)))
+            return rc;
+        if (nt == 0) continue;
+        if ((rc = run_shells<T>(ctx, (const C<T>*)w.box, (C<T>*)w.u1, (C<T>*)w.u2, (T*)w.g, 0, ctx->cg))) return rc;
+        for (int il = 0; il < nl; ++il) {
+            const int ell = 2 * il;
+            if (ell == 0) {
+                if ((rc = run_triplet_sums<T>(ctx, (const T*)w.g, ctx->d_S))) return rc;
+            } else {
+                for (int m = -ell; m <= ell; ++m) {
+                    uw::k_mul_ylm<T, float, float><<<grid1d(N), 256, 0, ctx->stream>>>(
+                        in, (const float*)nullptr, (const float*)nullptr, (T*)u->xmap, ell, m, geom);
+                    ctx->launches++;
+                    if ((rc = run_forward<T, T, float>(ctx, (const T*)u->xmap, (const float*)nullptr,
+                                                       (const float*)nullptr, (C<T>*)w.t1, (C<T>*)w.t2, tmp)))
+                        return rc;
+                    uw::k_ylm_box_accum<T><<<grid1d(nbox), 256, 0, ctx->stream>>>(tmp, H, ell, m, m == -ell ? 1 : 0,
+                                                                                  ctx->gx, ctx->gy, ctx->gz);
+                    ctx->launches++;
+                }
+                PB_CUDA_OK(cudaGetLastError());
+                if ((rc = run_shells<T>(ctx, H, (C<T>*)w.u1, (C<T>*)w.u2, (T*)w.g2, 0, ctx->cg))) return rc;
+                if ((rc = run_triplet_sums_ell<T>(ctx, (const T*)w.g, (const T*)w.g2, ctx->d_S))) return rc;
+            }
+            if ((rc = run_bk_normalise(ctx, ctx->d_S, ctx->d_B, 2.0 * ell + 1.0))) return rc;
+            PB_CUDA_OK(cudaMemcpyAsync(bk_out + ((size_t)f * nl + il) * nt, ctx->d_B, sizeof(double) * nt,
+                                       cudaMemcpyDeviceToHost, ctx->stream));
+        }
+        PB_CUDA_OK(cudaStreamSynchronize(ctx->stream));
+    }
+    return POLYBIN_OK;
+}
+
 template int run_inverse_box<float>(polybin_ctx*, const float2*, float2*, float2*, float*, const float*);
 template int run_inverse_box<double>(polybin_ctx*, const double2*, double2*, double2*, double*, const double*);
 
@@ -1574,6 +1630,14 @@ extern "C" int polybin_bk_unwindowed_shot(polybin_ctx* ctx, const float* d_dev, 
     return ctx->prec == POLYBIN_FP64
                ? bk_unwindowed_t<double>(ctx, d_dev, w_dev, mocks_dev, n_mocks, bk_out, bnum_out, nullptr, b.data())
                : bk_unwindowed_t<float>(ctx, d_dev, w_dev, mocks_dev, n_mocks, bk_out, bnum_out, nullptr, b.data());
+}
+
+extern "C" int polybin_bk_ideal_multipoles_local(polybin_ctx* ctx, const float* delta, int batch, int lmax_b,
+                                                 double* bk_out) {
+    if (!ctx || !delta || !bk_out || batch < 0 || lmax_b < 0 || lmax_b > 4 || lmax_b % 2)
+        return fail(ctx, POLYBIN_EINVAL, "polybin_bk_ideal_multipoles_local: bad argument (lmax_b in {0, 2, 4})");
+    return ctx->prec == POLYBIN_FP64 ? bk_multipoles_local_t<double>(ctx, delta, batch, lmax_b, bk_out)
+                                     : bk_multipoles_local_t<float>(ctx, delta, batch, lmax_b, bk_out);
 }
 
 extern "C" int polybin_solve(polybin_ctx* ctx, const double* A, int n, const double* B, int nrhs, double* X) {

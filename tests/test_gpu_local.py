@@ -1,6 +1,7 @@
 """GPU parity of the local (Yamamoto) line-of-sight power spectrum against the FP64 oracle (oracle/local.py), through
 the C-ABI: numerator (eq. pk-num-fft), one Monte Carlo Fisher term (eq. fish-from-Q with eq. Q-alpha-local), the
-end-to-end unwindowed estimate, and the observer bookkeeping.
+end-to-end unwindowed estimate, and the observer bookkeeping; and the ideal bispectrum multipoles with the local
+line of sight (eq. g-ell-def with its Ybar_lm expansion).
 
 Setup: the 32^3 masked box of the unwindowed tests (shell with holes, FKP weights), an observer off the box centre,
 P bins 0, 2, .., 10 k_F, ell = 0, 2, 4.  Tolerances as for the global line of sight: numerators within 1e-6 of the
@@ -13,6 +14,8 @@ torch = pytest.importorskip("torch")
 
 from oracle import binning, local, unwindowed
 from paper_2404_07249_gb300 import synth
+
+from bk_criterion import bk_errors, check, report
 
 pytestmark = pytest.mark.gpu
 
@@ -101,4 +104,40 @@ def test_local_unwindowed_end_to_end_and_observer(pkg, fields):
     pb.set_observer((0.0, 0.0, 0.0))
     with pytest.raises(pkg.PolybinError):
         pb.pk_unwindowed_local(_dev(d), _dev(w))
+    pb.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "split", "fp64"])
+def test_bk_multipoles_local(pkg, prec):
+    """Bispectrum multipoles ell = 0, 2, 4 with the local line of sight (eq. g-ell-def with Ybar_lm) against the oracle,
+    triplet by triplet with the criterion of tests/bk_criterion.py (kappa from sum_x |g_a g_b g_{c,ell}|); the
+    monopole equals the global one bit for bit."""
+    from oracle import ideal
+    grid, box = (48, 48, 48), 900.0
+    edges = binning.kf_of(box) * (0.5 + 2.0 * np.arange(7))
+    obs = (120.0, -310.0, 205.0)
+    f = synth.lognormal_field(grid, (box,) * 3, 77, kaiser_beta=0.5).astype(np.float32)
+    xhat = local.position_units(grid, box, obs)
+    khat = local.mode_units(grid)
+    ref = local.bk_ideal_multipoles_local(f, box, edges, 4, xhat, khat)
+    pb = pkg.PolyBin(grid, box, edges, prec=prec)
+    pb.set_observer(obs)
+    Bl = pb.bk_multipoles_local(_dev(f), 4)[0]
+    abc, _ = pb.triplets()
+    assert [tuple(t) for t in abc.tolist()] == ref["triplets"]
+    assert np.array_equal(Bl[0], pb.bk_ideal(_dev(f))[0])
+    tol = {"fp32": (1e-6, 1e-6, 10.0), "split": (1e-6, 1e-6, 10.0), "fp64": (1e-12, 1e-11, 1e3)}[prec]
+    nb = len(edges) - 1
+    bins = binning.bin_grid(grid, box, edges)
+    G = ideal.shell_maps(ideal.forward(f), bins, nb).reshape(nb, -1)
+    for il, ell in enumerate(ref["ells"]):
+        GL = G if ell == 0 else ideal.shell_maps(ref["H"][ell], bins, nb).reshape(nb, -1)
+        absS = np.array([np.dot(np.abs(G[a] * G[b]), np.abs(GL[c])) for a, b, c in ref["triplets"]])
+        e_rel, e_norm, kappa = bk_errors(Bl[il], ref["B"][il], ref["S"][il], absS)
+        s = check(ref["triplets"], e_rel, e_norm, kappa, norm_tol=tol[0], rel_tol=tol[1], kappa_max=tol[2],
+                  label=f"local {prec} ell {ell}")
+        print(report(s, f"local multipole ell={ell} {prec}"))
+    # the local quadrupole differs from the global one (the observer matters)
+    glob = pb.bk_multipoles(_dev(f), 4)[0]
+    assert np.max(np.abs(Bl[1] - glob[1])) > 1e-3 * np.max(np.abs(glob[1]))
     pb.close()
