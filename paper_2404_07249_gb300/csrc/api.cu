@@ -848,10 +848,13 @@ static int bk_multipoles_t(polybin_ctx* ctx, const float* delta, int batch, int 
     const int nl = lmax_b / 2 + 1;
     Work& w = ctx->w;
     if (lmax_b > 0 && !w.g2) PB_CUDA_OK(cudaMalloc(&w.g2, sizeof(T) * (size_t)ctx->nb * ctx->cg.ncell));
+    InputStager st{ctx, delta, batch};
+    if ((rc = st.init())) return rc;
     for (int f = 0; f < batch; ++f) {
         const float* in;
-        if ((rc = resolve_input(ctx, delta + (size_t)f * ctx->ncell, ctx->ncell, &in))) return rc;
+        if ((rc = st.get(f, &in))) return rc;
         if ((rc = run_forward<T, float, float>(ctx, in, (const float*)nullptr, (const float*)nullptr, (C<T>*)w.t1, (C<T>*)w.t2, (C<T>*)w.box))) return rc;
+        if ((rc = st.done(f))) return rc;
         if (nt == 0) continue;
         if ((rc = run_shells<T>(ctx, (const C<T>*)w.box, (C<T>*)w.u1, (C<T>*)w.u2, (T*)w.g, 0, ctx->cg))) return rc;
         for (int il = 0; il < nl; ++il) {
