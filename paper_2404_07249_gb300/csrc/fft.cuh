@@ -257,17 +257,45 @@ __global__ void __launch_bounds__(256) k_fwd_z(const TIN* __restrict__ in, const
     const int tid = threadIdx.x, nthr = blockDim.x;
     stage_twiddles<T>(tw, twg, n, tid, nthr);
     T* bs = reinterpret_cast<T*>(b0);
-    for (int idx = tid; idx < 2 * LP * n; idx += nthr) {
-        const int r = idx / n, e = idx - r * n;
-        const long gl = line0 + r;
-        T v = T(0);
-        if (gl < nlines) {
-            const long gi = gl * n + e;
-            v = T(in[gi]);
-            if (m1) v *= T(m1[gi]);
-            if (m2) v *= T(m2[gi]);
+    if constexpr (NT > 0) {
+        // compile-time trip count (256 threads): every load of the CTA's lines is issued before the first store, so
+        // the global latency is paid once rather than once per element
+        constexpr int IT = 2 * LT * NT / 256;
+        static_assert((2 * LT * NT) % 256 == 0, "z-pass tile must be a multiple of the CTA size");
+        T vals[IT];
+#pragma unroll
+        for (int q = 0; q < IT; ++q) {
+            const int idx = tid + 256 * q;
+            const int r = idx / NT, e = idx - r * NT;
+            const long gl = line0 + r;
+            T v = T(0);
+            if (gl < nlines) {
+                const long gi = gl * NT + e;
+                v = T(in[gi]);
+                if (m1) v *= T(m1[gi]);
+                if (m2) v *= T(m2[gi]);
+            }
+            vals[q] = v;
         }
-        bs[2 * ((r >> 1) + e * ES) + (r & 1)] = v;
+#pragma unroll
+        for (int q = 0; q < IT; ++q) {
+            const int idx = tid + 256 * q;
+            const int r = idx / NT, e = idx - r * NT;
+            bs[2 * ((r >> 1) + e * ES) + (r & 1)] = vals[q];
+        }
+    } else {
+        for (int idx = tid; idx < 2 * LP * n; idx += nthr) {
+            const int r = idx / n, e = idx - r * n;
+            const long gl = line0 + r;
+            T v = T(0);
+            if (gl < nlines) {
+                const long gi = gl * n + e;
+                v = T(in[gi]);
+                if (m1) v *= T(m1[gi]);
+                if (m2) v *= T(m2[gi]);
+            }
+            bs[2 * ((r >> 1) + e * ES) + (r & 1)] = v;
+        }
     }
     __syncthreads();
     C<T>* z = fft_any<T, -1, NT, LT, LT + 1>(b0, b1, LP, ES, plan, tw, tid, nthr);
@@ -711,9 +739,9 @@ static __global__ void __launch_bounds__(192, 3) k_inv_z288(ZInvBatch batch, lon
                                                            const float* __restrict__ mulout,
                                                            const float2* __restrict__ twg, int ppc) {
     constexpr int N = 288, TG = 12, P = 24, G = kZ288Pairs, RS = kZ288Rs, GS = kZ288Gs;
-    extern __shared__ __align__(16) float2 z288_smem[];
-    float2* stw = z288_smem;                          // e^{-2 pi i m / 288}
-    float2* sbuf = z288_smem + N;                     // exchange buffers
+    extern __shared__ __align__(16) float2 z288_dyn[];
+    float2* stw = z288_dyn;                           // e^{-2 pi i m / 288}
+    float2* sbuf = z288_dyn + N;                      // exchange buffers
     float2* stage = sbuf + G * GS;                    // the round's input lines, [2 G][kin]
     const ZInvItem item = batch.it[blockIdx.y];
     const float2* __restrict__ in = static_cast<const float2*>(item.in);
@@ -847,10 +875,44 @@ __global__ void __launch_bounds__(256) k_col(ColBatch batch, FftPlan plan, const
     C<T>* tw = b1 + (size_t)n * TK;
     const int tid = threadIdx.x, nthr = blockDim.x;
     stage_twiddles<T>(tw, twg, n, tid, nthr);
-    if (DIR < 0) {
+    if constexpr (DIR < 0 && NT > 0) {
+        // compile-time trip count (256 threads): all loads issued before the stores
+        constexpr int IT = (NT * TT + 255) / 256;
+        C<T> vals[IT];
+#pragma unroll
+        for (int q = 0; q < IT; ++q) {
+            const int idx = tid + 256 * q;
+            const int c = idx % TT, i = idx / TT;
+            vals[q] = (idx < NT * TT && c < nc) ? in[(long)i * item.in_es + c] : mk<T>(T(0), T(0));
+        }
+#pragma unroll
+        for (int q = 0; q < IT; ++q) {
+            const int idx = tid + 256 * q;
+            if (idx < NT * TT) b0[idx] = vals[q];
+        }
+    } else if constexpr (DIR < 0) {
         for (int idx = tid; idx < n * TK; idx += nthr) {
             const int c = idx % TK, i = idx / TK;
             b0[idx] = c < nc ? in[(long)i * item.in_es + c] : mk<T>(T(0), T(0));
+        }
+    } else if constexpr (NT > 0) {
+        // compile-time bound on the kept rows (<= n): the loads are issued before the zero fill and the stores
+        constexpr int IT = (NT * TT + 255) / 256;
+        const int nld = item.rng.cnt * TT;
+        C<T> vals[IT];
+#pragma unroll
+        for (int q = 0; q < IT; ++q) {
+            const int idx = tid + 256 * q;
+            const int c = idx % TT, i = idx / TT;
+            vals[q] = (idx < nld && c < nc) ? in[(long)i * item.in_es + c] : mk<T>(T(0), T(0));
+        }
+        for (int idx = tid; idx < NT * TT; idx += 256) b0[idx] = mk<T>(T(0), T(0));
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < IT; ++q) {
+            const int idx = tid + 256 * q;
+            const int c = idx % TT, i = idx / TT;
+            if (idx < nld && c < nc) b0[c + pos_of(item.rng.lo + i, NT) * TT] = vals[q];
         }
     } else {
         for (int idx = tid; idx < n * TK; idx += nthr) b0[idx] = mk<T>(T(0), T(0));
@@ -912,18 +974,17 @@ __global__ void __launch_bounds__(256) k_inv_x_filter(XInvBatch batch, const C<T
     C<T>* tw = b1 + (size_t)n * TK;
     const int tid = threadIdx.x, nthr = blockDim.x;
     stage_twiddles<T>(tw, twg, n, tid, nthr);
-    for (int idx = tid; idx < n * TK; idx += nthr) b0[idx] = mk<T>(T(0), T(0));
-    __syncthreads();
     const long gyz = (long)gy.cnt * gz.cnt;
-    for (int idx = tid; idx < item.rx.cnt * TK; idx += nthr) {
+    // the filtered value of element idx (column c, x index i) and its shared-memory slot (-1: outside the bin)
+    auto element = [&](int idx, C<T>& v) -> int {
         const int c = idx % TK, i = idx / TK;
-        if (c >= nc) continue;
+        if (c >= nc) return -1;
         const int cc = c0 + c;
         const int fy = item.ry.lo + cc / item.rz.cnt;
         const int fz = item.rz.lo + cc % item.rz.cnt;
         const int fx = item.rx.lo + i;
         const int s = fx * fx + fy * fy + fz * fz;
-        if (s > smax || lut[s] != item.bin) continue;
+        if (s > smax || lut[s] != item.bin) return -1;
         T wgt = scale;
         if (item.ell && item.m == kLegendreM) {
             const T mu2 = T(fz * fz) / T(s);
@@ -932,12 +993,42 @@ __global__ void __launch_bounds__(256) k_inv_x_filter(XInvBatch batch, const C<T
             const T inv = T(1) / sqrt(T(s));
             wgt *= ybar<T>(item.ell, item.m, T(fx) * inv, T(fy) * inv, T(fz) * inv);
         }
-        C<T> v = mk<T>(wgt, T(0));
+        v = mk<T>(wgt, T(0));
         if (spec) {
             const C<T> d = spec[(long)(fx - gx.lo) * gyz + (long)(fy - gy.lo) * gz.cnt + (fz - gz.lo)];
             v = mk<T>(d.x * wgt, d.y * wgt);
         }
-        b0[c + pos_of(fx, n) * TK] = v;
+        return c + pos_of(fx, n) * TK;
+    };
+    if constexpr (NT > 0) {
+        // compile-time bound on the loaded elements (rx.cnt <= n): the spectrum loads are issued before the zero
+        // fill and the stores
+        constexpr int IT = (NT * TT + 255) / 256;
+        static_assert(IT <= 32, "one validity bit an element");
+        const int nld = item.rx.cnt * TT;
+        C<T> vals[IT];
+        unsigned keep = 0u;                               // element q lies in the bin (its slot is recomputed below)
+#pragma unroll
+        for (int q = 0; q < IT; ++q) {
+            const int idx = tid + 256 * q;
+            if (idx < nld && element(idx, vals[q]) >= 0) keep |= 1u << q;
+        }
+        for (int idx = tid; idx < NT * TT; idx += 256) b0[idx] = mk<T>(T(0), T(0));
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < IT; ++q) {
+            if (!(keep >> q & 1u)) continue;
+            const int idx = tid + 256 * q;
+            b0[idx % TT + pos_of(item.rx.lo + idx / TT, NT) * TT] = vals[q];
+        }
+    } else {
+        for (int idx = tid; idx < n * TK; idx += nthr) b0[idx] = mk<T>(T(0), T(0));
+        __syncthreads();
+        for (int idx = tid; idx < item.rx.cnt * TK; idx += nthr) {
+            C<T> v;
+            const int d = element(idx, v);
+            if (d >= 0) b0[d] = v;
+        }
     }
     __syncthreads();
     C<T>* z = fft_any<T, +1, NT, TT, TT>(b0, b1, TK, TK, plan, tw, tid, nthr);
