@@ -413,6 +413,9 @@ struct UwState {
     // shot-noise bias of the P numerator per mode (POLYBIN_FISHER_PK, POLYBIN_FISHER_PK_OPT), subtracted by the
     // estimates while present
     std::vector<double> pbias[4];
+    // cross-bin partials of every alpha of one P Fisher draw (read back once a draw)
+    double* dpart_all = nullptr;
+    size_t dpart_all_cap = 0;
     // bispectrum shot noise: shell maps of X, Y, Z, X on the contraction grid [4][nb][cn], contraction partials and
     // output for 2 nb maps
     void* bmaps = nullptr;
@@ -425,7 +428,8 @@ static void uw_free(UwState* u) {
     if (!u) return;
     void* ptrs[] = {u->g2, u->xmap, u->a[0], u->a[1], u->spec[0], u->spec[1], u->spec[2], u->spec[3], u->pairs, u->qbox,
                     u->zc, u->yc, u->v1, u->v2, u->dF, u->dpart, u->dvec, u->dvec2, u->dinfo, u->dFp_inv, u->dFb_inv,
-                    u->ylc, u->hbox, u->g3, u->dFl_inv, u->dFo_inv, u->bmaps, u->bpart, u->bout};
+                    u->ylc, u->hbox, u->g3, u->dFl_inv, u->dFo_inv, u->bmaps, u->bpart, u->bout,
+                    u->dpart_all};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete u;
@@ -575,8 +579,23 @@ static int run_cross_bin(polybin_ctx* ctx, const C<T>* X, const C<T>* A, double*
 
 // ---------------------------------------------------------------------------------------------- P Fisher
 
+// The binned cross products of alpha's spectrum X with A into slot alpha of dpart_all (no read-back).
+template <typename T>
+static int launch_cross_bin(polybin_ctx* ctx, const C<T>* X, const C<T>* A, int alpha) {
+    UwState* u = static_cast<UwState*>(ctx->ext);
+    const int nb = ctx->nb, nell = ctx->nell;
+    const size_t per = (size_t)nb * ctx->pk_nseg * nell;
+    uw::k_cross_bin<T><<<dim3(nb, ctx->pk_nseg, 1), 256, 0, ctx->stream>>>(X, A, ctx->d_offs, ctx->d_coef, ctx->nmodes,
+                                                                            ctx->d_bin_start, nell, ctx->pk_seg_len,
+                                                                            u->dpart_all + (size_t)alpha * per);
+    ctx->launches++;
+    PB_CUDA_OK(cudaGetLastError());
+    return POLYBIN_OK;
+}
+
 // One Monte Carlo term of the P Fisher matrix (eq. fish-from-Q, global line of sight), host [na][na], na = nell*nb:
 // F[(l,b)][(l',b')] = 1/2 (1/N) sum_k conj(FT[s IFT[Theta_b L_l FT[s a]]]) Theta_b' L_l' FT[a],  s = w n.
+// The cross products of all alpha go to one device buffer read back once a draw.
 template <typename T>
 static int pk_fisher_draw(polybin_ctx* ctx, const float* n, const float* w, unsigned long long seed, int r,
                           std::vector<double>& F) {
@@ -593,7 +612,14 @@ static int pk_fisher_draw(polybin_ctx* ctx, const float* n, const float* w, unsi
     if ((rc = run_forward<T, T, float>(ctx, a, (const float*)nullptr, (const float*)nullptr, (C<T>*)W.t1, (C<T>*)W.t2, A))) return rc;
     if ((rc = run_forward<T, T, float>(ctx, a, w, n, (C<T>*)W.t1, (C<T>*)W.t2, SA))) return rc;
     F.assign((size_t)na * na, 0.0);
-    std::vector<double> cross;
+    const size_t per = (size_t)nb * ctx->pk_nseg * nell;
+    if (u->dpart_all_cap < (size_t)na * per) {
+        if (u->dpart_all) cudaFree(u->dpart_all);
+        u->dpart_all = nullptr;
+        u->dpart_all_cap = 0;
+        PB_CUDA_OK(cudaMalloc((void**)&u->dpart_all, sizeof(double) * (size_t)na * per));
+        u->dpart_all_cap = (size_t)na * per;
+    }
     T* q = (T*)u->g2;
     for (int il = 0; il < nell; ++il) {
         if ((rc = ensure_fine_inv<T>(ctx))) return rc;
@@ -601,11 +627,20 @@ static int pk_fisher_draw(polybin_ctx* ctx, const float* n, const float* w, unsi
         for (int b = 0; b < nb; ++b) {
             C<T>* X = (C<T>*)u->spec[2];
             if ((rc = run_forward<T, T, float>(ctx, q + (size_t)b * N, w, n, (C<T>*)W.t1, (C<T>*)W.t2, X))) return rc;
-            if ((rc = run_cross_bin<T>(ctx, X, A, u->dpart, cross))) return rc;
-            const int alpha = il * nb + b;
-            for (int jl = 0; jl < nell; ++jl)
-                for (int b2 = 0; b2 < nb; ++b2) F[(size_t)alpha * na + jl * nb + b2] = 0.5 * cross[(size_t)jl * nb + b2] / (double)N;
+            if ((rc = launch_cross_bin<T>(ctx, X, A, il * nb + b))) return rc;
         }
+    }
+    std::vector<double> part((size_t)na * per);
+    PB_CUDA_OK(cudaMemcpyAsync(part.data(), u->dpart_all, part.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    PB_CUDA_OK(cudaStreamSynchronize(ctx->stream));
+    for (int alpha = 0; alpha < na; ++alpha) {
+        const double* pa = part.data() + (size_t)alpha * per;
+        for (int b2 = 0; b2 < nb; ++b2)
+            for (int jl = 0; jl < nell; ++jl) {
+                double acc = 0.0;
+                for (int sg = 0; sg < ctx->pk_nseg; ++sg) acc += pa[((size_t)b2 * ctx->pk_nseg + sg) * nell + jl];
+                F[(size_t)alpha * na + jl * nb + b2] = 0.5 * acc / (double)N;
+            }
     }
     return POLYBIN_OK;
 }
