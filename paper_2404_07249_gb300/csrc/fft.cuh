@@ -260,8 +260,8 @@ __global__ void __launch_bounds__(256) k_fwd_z(const TIN* __restrict__ in, const
     if constexpr (NT > 0) {
         // compile-time trip count (256 threads): every load of the CTA's lines is issued before the first store, so
         // the global latency is paid once rather than once per element
-        constexpr int IT = 2 * LT * NT / 256;
-        static_assert((2 * LT * NT) % 256 == 0, "z-pass tile must be a multiple of the CTA size");
+        constexpr int TOT = 2 * LT * NT;
+        constexpr int IT = (TOT + 255) / 256;
         T vals[IT];
 #pragma unroll
         for (int q = 0; q < IT; ++q) {
@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(256) k_fwd_z(const TIN* __restrict__ in, const
             const int r = idx / NT, e = idx - r * NT;
             const long gl = line0 + r;
             T v = T(0);
-            if (gl < nlines) {
+            if (idx < TOT && gl < nlines) {
                 const long gi = gl * NT + e;
                 v = T(in[gi]);
                 if (m1) v *= T(m1[gi]);
@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(256) k_fwd_z(const TIN* __restrict__ in, const
         for (int q = 0; q < IT; ++q) {
             const int idx = tid + 256 * q;
             const int r = idx / NT, e = idx - r * NT;
-            bs[2 * ((r >> 1) + e * ES) + (r & 1)] = vals[q];
+            if (idx < TOT) bs[2 * ((r >> 1) + e * ES) + (r & 1)] = vals[q];
         }
     } else {
         for (int idx = tid; idx < 2 * LP * n; idx += nthr) {
@@ -1046,6 +1046,7 @@ namespace pb {
 #define PB_WITH_NT(n, NTV, ...)                              \
     switch (n) {                                             \
         case 64: { constexpr int NTV = 64; __VA_ARGS__ } break;   \
+        case 100: { constexpr int NTV = 100; __VA_ARGS__ } break; \
         case 128: { constexpr int NTV = 128; __VA_ARGS__ } break; \
         case 256: { constexpr int NTV = 256; __VA_ARGS__ } break; \
         case 512: { constexpr int NTV = 512; __VA_ARGS__ } break; \
@@ -1053,12 +1054,14 @@ namespace pb {
         default: { constexpr int NTV = 0; __VA_ARGS__ } break;    \
     }
 // The inverse passes also run on the contraction grids (lengths 3m + 1 and up rounded to a 2-3-5 length):
-// compile-time versions of the common ones.
+// compile-time versions of the common ones (100: the masked 256^3 workload's bispectrum grid, whose B Fisher also
+// takes forward transforms there).
 #define PB_WITH_NT_INV(n, NTV, ...)                          \
     switch (n) {                                             \
         case 64: { constexpr int NTV = 64; __VA_ARGS__ } break;   \
         case 80: { constexpr int NTV = 80; __VA_ARGS__ } break;   \
         case 96: { constexpr int NTV = 96; __VA_ARGS__ } break;   \
+        case 100: { constexpr int NTV = 100; __VA_ARGS__ } break; \
         case 128: { constexpr int NTV = 128; __VA_ARGS__ } break; \
         case 160: { constexpr int NTV = 160; __VA_ARGS__ } break; \
         case 192: { constexpr int NTV = 192; __VA_ARGS__ } break; \

@@ -55,6 +55,8 @@ CASES = [
     ((16, 8, 256), 2000.0, 1.0 + 6.0 * np.arange(8), "lognormal"),    # 256-point z lines (register-resident passes)
     ((6, 10, 256), 1500.0, 1.0 + 4.0 * np.arange(7), "lognormal"),    # 256-point lines, radix-3 and radix-5 x, y
     ((8, 8, 256), 2000.0, 0.5 + 11.25 * np.arange(9), "lognormal"),   # m = 90: shells on 256-point z lines
+    ((20, 10, 100), 1500.0, 1.0 + 2.0 * np.arange(8), "lognormal"),   # compile-time 100-point passes (z)
+    ((100, 100, 20), 1500.0, 1.0 + 2.0 * np.arange(8), "lognormal"),  # compile-time 100-point column passes
 ]
 
 
