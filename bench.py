@@ -318,6 +318,51 @@ def other_workloads(pkg, synth, stream, dev) -> dict:
                               "pk_unwindowed_s": tpu, "bk_unwindowed_s_with_2_mocks": tbu,
                               "pk_shot_noise_s_per_draw": tpb, "bk_shot_noise_s_per_pair": tbb}
     out["masked256_optimal_fp32"] = optimal_workload(pkg, synth, stream, dev)
+    out["masked256_local_split"] = local_workload(pkg, synth, stream, dev)
+    return out
+
+
+def noise_workload(pkg, synth, stream, dev) -> dict:
+    """Shot-noise bias terms on the masked 256^3 workload (unit weights: n2 = n3 = n, d2 = d): one Monte Carlo map for
+    P, one pair for B."""
+    import torch
+    w = synth.WORKLOADS[5]
+    n = synth.survey_mask(w.grid, (w.box,) * 3, 5000).astype(np.float32)
+    nd = torch.from_numpy(n).to(dev)
+    d = torch.from_numpy((n * synth.workload_field(5, 0)).astype(np.float32)).to(dev)
+    out = {}
+    pb = pkg.PolyBin(w.grid, w.box, w.pk_edges, lmax=4, prec="split", stream=stream.cuda_stream)
+    wd = pb.fkp_weights(nd, w.extra["P0"])
+    out["pk_bias_s_per_draw"] = _time(lambda: pb.pk_bias(nd, wd, pkg.FISHER_PK, n_mc=1, seed=3), 3)
+    pb.close()
+    pbb = pkg.PolyBin(w.grid, w.box, w.bk_edges, prec="split", stream=stream.cuda_stream)
+    pbb.num_triplets()
+    out["bk_bias_s_per_pair"] = _time(lambda: pbb.bk_bias(nd, d, d, wd, n_mc=1, seed=3), 1)
+    pbb.close()
+    return out
+
+
+def local_workload(pkg, synth, stream, dev) -> dict:
+    """Local (Yamamoto) line of sight on the masked 256^3 workload, observer at the box centre (the survey geometry's
+    own): the P numerator, one P Fisher draw, and the ideal bispectrum multipoles ell = 0, 2 of one field."""
+    import torch
+    w = synth.WORKLOADS[5]
+    n = synth.survey_mask(w.grid, (w.box,) * 3, 5000).astype(np.float32)
+    nd = torch.from_numpy(n).to(dev)
+    d = torch.from_numpy((n * synth.workload_field(5, 0)).astype(np.float32)).to(dev)
+    out = {}
+    pb = pkg.PolyBin(w.grid, w.box, w.pk_edges, lmax=4, prec="split", stream=stream.cuda_stream)
+    pb.set_observer((0.0, 0.0, 0.0))
+    wd = pb.fkp_weights(nd, w.extra["P0"])
+    out["pk_numerator_s"] = _time(lambda: pb.pk_unwindowed_local(d, wd, with_estimate=False), 3)
+    out["pk_fisher_s_per_draw"] = _time(lambda: pb.fisher_draws(nd, wd, 1, pkg.FISHER_PK_LOCAL, 0, 1), 1)
+    pb.close()
+    pbb = pkg.PolyBin(w.grid, w.box, w.bk_edges, prec="split", stream=stream.cuda_stream)
+    pbb.set_observer((0.0, 0.0, 0.0))
+    pbb.num_triplets()
+    out["bk_multipoles_l2_s"] = _time(lambda: pbb.bk_multipoles_local(d, 2), 3)
+    out["bk_multipoles_l2_global_s"] = _time(lambda: pbb.bk_multipoles(d, 2), 3)
+    pbb.close()
     return out
 
 
@@ -366,6 +411,8 @@ def main():
                     help="profiling only: run the workload's field model, box and bins on another grid")
     ap.add_argument("--optimal-only", action="store_true",
                     help="profiling only: time the optimal-weighting solves on the masked 256^3 workload and exit")
+    ap.add_argument("--only", choices=["local", "noise"], default=None,
+                    help="profiling only: time the local line-of-sight or the shot-noise workload (masked 256^3) and exit")
     ap.add_argument("--no-other-workloads", action="store_true",
                     help="skip the other workloads (64^3 FP64, 256^3, batched uneven grids, masked 256^3)")
     args = ap.parse_args()
@@ -395,6 +442,12 @@ def main():
         out = optimal_workload(pkg, synth, torch.cuda.current_stream(dev), dev, fisher=False)
         if rank == 0:
             print(json.dumps({"workload": "masked256_optimal_fp32", **out}), flush=True)
+        return
+    if args.only:
+        fn = local_workload if args.only == "local" else noise_workload
+        out = fn(pkg, synth, torch.cuda.current_stream(dev), dev)
+        if rank == 0:
+            print(json.dumps({"workload": f"masked256_{args.only}", **out}), flush=True)
         return
 
     w, edges = _workload(args.config)
