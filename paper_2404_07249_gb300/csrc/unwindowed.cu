@@ -266,8 +266,10 @@ __global__ void k_mul_ylm(const TIN* __restrict__ in, const TM* __restrict__ m1,
                           T* __restrict__ out, int ell, int m, CellGeom<T> cg) {
     const long n = (long)cg.N[0] * cg.N[1] * cg.N[2];
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-        const long k = i % cg.N[2], r = i / cg.N[2];
-        const long j = r % cg.N[1], a = r / cg.N[1];
+        // 32-bit unsigned index arithmetic (N < 2^31): 64-bit division per cell dominated these kernels
+        const unsigned ui = (unsigned)i, n2 = (unsigned)cg.N[2], n1 = (unsigned)cg.N[1];
+        const unsigned r = ui / n2, k = ui - r * n2;
+        const unsigned a = r / n1, j = r - a * n1;
         T x, y, z;
         cell_direction<T>(a, j, k, cg.h, cg.half_l, cg.obs, x, y, z);
         T v = ybar<T>(ell, m, x, y, z) * T(in[i]);
@@ -282,8 +284,10 @@ template <typename T>
 __global__ void k_ylm_axpy(T* __restrict__ Q, const T* __restrict__ q, int nb, int ell, int m, T fac, CellGeom<T> cg) {
     const long n = (long)cg.N[0] * cg.N[1] * cg.N[2];
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-        const long k = i % cg.N[2], r = i / cg.N[2];
-        const long j = r % cg.N[1], a = r / cg.N[1];
+        // 32-bit unsigned index arithmetic (N < 2^31): 64-bit division per cell dominated these kernels
+        const unsigned ui = (unsigned)i, n2 = (unsigned)cg.N[2], n1 = (unsigned)cg.N[1];
+        const unsigned r = ui / n2, k = ui - r * n2;
+        const unsigned a = r / n1, j = r - a * n1;
         T x, y, z;
         cell_direction<T>(a, j, k, cg.h, cg.half_l, cg.obs, x, y, z);
         const T yv = fac * ybar<T>(ell, m, x, y, z);
