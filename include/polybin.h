@@ -331,9 +331,11 @@ int polybin_last_path(const polybin_ctx* ctx, int* path);
  * polybin_contract stay on the data grid. */
 int polybin_contraction_grid(const polybin_ctx* ctx, int dims[3]);
 
-/* Failure-detection self-test: a kernel waits on an mbarrier phase that nothing completes, using the same bounded
- * poll as the tensor-core pipeline; the wait gives up after 2^14 polls and sets the device error flag, the kernel
- * returns and the context stays usable.  *timed_out = 1 when the bounded wait gave up (the expected outcome). */
+/* Failure-detection self-test: one kernel waits on an mbarrier phase that nothing completes, using the same bounded
+ * poll as the tensor-core pipeline, and another on a barrier armed for a bulk staging copy that is never issued,
+ * using the bounded wait of the transform passes' staging; each wait gives up after 2^14 polls and sets its device
+ * error flag, the kernels return and the context stays usable (the flags are cleared afterwards).
+ * *timed_out = 1 when both bounded waits gave up (the expected outcome). */
 int polybin_selftest_wait(polybin_ctx* ctx, int* timed_out);
 
 /* ---- individual steps, for testing and composition (device pointers only) --------------------------------- */

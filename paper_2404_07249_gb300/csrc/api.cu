@@ -223,8 +223,10 @@ int run_shells_m(polybin_ctx* ctx, const C<T>* box, C<T>* u1, C<T>* u2, T* g, in
             dim3 grid256((unsigned)(((nlines + 1) / 2 + lpc - 1) / lpc), nb, 1);
             k_inv_z256<T><<<grid256, 256, 0, ctx->stream>>>(b, nlines, T(1), (const T*)nullptr, tw(2), lpc);
         } else if (N2 == 288 && sizeof(T) == 4) {
-            // register-resident 288-point transform, 128 line pairs per CTA (8 rounds of 16, input staged with
-            // cp.async one round ahead)
+            // register-resident 288-point transform, 128 line pairs per CTA (8 rounds of 16, each round's input
+            // staged one round ahead by one bulk copy of the TMA engine; a copy that never lands raises the
+            // staging error flag, reported at the next read of the flags)
+            if ((rc = ensure_err_flag(ctx))) return rc;
             const int ppc = 128;
             int kin_max = 1;
             for (int i = 0; i < nb; ++i) kin_max = std::max(kin_max, b.it[i].kin);
@@ -232,7 +234,8 @@ int run_shells_m(polybin_ctx* ctx, const C<T>* box, C<T>* u1, C<T>* u2, T* g, in
             dim3 grid288((unsigned)(((nlines + 1) / 2 + ppc - 1) / ppc), nb, 1);
             if ((rc = set_smem<T>(ctx, (const void*)k_inv_z288, smz))) return rc;
             k_inv_z288<<<grid288, kZ288Threads, smz, ctx->stream>>>(b, nlines, 1.f, (const float*)nullptr,
-                                                                    (const float2*)tw(2), ppc);
+                                                                    (const float2*)tw(2), ppc,
+                                                                    ctx->d_err + kErrStaging);
         } else {
             dim3 grid((unsigned)((nlines + 2 * LP - 1) / (2 * LP)), nb, 1);
             PB_WITH_NT_INV(N2, NT, {
@@ -243,6 +246,12 @@ int run_shells_m(polybin_ctx* ctx, const C<T>* box, C<T>* u1, C<T>* u2, T* g, in
         if ((rc = launch_check(ctx, "k_inv_z"))) return rc;
     }
     return POLYBIN_OK;
+}
+
+// Launches the staging-wait self-test into the staging error flag (the caller clears and reads it).
+int run_bulk_wait_selftest(polybin_ctx* ctx, unsigned limit) {
+    k_bulk_wait_selftest<<<1, 32, 0, ctx->stream>>>(ctx->d_err + kErrStaging, limit);
+    return launch_check(ctx, "k_bulk_wait_selftest");
 }
 
 ContractGeom contract_geom(int nb, int nh, long ncell) {

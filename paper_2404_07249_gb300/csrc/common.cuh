@@ -14,6 +14,20 @@ template <typename T> __host__ __device__ __forceinline__ C<T> mk(T x, T y) { C<
 template <typename T> __device__ __forceinline__ C<T> add(C<T> a, C<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
 template <typename T> __device__ __forceinline__ C<T> sub(C<T> a, C<T> b) { return mk<T>(a.x - b.x, a.y - b.y); }
 template <typename T> __device__ __forceinline__ C<T> scl(C<T> a, T s) { return mk<T>(a.x * s, a.y * s); }
+// FP32 complex sums as one packed f32x2 instruction (two round-to-nearest adds, the same values as two scalar
+// adds): the butterflies of the FFT passes are mostly such sums, and the passes are bound by instruction issue.
+__device__ __forceinline__ uint64_t f32x2_bits(float2 a) { return *reinterpret_cast<const uint64_t*>(&a); }
+__device__ __forceinline__ float2 f32x2_val(uint64_t r) { return *reinterpret_cast<const float2*>(&r); }
+template <> __device__ __forceinline__ float2 add<float>(float2 a, float2 b) {
+    uint64_t r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f32x2_bits(a)), "l"(f32x2_bits(b)));
+    return f32x2_val(r);
+}
+template <> __device__ __forceinline__ float2 sub<float>(float2 a, float2 b) {
+    uint64_t r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f32x2_bits(a)), "l"(f32x2_bits(b)));
+    return f32x2_val(r);
+}
 template <typename T> __device__ __forceinline__ C<T> mul(C<T> a, C<T> b) {
     return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }

@@ -1326,13 +1326,8 @@ static int launch(polybin_ctx* ctx, Plan& pl, const float* g, const float* h, do
         e = cudaGetLastError();
         if (e != cudaSuccess) return fail_cuda(ctx, e, "k_reduce_gather", __FILE__, __LINE__);
     }
-    if (ctx->capturing) return POLYBIN_OK;   // the caller reads the error flag after the graph has run
-    int herr = 0;
-    e = cudaMemcpyAsync(&herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-    if (e != cudaSuccess) return fail_cuda(ctx, e, "contract_tc error flag", __FILE__, __LINE__);
-    if (herr) return fail(ctx, POLYBIN_ETIMEOUT, "contract_tc: a pipeline wait timed out");
-    return POLYBIN_OK;
+    if (ctx->capturing) return POLYBIN_OK;   // the caller reads the error flags after the graph has run
+    return read_err_flags(ctx, "contract_tc");
 }
 
 static PlanCache* cache_of(polybin_ctx* ctx) {
@@ -1551,10 +1546,26 @@ void destroy_tc(polybin_ctx* ctx) {
 
 int ensure_err_flag(polybin_ctx* ctx) {
     if (ctx->d_err) return POLYBIN_OK;
-    cudaError_t e = cudaMalloc(&ctx->d_err, sizeof(int));
+    cudaError_t e = cudaMalloc(&ctx->d_err, kErrFlags * sizeof(int));
     if (e != cudaSuccess) return fail_cuda(ctx, e, "cudaMalloc err flag", __FILE__, __LINE__);
-    e = cudaMemset(ctx->d_err, 0, sizeof(int));
+    e = cudaMemset(ctx->d_err, 0, kErrFlags * sizeof(int));
     if (e != cudaSuccess) return fail_cuda(ctx, e, "cudaMemset err flag", __FILE__, __LINE__);
+    return POLYBIN_OK;
+}
+
+// Reads both error flags after the work queued on the stream (synchronising it).  The staging flag is raised by the
+// transform passes that run before the contraction on the same stream and is cleared once reported.
+int read_err_flags(polybin_ctx* ctx, const char* what) {
+    int herr[kErrFlags] = {0, 0};
+    cudaError_t e = cudaMemcpyAsync(herr, ctx->d_err, sizeof(herr), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return fail_cuda(ctx, e, "error flags", __FILE__, __LINE__);
+    if (herr[kErrStaging]) {
+        e = cudaMemset(ctx->d_err + kErrStaging, 0, sizeof(int));
+        if (e != cudaSuccess) return fail_cuda(ctx, e, "cudaMemset err flag", __FILE__, __LINE__);
+        return fail(ctx, POLYBIN_ETIMEOUT, "%s: a bulk staging copy of a transform pass did not complete", what);
+    }
+    if (herr[kErrPipeline]) return fail(ctx, POLYBIN_ETIMEOUT, "%s: a pipeline wait timed out", what);
     return POLYBIN_OK;
 }
 
@@ -1638,11 +1649,7 @@ int run_gram_tc(polybin_ctx* ctx, const float* A, int nA, const float* B, int nB
                                                                           scale, d_out);
     ctx->launches += 1;
     PB_CUDA_OK(cudaGetLastError());
-    int herr = 0;
-    PB_CUDA_OK(cudaMemcpyAsync(&herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-    PB_CUDA_OK(cudaStreamSynchronize(ctx->stream));
-    if (herr) return fail(ctx, POLYBIN_ETIMEOUT, "gram: a pipeline wait timed out");
-    return POLYBIN_OK;
+    return read_err_flags(ctx, "gram");
 }
 
 // S'_abc of every closed triplet (device, triplet order) from the shell maps g on the contraction grid.
@@ -1659,12 +1666,16 @@ extern "C" int polybin_selftest_wait(polybin_ctx* ctx, int* timed_out) {
     if (!ctx || !timed_out) return pb::fail(ctx, POLYBIN_EINVAL, "polybin_selftest_wait: NULL argument");
     int rc = pb::ensure_err_flag(ctx);
     if (rc) return rc;
-    PB_CUDA_OK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
-    pb::tc::k_wait_selftest<<<1, 32, 0, ctx->stream>>>(ctx->d_err, 1u << 14);
+    PB_CUDA_OK(cudaMemsetAsync(ctx->d_err, 0, pb::kErrFlags * sizeof(int), ctx->stream));
+    pb::tc::k_wait_selftest<<<1, 32, 0, ctx->stream>>>(ctx->d_err + pb::kErrPipeline, 1u << 14);
     ctx->launches++;
     PB_CUDA_OK(cudaGetLastError());
-    PB_CUDA_OK(cudaMemcpyAsync(timed_out, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    if ((rc = pb::run_bulk_wait_selftest(ctx, 1u << 14))) return rc;
+    int h[pb::kErrFlags] = {0, 0};
+    PB_CUDA_OK(cudaMemcpyAsync(h, ctx->d_err, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
     PB_CUDA_OK(cudaStreamSynchronize(ctx->stream));
+    PB_CUDA_OK(cudaMemsetAsync(ctx->d_err, 0, pb::kErrFlags * sizeof(int), ctx->stream));
+    *timed_out = (h[pb::kErrPipeline] && h[pb::kErrStaging]) ? 1 : 0;
     return POLYBIN_OK;
 }
 

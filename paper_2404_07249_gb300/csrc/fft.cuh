@@ -726,23 +726,66 @@ __device__ __forceinline__ void stage_block(unsigned char* dst, const unsigned c
     cp_async_commit();
 }
 
+// One-shot bulk copy global -> shared through the TMA engine (cp.async.bulk: both addresses 16-byte aligned, size a
+// multiple of 16), completing on an mbarrier with the byte count; and the bounded wait on that barrier.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void bulk_bar_init(uint64_t* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n\tfence.mbarrier_init.release.cluster;" ::"r"(smem_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "fence.proxy.async.shared::cta;\n\t"
+        "mbarrier.arrive.expect_tx.shared::cta.b64 _, [%2], %3;\n\t"
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %3, [%2];" ::"r"(smem_addr(dst)),
+        "l"(src), "r"(smem_addr(bar)), "r"(bytes)
+        : "memory");
+}
+// Waits for phase `parity` of the barrier; false after `limit` polls (the copy never landed).
+__device__ __forceinline__ bool bulk_wait(uint64_t* bar, uint32_t parity, unsigned limit) {
+    for (unsigned it = 0; it < limit; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(smem_addr(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+constexpr unsigned kBulkSpinLimit = 1u << 22;
+// Self-test of the staging wait: a barrier armed for 16 bytes that no copy delivers (none is issued); the bounded
+// wait gives up and raises the flag.
+static __global__ void k_bulk_wait_selftest(int* err, unsigned limit) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        bulk_bar_init(&bar);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], 16;" ::"r"(smem_addr(&bar)) : "memory");
+        if (!bulk_wait(&bar, 0u, limit)) atomicExch(err, 1);
+    }
+}
+
 constexpr int kZ288Threads = 192, kZ288Pairs = 16, kZ288Kmax = 145;
 // exchange buffer of a group: 24 rows of 13 (row stride 13: the 12 threads of a group read 12 rows conflict-free),
 // groups 316 float2 apart (316 = 12 mod 16: the two groups of a half-warp cover the 32 banks exactly)
 constexpr int kZ288Rs = 13, kZ288Gs = 316;
-// dynamic shared memory: twiddle table [288] float2, exchange buffers [16][316] float2, input stage [32 lines][kin]
+// dynamic shared memory: twiddle table [288] float2, exchange buffers [16][316] float2, the staging barrier (16
+// bytes), input stage [32 lines][kin] (16-byte aligned: (288 + 16 x 316) x 8 + 16 = 42768 bytes in)
 inline size_t z288_smem(int kin_max) {
-    return (size_t)(288 + kZ288Pairs * kZ288Gs + 2 * kZ288Pairs * kin_max) * sizeof(float2);
+    return (size_t)(288 + kZ288Pairs * kZ288Gs + 2 + 2 * kZ288Pairs * kin_max) * sizeof(float2);
 }
 
 static __global__ void __launch_bounds__(192, 3) k_inv_z288(ZInvBatch batch, long nlines, float scale,
                                                            const float* __restrict__ mulout,
-                                                           const float2* __restrict__ twg, int ppc) {
+                                                           const float2* __restrict__ twg, int ppc, int* err) {
     constexpr int N = 288, TG = 12, P = 24, G = kZ288Pairs, RS = kZ288Rs, GS = kZ288Gs;
+    static_assert((TG - 1) * (P - 1) < N, "twiddle index t n1 stays below N");
     extern __shared__ __align__(16) float2 z288_dyn[];
     float2* stw = z288_dyn;                           // e^{-2 pi i m / 288}
     float2* sbuf = z288_dyn + N;                      // exchange buffers
-    float2* stage = sbuf + G * GS;                    // the round's input lines, [2 G][kin]
+    uint64_t* sbar = reinterpret_cast<uint64_t*>(sbuf + G * GS);   // completion barrier of the staging copies
+    float2* stage = sbuf + G * GS + 2;                // the round's input lines, [2 G][kin]
     const ZInvItem item = batch.it[blockIdx.y];
     const float2* __restrict__ in = static_cast<const float2*>(item.in);
     float* __restrict__ out = static_cast<float*>(item.out);
@@ -753,18 +796,42 @@ static __global__ void __launch_bounds__(192, 3) k_inv_z288(ZInvBatch batch, lon
     const long npairs = (nlines + 1) / 2;
     const long p_beg = (long)blockIdx.x * ppc;
     const long p_end = min(npairs, p_beg + ppc);
-    // the input lines of the round starting at pair q: lines 2q .. min(2 (q + G), nlines) - 1, contiguous
+    // A round's input lines, 2q .. min(2 (q + G), nlines) - 1, are one contiguous block: with an even line count
+    // (an even number of lines a round, 16 kin bytes a line pair) and a 16-byte aligned item, one bulk copy by the
+    // TMA engine stages it (completion on sbar); otherwise every thread issues its share of 16-byte cp.async copies.
+    const bool bulk = (nlines % 2 == 0) && (reinterpret_cast<uintptr_t>(in) & 15) == 0;
+    uint32_t phase = 0;
+    if (bulk && tid == 0) bulk_bar_init(sbar);
+    __syncthreads();                                  // the barrier is initialised before its first use
     auto issue = [&](long q) {
         const long l0 = 2 * q, l1 = min(2 * min(q + G, p_end), nlines);
-        stage_block(reinterpret_cast<unsigned char*>(stage), reinterpret_cast<const unsigned char*>(in + l0 * kin),
-                    (l1 - l0) * kin * (long)sizeof(float2), tid, kZ288Threads);
+        const long bytes = (l1 - l0) * kin * (long)sizeof(float2);
+        if (bulk) {
+            if (tid == 0) bulk_g2s(stage, in + l0 * kin, (uint32_t)bytes, sbar);
+        } else {
+            stage_block(reinterpret_cast<unsigned char*>(stage), reinterpret_cast<const unsigned char*>(in + l0 * kin),
+                        bytes, tid, kZ288Threads);
+        }
     };
     if (p_beg < p_end) issue(p_beg);
     for (long p0 = p_beg; p0 < p_end; p0 += G) {
         const long p = p0 + g;
         const bool act = p < p_end;
-        cp_async_wait_all();
-        __syncthreads();                              // the round's lines are in `stage`
+        if (bulk) {
+            // bounded wait for the round's copy; every thread takes the same decision (the barrier below)
+            const bool landed = bulk_wait(sbar, phase, kBulkSpinLimit);
+            phase ^= 1u;
+            if (!__syncthreads_and(landed)) {
+                if (tid == 0) {
+                    atomicExch(err, 1);
+                    bulk_wait(sbar, phase ^ 1u, kBulkSpinLimit);   // let the copy in flight land before exiting
+                }
+                return;
+            }
+        } else {
+            cp_async_wait_all();
+            __syncthreads();                          // the round's lines are in `stage`
+        }
         float2 v[P];
         {
             const bool has2 = act && 2 * p + 1 < nlines;
@@ -794,9 +861,9 @@ static __global__ void __launch_bounds__(192, 3) k_inv_z288(ZInvBatch batch, lon
         if (p0 + G < p_end) issue(p0 + G);
         // stage 1: 24-point DFT over j, twiddle w288^(t n1); rows n1 of the group's exchange buffer
         dft24<float, +1>(v);
-        // twiddle w288^(t n1) = conj(tw[t n1 mod N])
+        // twiddle w288^(t n1) = conj(tw[t n1]) (t n1 <= 11 x 23 < N: no reduction modulo N)
 #pragma unroll
-        for (int n1 = 1; n1 < P; ++n1) v[n1] = mulc<float>(v[n1], stw[(t * n1) % N]);
+        for (int n1 = 1; n1 < P; ++n1) v[n1] = mulc<float>(v[n1], stw[t * n1]);
 #pragma unroll
         for (int n1 = 0; n1 < P; ++n1) buf[n1 * RS + t] = v[n1];
         __syncthreads();

@@ -138,12 +138,15 @@ extern "C" int polybin_bk_ideal_multi(polybin_ctx* const* ctxs, const float* con
     if (e != cudaSuccess) return fail_cuda(c0, e, "cudaGraphLaunch", __FILE__, __LINE__);
     for (int i = 0; i < n_fields; ++i) {
         polybin_ctx* c = ctxs[i];
-        int herr = 0;
+        int herr[kErrFlags] = {0, 0};
         {
             polybin_ctx* ctx = c0;
-            PB_CUDA_OK(cudaMemcpy(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+            PB_CUDA_OK(cudaMemcpy(herr, c->d_err, sizeof(herr), cudaMemcpyDeviceToHost));
+            if (herr[kErrStaging]) PB_CUDA_OK(cudaMemset(c->d_err + kErrStaging, 0, sizeof(int)));
         }
-        if (herr) return fail(c0, POLYBIN_ETIMEOUT, "polybin_bk_ideal_multi: a pipeline wait timed out (field %d)", i);
+        if (herr[kErrPipeline] || herr[kErrStaging])
+            return fail(c0, POLYBIN_ETIMEOUT, "polybin_bk_ideal_multi: a %s wait timed out (field %d)",
+                        herr[kErrStaging] ? "bulk staging" : "pipeline", i);
         const double* B = m->host + m->off[i];
         std::memcpy(bk_out[i], B, sizeof(double) * c->Nabc.size());
     }

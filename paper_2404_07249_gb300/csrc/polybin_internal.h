@@ -139,7 +139,12 @@ void destroy_optimal(polybin_ctx*);
 void destroy_extras(polybin_ctx*);
 void destroy_unwindowed(polybin_ctx*);
 void destroy_multi(polybin_ctx*);
+// Device error flags of a context: [kErrPipeline] the tensor-core kernels' bounded waits (cleared before each of
+// their launches), [kErrStaging] the bulk staging copies of the transform passes (cleared when reported).
+constexpr int kErrPipeline = 0, kErrStaging = 1, kErrFlags = 2;
 int ensure_err_flag(polybin_ctx*);
+int read_err_flags(polybin_ctx*, const char* what);
+int run_bulk_wait_selftest(polybin_ctx*, unsigned limit);
 
 }  // namespace pb
 
@@ -219,7 +224,7 @@ struct polybin_ctx {
     double observer[3] = {0.0, 0.0, 0.0};
     // the contraction kernel that ran last (polybin_contract_path values), -1 before the first contraction
     int last_path = -1;
-    // device error flag of the kernels with bounded waits
+    // device error flags of the kernels with bounded waits ([kErrFlags] ints)
     int* d_err = nullptr;
     // stream capture in progress: kernels are enqueued without host synchronisation or read-backs
     bool capturing = false;
