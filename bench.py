@@ -39,8 +39,8 @@ UNIT = "estimates/s"
 E2E_BATCH = 8   # fields a call in the end-to-end measurement (pinned host memory: 8 x 537 MB at 512^3)
 
 CAPTURED_TRAFFIC = {
-    ("373cb97f2b0fe1b34501ac5024d188a48b5596215a4dff1f9db08c34f6f532d9", "lognormal_kaiser512", "split"):
-        2866815744 + 3194112,
+    ("d0adcdac6517b4a7bcd1f13ff32d196a0d7b114e6af7dc113e7bf9bd4606e7a5", "lognormal_kaiser512", "split"):
+        2866680832 + 3096832,
 }
 
 
