@@ -757,6 +757,8 @@ extern "C" int polybin_init(polybin_ctx** out, const int grid[3], const double b
         if (e != cudaSuccess) rc = fail_cuda(ctx, e, "pairs upload", __FILE__, __LINE__);
     }
     if (!rc) rc = plan_pk(ctx);
+    // the device error flags exist from the start (kernels captured into CUDA graphs write them)
+    if (!rc) rc = ensure_err_flag(ctx);
     if (!rc) rc = (prec == POLYBIN_FP64) ? alloc_work<double>(ctx, ctx->w) : alloc_work<float>(ctx, ctx->w);
     if (!rc && prec == POLYBIN_SPLIT_TF32X3) rc = tf32_selfcheck(ctx);
     if (rc) {

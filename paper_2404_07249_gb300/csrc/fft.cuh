@@ -237,6 +237,46 @@ __device__ __forceinline__ void stage_twiddles(C<T>* dst, const C<T>* __restrict
     for (int i = tid; i < n; i += nthr) dst[i] = tw[i];
 }
 
+// One-shot bulk copy global -> shared through the TMA engine (cp.async.bulk: both addresses 16-byte aligned, size a
+// multiple of 16), completing on an mbarrier with the byte count; and the bounded wait on that barrier.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void bulk_bar_init(uint64_t* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n\tfence.mbarrier_init.release.cluster;" ::"r"(smem_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "fence.proxy.async.shared::cta;\n\t"
+        "mbarrier.arrive.expect_tx.shared::cta.b64 _, [%2], %3;\n\t"
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %3, [%2];" ::"r"(smem_addr(dst)),
+        "l"(src), "r"(smem_addr(bar)), "r"(bytes)
+        : "memory");
+}
+// Waits for phase `parity` of the barrier; false after `limit` polls (the copy never landed).
+__device__ __forceinline__ bool bulk_wait(uint64_t* bar, uint32_t parity, unsigned limit) {
+    for (unsigned it = 0; it < limit; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(smem_addr(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+constexpr unsigned kBulkSpinLimit = 1u << 22;
+// Self-test of the staging wait: a barrier armed for 16 bytes that no copy delivers (none is issued); the bounded
+// wait gives up and raises the flag.
+static __global__ void k_bulk_wait_selftest(int* err, unsigned limit) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        bulk_bar_init(&bar);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], 16;" ::"r"(smem_addr(&bar)) : "memory");
+        if (!bulk_wait(&bar, 0u, limit)) atomicExch(err, 1);
+    }
+}
+
 // ------------------------------------------------------------------------------------------------
 // z-pass, forward: pairs of real lines (lines 2p, 2p+1 of the flattened (x, y) index) packed as one
 // complex line, transformed, then split into the two Hermitian half-spectra; only kz < kout is stored.
@@ -724,46 +764,6 @@ __device__ __forceinline__ void stage_block(unsigned char* dst, const unsigned c
     for (long i = tid; i < n16; i += nthr) cp_async16(dst + 16 * i, src + 16 * i);
     if ((bytes & 15) && tid == 0) cp_async8(dst + 16 * n16, src + 16 * n16);
     cp_async_commit();
-}
-
-// One-shot bulk copy global -> shared through the TMA engine (cp.async.bulk: both addresses 16-byte aligned, size a
-// multiple of 16), completing on an mbarrier with the byte count; and the bounded wait on that barrier.
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void bulk_bar_init(uint64_t* bar) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n\tfence.mbarrier_init.release.cluster;" ::"r"(smem_addr(bar))
-                 : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile(
-        "fence.proxy.async.shared::cta;\n\t"
-        "mbarrier.arrive.expect_tx.shared::cta.b64 _, [%2], %3;\n\t"
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %3, [%2];" ::"r"(smem_addr(dst)),
-        "l"(src), "r"(smem_addr(bar)), "r"(bytes)
-        : "memory");
-}
-// Waits for phase `parity` of the barrier; false after `limit` polls (the copy never landed).
-__device__ __forceinline__ bool bulk_wait(uint64_t* bar, uint32_t parity, unsigned limit) {
-    for (unsigned it = 0; it < limit; ++it) {
-        uint32_t ok;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(ok)
-            : "r"(smem_addr(bar)), "r"(parity)
-            : "memory");
-        if (ok) return true;
-    }
-    return false;
-}
-constexpr unsigned kBulkSpinLimit = 1u << 22;
-// Self-test of the staging wait: a barrier armed for 16 bytes that no copy delivers (none is issued); the bounded
-// wait gives up and raises the flag.
-static __global__ void k_bulk_wait_selftest(int* err, unsigned limit) {
-    __shared__ uint64_t bar;
-    if (threadIdx.x == 0) {
-        bulk_bar_init(&bar);
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], 16;" ::"r"(smem_addr(&bar)) : "memory");
-        if (!bulk_wait(&bar, 0u, limit)) atomicExch(err, 1);
-    }
 }
 
 constexpr int kZ288Threads = 192, kZ288Pairs = 16, kZ288Kmax = 145;

@@ -189,14 +189,22 @@ def test_unwindowed_bk_end_to_end(pkg, fields):
 
 
 def test_fisher_ideal_limit(pkg):
-    """n = w = 1: the Monte Carlo B Fisher is centred on the ideal diagonal N_abc / (N Delta)."""
+    """n = w = 1: the Monte Carlo B Fisher equals the oracle's on the same four draw pairs element by element, and its
+    diagonal is centred on the ideal N_abc / (N Delta): over the triplets the mean ratio is within 5 % of 1 (the oracle
+    gives 1.003 with a standard error of 0.011 over these 19 triplets, and 1.011 +- 0.003 with 32 pairs: the ideal
+    form is the continuum count, so a per-cent offset remains), every ratio within 25 %."""
     pb = pkg.PolyBin(GRID, BOX, BK_EDGES, prec="split")
     abc, nabc = pb.triplets()
+    trip = [tuple(t) for t in abc.tolist()]
     one = torch.ones(GRID, device="cuda")
     F, _ = pb.fisher(one, one, 4, SEED, 1)
+    bins = binning.bin_grid(GRID, BOX, BK_EDGES)
+    ones = np.ones(GRID)
+    Fref = unwindowed.bk_fisher(ones, ones, bins, len(BK_EDGES) - 1, trip, SEED, 4, np.float32)
+    assert _fisher_close(F, Fref, 1e-6) < 1e-6
     N = np.prod(GRID)
-    dl = np.array([binning.degeneracy(*t) for t in abc.tolist()])
-    ideal_diag = nabc / (N * dl)
-    ratio = np.diag(F) / ideal_diag
-    assert abs(np.median(ratio) - 1.0) < 0.2, ratio
+    dl = np.array([binning.degeneracy(*t) for t in trip])
+    ratio = np.diag(F) / (nabc / (N * dl))
+    assert abs(np.mean(ratio) - 1.0) < 0.05, ratio
+    assert np.all(np.abs(ratio - 1.0) < 0.25), ratio
     pb.close()
