@@ -194,11 +194,17 @@ int run_shells_m(polybin_ctx* ctx, const C<T>* box, C<T>* u1, C<T>* u2, T* g, in
             it.ncols = bb.rz.cnt; it.nouter = N0; it.rng = bb.ry;
             maxc = std::max(maxc, bb.rz.cnt);
         }
-        dim3 grid((maxc + TK - 1) / TK, N0, nb);
-        PB_WITH_NT_INV(N1, NT, {
-            if ((rc = set_smem<T>(ctx, (const void*)k_col<T, +1, NT>, sm))) return rc;
-            k_col<T, +1, NT><<<grid, 256, sm, ctx->stream>>>(b, ig.plan[1], tw(1), TK);
-        })
+        if (N1 == 288 && sizeof(T) == 4) {
+            // register-resident 288-point columns, 16 wave numbers kz a CTA
+            dim3 grid288((maxc + kY288Cols - 1) / kY288Cols, N0, nb);
+            k_inv_y288<<<grid288, kY288Threads, y288_smem(), ctx->stream>>>(b, (const float2*)tw(1));
+        } else {
+            dim3 grid((maxc + TK - 1) / TK, N0, nb);
+            PB_WITH_NT_INV(N1, NT, {
+                if ((rc = set_smem<T>(ctx, (const void*)k_col<T, +1, NT>, sm))) return rc;
+                k_col<T, +1, NT><<<grid, 256, sm, ctx->stream>>>(b, ig.plan[1], tw(1), TK);
+            })
+        }
         if ((rc = launch_check(ctx, "k_col inv y"))) return rc;
     }
     {

@@ -1005,6 +1005,63 @@ __global__ void __launch_bounds__(256) k_col(ColBatch batch, FftPlan plan, const
 }
 
 // ------------------------------------------------------------------------------------------------
+// Inverse y pass on 288-point columns (FP32), register-resident: the same two-stage transform as k_inv_z288
+// (k = t + 12 j, n = n1 + 24 n2; a 24-point DFT over j, the twiddle w288^(t n1), a 12-point DFT over t), applied to
+// complex columns.  A CTA of 192 threads takes 16 consecutive columns (wave numbers kz) of one x slab of one bin:
+// thread (t, c) = (tid / 16, tid % 16) loads its 24 points straight from the bin's pruned input (rows = the bin's
+// y wave numbers; zero outside them), so a warp reads and writes two rows of 16 consecutive columns (128 bytes
+// each) at a time; the two stages exchange through shared memory (one 24 x 13 buffer a column).
+constexpr int kY288Cols = 16, kY288Threads = 12 * kY288Cols;
+// exchange buffers 313 float2 apart (>= 24 x 13; odd, so the 16 columns a half-warp touches fall on distinct bank
+// pairs: 2 x 313 = 18 mod 32 words)
+constexpr int kY288Gs = 313;
+inline size_t y288_smem() { return (size_t)(288 + kY288Cols * kY288Gs) * sizeof(float2); }
+
+static __global__ void __launch_bounds__(192, 3) k_inv_y288(ColBatch batch, const float2* __restrict__ twg) {
+    constexpr int N = 288, TG = 12, P = 24, TC = kY288Cols, RS = kZ288Rs, GS = kY288Gs;
+    static_assert(P * RS <= GS, "a column's exchange buffer holds 24 rows of 13");
+    static_assert((TG - 1) * (P - 1) < N, "twiddle index t n1 stays below N");
+    extern __shared__ __align__(16) float2 y288_dyn[];
+    float2* stw = y288_dyn;                           // e^{-2 pi i m / 288}
+    const ColItem item = batch.it[blockIdx.z];
+    const int c0 = blockIdx.x * TC, o = blockIdx.y;
+    if (c0 >= item.ncols || o >= item.nouter) return;   // uniform over the CTA
+    const int tid = threadIdx.x, t = tid / TC, c = tid - t * TC;
+    float2* buf = y288_dyn + N + c * GS;              // this column's exchange buffer
+    for (int i = tid; i < N; i += kY288Threads) stw[i] = twg[i];
+    const bool act = c0 + c < item.ncols;
+    const float2* __restrict__ in = static_cast<const float2*>(item.in) + (long)o * item.in_os + c0 + c;
+    float2* __restrict__ out = static_cast<float2*>(item.out) + (long)o * item.out_os + c0 + c;
+    // points k = t + 12 j: wave number f = k (k < 144) or k - 288, input row f - lo when inside the bin's range
+    float2 v[P];
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+        const int k = t + TG * j;
+        const int i = (k < N / 2 ? k : k - N) - item.rng.lo;
+        v[j] = (act && i >= 0 && i < item.rng.cnt) ? in[(long)i * item.in_es] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();                                  // the twiddle table is in place
+    dft24<float, +1>(v);
+#pragma unroll
+    for (int n1 = 1; n1 < P; ++n1) v[n1] = mulc<float>(v[n1], stw[t * n1]);
+#pragma unroll
+    for (int n1 = 0; n1 < P; ++n1) buf[n1 * RS + t] = v[n1];
+    __syncthreads();
+    float2 w[2][TG];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+#pragma unroll
+        for (int u = 0; u < TG; ++u) w[h][u] = buf[(t + 12 * h) * RS + u];
+        dft12<float, +1>(w[h]);
+    }
+    if (!act) return;
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int n2 = 0; n2 < TG; ++n2) out[(long)(t + 12 * h + 24 * n2) * item.out_es] = w[h][n2];
+}
+
+// ------------------------------------------------------------------------------------------------
 // First inverse pass with the shell filter: for bin b, columns are the (n_y, n_z) points of that bin's
 // bounding box (flattened, n_z fastest); along x only wave numbers in the bin's x-range are loaded,
 // each multiplied by Theta_b(|n|) (bin lookup on the integer |n|^2), an optional per-mode weight

@@ -57,6 +57,8 @@ CASES = [
     ((8, 8, 256), 2000.0, 0.5 + 11.25 * np.arange(9), "lognormal"),   # m = 90: shells on 256-point z lines
     ((20, 10, 100), 1500.0, 1.0 + 2.0 * np.arange(8), "lognormal"),   # compile-time 100-point passes (z)
     ((100, 100, 20), 1500.0, 1.0 + 2.0 * np.arange(8), "lognormal"),  # compile-time 100-point column passes
+    ((6, 288, 8), 2000.0, 1.0 + 20.0 * np.arange(8), "lognormal"),    # 288-point y columns up to |n_y| = 141
+    ((4, 288, 64), 2000.0, 1.0 + 4.0 * np.arange(8), "lognormal"),    # 288-point y columns, 29 kz columns (2 CTAs)
 ]
 
 
