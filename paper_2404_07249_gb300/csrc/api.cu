@@ -172,12 +172,21 @@ int run_shells_m(polybin_ctx* ctx, const C<T>* box, C<T>* u1, C<T>* u2, T* g, in
             b.it[i].m = m;
             maxcols = std::max(maxcols, bb.ry.cnt * bb.rz.cnt);
         }
-        dim3 grid((maxcols + TK - 1) / TK, nb, 1);
-        PB_WITH_NT_INV(N0, NT, {
-            if ((rc = set_smem<T>(ctx, (const void*)k_inv_x_filter<T, NT>, sm))) return rc;
-            k_inv_x_filter<T, NT><<<grid, 256, sm, ctx->stream>>>(b, box, ctx->gx, ctx->gy, ctx->gz, ctx->d_lut, ctx->smax,
-                                                                  T(1.0 / (double)ctx->ncell), ig.plan[0], tw(0), TK);
-        })
+        if (N0 == 288 && sizeof(T) == 4) {
+            // register-resident 288-point x lines, 16 columns of the bin's box a CTA
+            dim3 grid288((maxcols + kY288Cols - 1) / kY288Cols, nb, 1);
+            k_inv_x288_filter<<<grid288, kY288Threads, y288_smem(), ctx->stream>>>(
+                b, (const float2*)box, ctx->gx, ctx->gy, ctx->gz, ctx->d_lut, ctx->smax, (float)(1.0 / (double)ctx->ncell),
+                (const float2*)tw(0));
+        } else {
+            dim3 grid((maxcols + TK - 1) / TK, nb, 1);
+            PB_WITH_NT_INV(N0, NT, {
+                if ((rc = set_smem<T>(ctx, (const void*)k_inv_x_filter<T, NT>, sm))) return rc;
+                k_inv_x_filter<T, NT><<<grid, 256, sm, ctx->stream>>>(b, box, ctx->gx, ctx->gy, ctx->gz, ctx->d_lut,
+                                                                      ctx->smax, T(1.0 / (double)ctx->ncell), ig.plan[0],
+                                                                      tw(0), TK);
+            })
+        }
         if ((rc = launch_check(ctx, "k_inv_x_filter"))) return rc;
     }
     {

@@ -1079,6 +1079,29 @@ struct XInvBatch {
     XInvItem it[kMaxItems];
 };
 
+// Theta_b(|n|) x weight x scale x D(n) at the mode (fx, fy, fz) of the item's bin; false outside the bin.
+template <typename T>
+__device__ __forceinline__ bool x_filter_value(const XInvItem& item, const C<T>* __restrict__ spec, AxisRange gx,
+                                               AxisRange gy, AxisRange gz, const int16_t* __restrict__ lut, int smax,
+                                               T scale, int fx, int fy, int fz, C<T>& v) {
+    const int s = fx * fx + fy * fy + fz * fz;
+    if (s > smax || lut[s] != item.bin) return false;
+    T wgt = scale;
+    if (item.ell && item.m == kLegendreM) {
+        const T mu2 = T(fz * fz) / T(s);
+        wgt *= item.ell == 2 ? T(0.5) * (T(3) * mu2 - T(1)) : (T(35) * mu2 * mu2 - T(30) * mu2 + T(3)) / T(8);
+    } else if (item.ell) {
+        const T inv = T(1) / sqrt(T(s));
+        wgt *= ybar<T>(item.ell, item.m, T(fx) * inv, T(fy) * inv, T(fz) * inv);
+    }
+    v = mk<T>(wgt, T(0));
+    if (spec) {
+        const C<T> d = spec[(long)(fx - gx.lo) * ((long)gy.cnt * gz.cnt) + (long)(fy - gy.lo) * gz.cnt + (fz - gz.lo)];
+        v = mk<T>(d.x * wgt, d.y * wgt);
+    }
+    return true;
+}
+
 template <typename T, int NT = 0>
 __global__ void __launch_bounds__(256) k_inv_x_filter(XInvBatch batch, const C<T>* __restrict__ spec,
                                                       AxisRange gx, AxisRange gy, AxisRange gz,
@@ -1098,7 +1121,6 @@ __global__ void __launch_bounds__(256) k_inv_x_filter(XInvBatch batch, const C<T
     C<T>* tw = b1 + (size_t)n * TK;
     const int tid = threadIdx.x, nthr = blockDim.x;
     stage_twiddles<T>(tw, twg, n, tid, nthr);
-    const long gyz = (long)gy.cnt * gz.cnt;
     // the filtered value of element idx (column c, x index i) and its shared-memory slot (-1: outside the bin)
     auto element = [&](int idx, C<T>& v) -> int {
         const int c = idx % TK, i = idx / TK;
@@ -1107,21 +1129,7 @@ __global__ void __launch_bounds__(256) k_inv_x_filter(XInvBatch batch, const C<T
         const int fy = item.ry.lo + cc / item.rz.cnt;
         const int fz = item.rz.lo + cc % item.rz.cnt;
         const int fx = item.rx.lo + i;
-        const int s = fx * fx + fy * fy + fz * fz;
-        if (s > smax || lut[s] != item.bin) return -1;
-        T wgt = scale;
-        if (item.ell && item.m == kLegendreM) {
-            const T mu2 = T(fz * fz) / T(s);
-            wgt *= item.ell == 2 ? T(0.5) * (T(3) * mu2 - T(1)) : (T(35) * mu2 * mu2 - T(30) * mu2 + T(3)) / T(8);
-        } else if (item.ell) {
-            const T inv = T(1) / sqrt(T(s));
-            wgt *= ybar<T>(item.ell, item.m, T(fx) * inv, T(fy) * inv, T(fz) * inv);
-        }
-        v = mk<T>(wgt, T(0));
-        if (spec) {
-            const C<T> d = spec[(long)(fx - gx.lo) * gyz + (long)(fy - gy.lo) * gz.cnt + (fz - gz.lo)];
-            v = mk<T>(d.x * wgt, d.y * wgt);
-        }
+        if (!x_filter_value<T>(item, spec, gx, gy, gz, lut, smax, scale, fx, fy, fz, v)) return -1;
         return c + pos_of(fx, n) * TK;
     };
     if constexpr (NT > 0) {
@@ -1161,6 +1169,60 @@ __global__ void __launch_bounds__(256) k_inv_x_filter(XInvBatch batch, const C<T
         const int c = idx % TK, i = idx / TK;
         if (c < nc) out[(long)i * ncols + c0 + c] = z[idx];
     }
+}
+
+// The filter + x IFFT on 288-point x lines (FP32), register-resident like k_inv_y288: a CTA of 192 threads takes 16
+// consecutive columns (points (n_y, n_z) of the bin's box, n_z fastest) of one bin; thread (t, c) forms its 24
+// filtered points k = t + 12 j (wave number n_x = k or k - 288, zero outside the bin's x range and the bin) and
+// takes the two-stage 288-point transform; rows of 16 consecutive columns are written (128 bytes).
+static __global__ void __launch_bounds__(192, 3) k_inv_x288_filter(XInvBatch batch, const float2* __restrict__ spec,
+                                                                  AxisRange gx, AxisRange gy, AxisRange gz,
+                                                                  const int16_t* __restrict__ lut, int smax,
+                                                                  float scale, const float2* __restrict__ twg) {
+    constexpr int N = 288, TG = 12, P = 24, TC = kY288Cols, RS = kZ288Rs, GS = kY288Gs;
+    extern __shared__ __align__(16) float2 x288_dyn[];
+    float2* stw = x288_dyn;                           // e^{-2 pi i m / 288}
+    const XInvItem item = batch.it[blockIdx.y];
+    const int ncols = item.ry.cnt * item.rz.cnt;
+    const int c0 = blockIdx.x * TC;
+    if (c0 >= ncols) return;                          // uniform over the CTA
+    const int tid = threadIdx.x, t = tid / TC, c = tid - t * TC;
+    float2* buf = x288_dyn + N + c * GS;
+    for (int i = tid; i < N; i += kY288Threads) stw[i] = twg[i];
+    const int cc = c0 + c;
+    const bool act = cc < ncols;
+    const int fy = act ? item.ry.lo + cc / item.rz.cnt : 0;
+    const int fz = act ? item.rz.lo + cc % item.rz.cnt : 0;
+    float2 v[P];
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+        const int k = t + TG * j;
+        const int fx = k < N / 2 ? k : k - N;
+        const int i = fx - item.rx.lo;
+        float2 x = make_float2(0.f, 0.f);          // stays zero outside the bin
+        if (act && i >= 0 && i < item.rx.cnt) x_filter_value<float>(item, spec, gx, gy, gz, lut, smax, scale, fx, fy, fz, x);
+        v[j] = x;
+    }
+    __syncthreads();                                  // the twiddle table is in place
+    dft24<float, +1>(v);
+#pragma unroll
+    for (int n1 = 1; n1 < P; ++n1) v[n1] = mulc<float>(v[n1], stw[t * n1]);
+#pragma unroll
+    for (int n1 = 0; n1 < P; ++n1) buf[n1 * RS + t] = v[n1];
+    __syncthreads();
+    float2 w[2][TG];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+#pragma unroll
+        for (int u = 0; u < TG; ++u) w[h][u] = buf[(t + 12 * h) * RS + u];
+        dft12<float, +1>(w[h]);
+    }
+    if (!act) return;
+    float2* __restrict__ out = static_cast<float2*>(item.out) + cc;
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int n2 = 0; n2 < TG; ++n2) out[(long)(t + 12 * h + 24 * n2) * ncols] = w[h][n2];
 }
 
 }  // namespace pb

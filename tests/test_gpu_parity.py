@@ -59,6 +59,7 @@ CASES = [
     ((100, 100, 20), 1500.0, 1.0 + 2.0 * np.arange(8), "lognormal"),  # compile-time 100-point column passes
     ((6, 288, 8), 2000.0, 1.0 + 20.0 * np.arange(8), "lognormal"),    # 288-point y columns up to |n_y| = 141
     ((4, 288, 64), 2000.0, 1.0 + 4.0 * np.arange(8), "lognormal"),    # 288-point y columns, 29 kz columns (2 CTAs)
+    ((288, 6, 8), 2000.0, 1.0 + 20.0 * np.arange(8), "lognormal"),    # 288-point x lines with the shell filter
 ]
 
 
