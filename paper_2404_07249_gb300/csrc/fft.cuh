@@ -1085,9 +1085,6 @@ __device__ __forceinline__ bool x_filter_value(const XInvItem& item, const C<T>*
                                                AxisRange gy, AxisRange gz, const int16_t* __restrict__ lut, int smax,
                                                T scale, int fx, int fy, int fz, C<T>& v) {
     const int s = fx * fx + fy * fy + fz * fz;
-    // the mode lies in the spectrum's box, so its load is issued before (and overlaps) the bin look-up
-    C<T> d = mk<T>(T(1), T(0));
-    if (spec) d = spec[(long)(fx - gx.lo) * ((long)gy.cnt * gz.cnt) + (long)(fy - gy.lo) * gz.cnt + (fz - gz.lo)];
     if (s > smax || lut[s] != item.bin) return false;
     T wgt = scale;
     if (item.ell && item.m == kLegendreM) {
@@ -1097,7 +1094,11 @@ __device__ __forceinline__ bool x_filter_value(const XInvItem& item, const C<T>*
         const T inv = T(1) / sqrt(T(s));
         wgt *= ybar<T>(item.ell, item.m, T(fx) * inv, T(fy) * inv, T(fz) * inv);
     }
-    v = spec ? mk<T>(d.x * wgt, d.y * wgt) : mk<T>(wgt, T(0));
+    v = mk<T>(wgt, T(0));
+    if (spec) {
+        const C<T> d = spec[(long)(fx - gx.lo) * ((long)gy.cnt * gz.cnt) + (long)(fy - gy.lo) * gz.cnt + (fz - gz.lo)];
+        v = mk<T>(d.x * wgt, d.y * wgt);
+    }
     return true;
 }
 
