@@ -168,6 +168,8 @@ int run_shells_m(polybin_ctx* ctx, const C<T>* box, C<T>* u1, C<T>* u2, T* g, in
             b.it[i].out = u1 + bb.u1_off;
             b.it[i].rx = bb.rx; b.it[i].ry = bb.ry; b.it[i].rz = bb.rz;
             b.it[i].bin = i;
+            b.it[i].slo = ctx->bin_slo[i];
+            b.it[i].shi = ctx->bin_shi[i];
             b.it[i].ell = ell;
             b.it[i].m = m;
             maxcols = std::max(maxcols, bb.ry.cnt * bb.rz.cnt);
@@ -176,15 +178,13 @@ int run_shells_m(polybin_ctx* ctx, const C<T>* box, C<T>* u1, C<T>* u2, T* g, in
             // register-resident 288-point x lines, 16 columns of the bin's box a CTA
             dim3 grid288((maxcols + kY288Cols - 1) / kY288Cols, nb, 1);
             k_inv_x288_filter<<<grid288, kY288Threads, y288_smem(), ctx->stream>>>(
-                b, (const float2*)box, ctx->gx, ctx->gy, ctx->gz, ctx->d_lut, ctx->smax, (float)(1.0 / (double)ctx->ncell),
-                (const float2*)tw(0));
+                b, (const float2*)box, ctx->gx, ctx->gy, ctx->gz, (float)(1.0 / (double)ctx->ncell), (const float2*)tw(0));
         } else {
             dim3 grid((maxcols + TK - 1) / TK, nb, 1);
             PB_WITH_NT_INV(N0, NT, {
                 if ((rc = set_smem<T>(ctx, (const void*)k_inv_x_filter<T, NT>, sm))) return rc;
-                k_inv_x_filter<T, NT><<<grid, 256, sm, ctx->stream>>>(b, box, ctx->gx, ctx->gy, ctx->gz, ctx->d_lut,
-                                                                      ctx->smax, T(1.0 / (double)ctx->ncell), ig.plan[0],
-                                                                      tw(0), TK);
+                k_inv_x_filter<T, NT><<<grid, 256, sm, ctx->stream>>>(b, box, ctx->gx, ctx->gy, ctx->gz,
+                                                                      T(1.0 / (double)ctx->ncell), ig.plan[0], tw(0), TK);
             })
         }
         if ((rc = launch_check(ctx, "k_inv_x_filter"))) return rc;
@@ -403,6 +403,18 @@ static int plan_bins(polybin_ctx* ctx) {
         for (int b = 0; b < nb; ++b)
             if (k >= ctx->edges[b] && k < ctx->edges[b + 1]) { ctx->lut[s] = (int16_t)b; break; }
     }
+    // each bin is one contiguous range of |n|^2 (ascending edges): the shell filter tests the range, not the table
+    ctx->bin_slo.assign(nb, 1);
+    ctx->bin_shi.assign(nb, 0);
+    for (long s = 1; s <= smax; ++s) {
+        const int b = ctx->lut[s];
+        if (b < 0) continue;
+        if (ctx->bin_shi[b] < ctx->bin_slo[b]) ctx->bin_slo[b] = (int)s;
+        ctx->bin_shi[b] = (int)s;
+    }
+    for (int b = 0; b < nb; ++b)
+        for (int s = ctx->bin_slo[b]; s <= ctx->bin_shi[b]; ++s)
+            if (ctx->lut[s] != b) return fail(ctx, POLYBIN_EINVAL, "bin %d is not one range of |n|^2", b);
     const int m = max_component(kf, elast);
     ctx->gx = axis_box(m, ctx->N[0]);
     ctx->gy = axis_box(m, ctx->N[1]);

@@ -1064,7 +1064,7 @@ static __global__ void __launch_bounds__(192, 3) k_inv_y288(ColBatch batch, cons
 // ------------------------------------------------------------------------------------------------
 // First inverse pass with the shell filter: for bin b, columns are the (n_y, n_z) points of that bin's
 // bounding box (flattened, n_z fastest); along x only wave numbers in the bin's x-range are loaded,
-// each multiplied by Theta_b(|n|) (bin lookup on the integer |n|^2), an optional per-mode weight
+// each multiplied by Theta_b(|n|) (the bin's range of integer |n|^2), an optional per-mode weight
 // (|n|^2-indexed table wtab, or the Legendre factor of the line of sight), and `scale`.
 // spec == nullptr means a unit spectrum (the t_b maps that normalise the bispectrum).
 constexpr int kLegendreM = 100;   // XInvItem::m of the global line of sight (weight L_ell(mu))
@@ -1072,6 +1072,7 @@ struct XInvItem {
     void* out;            // C<T>* [n0][ry.cnt * rz.cnt]
     AxisRange rx, ry, rz; // bin bounding box
     int bin;
+    int slo, shi;         // the bin's range of integer |n|^2 (empty when slo > shi)
     int ell;              // 0: no weight; else L_ell(mu), mu = n_z / |n| (m == kLegendreM) or Ybar_lm(n / |n|)
     int m;
 };
@@ -1082,10 +1083,9 @@ struct XInvBatch {
 // Theta_b(|n|) x weight x scale x D(n) at the mode (fx, fy, fz) of the item's bin; false outside the bin.
 template <typename T>
 __device__ __forceinline__ bool x_filter_value(const XInvItem& item, const C<T>* __restrict__ spec, AxisRange gx,
-                                               AxisRange gy, AxisRange gz, const int16_t* __restrict__ lut, int smax,
-                                               T scale, int fx, int fy, int fz, C<T>& v) {
+                                               AxisRange gy, AxisRange gz, T scale, int fx, int fy, int fz, C<T>& v) {
     const int s = fx * fx + fy * fy + fz * fz;
-    if (s > smax || lut[s] != item.bin) return false;
+    if (s < item.slo || s > item.shi) return false;
     T wgt = scale;
     if (item.ell && item.m == kLegendreM) {
         const T mu2 = T(fz * fz) / T(s);
@@ -1104,8 +1104,7 @@ __device__ __forceinline__ bool x_filter_value(const XInvItem& item, const C<T>*
 
 template <typename T, int NT = 0>
 __global__ void __launch_bounds__(256) k_inv_x_filter(XInvBatch batch, const C<T>* __restrict__ spec,
-                                                      AxisRange gx, AxisRange gy, AxisRange gz,
-                                                      const int16_t* __restrict__ lut, int smax, T scale,
+                                                      AxisRange gx, AxisRange gy, AxisRange gz, T scale,
                                                       FftPlan plan, const C<T>* __restrict__ twg, int TKrt) {
     extern __shared__ unsigned char smem_raw[];
     constexpr int TT = NT > 0 ? cols_per_cta_of<T>(NT) : 0;
@@ -1129,7 +1128,7 @@ __global__ void __launch_bounds__(256) k_inv_x_filter(XInvBatch batch, const C<T
         const int fy = item.ry.lo + cc / item.rz.cnt;
         const int fz = item.rz.lo + cc % item.rz.cnt;
         const int fx = item.rx.lo + i;
-        if (!x_filter_value<T>(item, spec, gx, gy, gz, lut, smax, scale, fx, fy, fz, v)) return -1;
+        if (!x_filter_value<T>(item, spec, gx, gy, gz, scale, fx, fy, fz, v)) return -1;
         return c + pos_of(fx, n) * TK;
     };
     if constexpr (NT > 0) {
@@ -1177,7 +1176,6 @@ __global__ void __launch_bounds__(256) k_inv_x_filter(XInvBatch batch, const C<T
 // takes the two-stage 288-point transform; rows of 16 consecutive columns are written (128 bytes).
 static __global__ void __launch_bounds__(192, 3) k_inv_x288_filter(XInvBatch batch, const float2* __restrict__ spec,
                                                                   AxisRange gx, AxisRange gy, AxisRange gz,
-                                                                  const int16_t* __restrict__ lut, int smax,
                                                                   float scale, const float2* __restrict__ twg) {
     constexpr int N = 288, TG = 12, P = 24, TC = kY288Cols, RS = kZ288Rs, GS = kY288Gs;
     extern __shared__ __align__(16) float2 x288_dyn[];
@@ -1200,7 +1198,7 @@ static __global__ void __launch_bounds__(192, 3) k_inv_x288_filter(XInvBatch bat
         const int fx = k < N / 2 ? k : k - N;
         const int i = fx - item.rx.lo;
         float2 x = make_float2(0.f, 0.f);          // stays zero outside the bin
-        if (act && i >= 0 && i < item.rx.cnt) x_filter_value<float>(item, spec, gx, gy, gz, lut, smax, scale, fx, fy, fz, x);
+        if (act && i >= 0 && i < item.rx.cnt) x_filter_value<float>(item, spec, gx, gy, gz, scale, fx, fy, fz, x);
         v[j] = x;
     }
     __syncthreads();                                  // the twiddle table is in place

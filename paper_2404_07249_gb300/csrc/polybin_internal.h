@@ -167,6 +167,7 @@ struct polybin_ctx {
     void* d_ctw[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};   // contraction-grid twiddles (f, d)
     int smax = 0;
     std::vector<int16_t> lut;
+    std::vector<int> bin_slo, bin_shi;   // range of integer |n|^2 of each bin (bins are contiguous in |n|)
     int16_t* d_lut = nullptr;
     pb::FftPlan plan[3];
     void* d_tw_f[3] = {nullptr, nullptr, nullptr};
